@@ -1,0 +1,450 @@
+"""Benchmark of the spectral-cube ray caster on the survey-sized workload.
+
+One step = the whole hot path over the survey input (512 x 512 x 1024 float32 cube
+and its co-registered second line): separable Gaussian smoothing (sigma 2, radius 6)
+of both cubes, then one 1920 x 1080 perspective render (yaw 30, pitch 20, fov 45,
+step 0.5, trilinear) per transfer function -- MIP, average, compositing,
+spectral-position colouring, line ratio -- on the smoothed cubes.
+
+value   = ray-cast Gsamples/s over the whole job (samples of all renders of all ranks / time)
+e2e     = the same metric through the public API with host buffers: the two cubes copied
+          host->device and the five RGBA images copied back every step
+Launch: python bench.py [--gpus N --steps K --warmup W]; N > 1 under torchrun, one rank
+per GPU, each rank an independent replica (weak scaling, no collective on the data path).
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scene  # noqa: E402
+from scene import workloads as WL  # noqa: E402
+
+WORKLOADS = {"survey": WL.SURVEY, "survey-small": WL.SURVEY_SMALL}
+METRIC = "ray-cast Gsamples/s and fps vs plain FP32 path; fraction of HBM roofline"
+UNIT = "Gsamples/s"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            p = json.load(f)
+        return p, "measured"
+    except (OSError, ValueError):
+        return dict(FALLBACK_PEAKS), "fallback"
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples taken while the timed region runs."""
+    Q = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = bus_id
+        self.lines: list[str] = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.bus_id:
+            cmd += ["-i", self.bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                sm.append(float(f[2]))
+                mx.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[6:10]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- workload
+
+def make_inputs(w=None):
+    w = WL.SURVEY if w is None else w
+    t = time.time()
+    cube = scene.survey_cube(dims=w["dims"], n_sources=w["n_sources"])
+    cube2 = scene.ratio_cube(cube)
+    log(f"inputs generated in {time.time() - t:.1f}s")
+    return cube, cube2
+
+
+class Step:
+    """The survey step on one GPU: 2 smooths + 5 renders, all launches on one stream."""
+
+    def __init__(self, shw, torch, cube_t, cube2_t, w):
+        self.shw, self.torch, self.w = shw, torch, w
+        self.cam = WL.survey_camera(w=w)
+        dev = cube_t.device
+        self.cube, self.cube2 = cube_t, cube2_t
+        self.s1, self.s2 = torch.empty_like(cube_t), torch.empty_like(cube2_t)
+        self.lut = torch.from_numpy(scene.linear_lut()).to(dev)
+        self.rlut = torch.from_numpy(scene.ratio_lut()).to(dev)
+        H, W = self.cam.height, self.cam.width
+        self.outs = {m: {"rgba": torch.empty((H, W, 4), dtype=torch.float32, device=dev)} for m in WL.MODES}
+        self.names = ["smooth", "smooth2"] + [f"render_{m}" for m in WL.MODES]
+
+    def launches(self):
+        shw, w = self.shw, self.w
+        yield "smooth", lambda: shw.smooth(self.cube, w["sigma"], w["radius"], out=self.s1)
+        yield "smooth2", lambda: shw.smooth(self.cube2, w["sigma"], w["radius"], out=self.s2)
+        for m in WL.MODES:
+            kw = dict(WL.MODE_PARAMS[m])
+            lut = self.rlut if m == "ratio" else self.lut
+            yield f"render_{m}", (lambda m=m, kw=kw, lut=lut: shw.render(
+                self.s1, self.cam, m, lut=lut, vol2=self.s2 if m == "ratio" else None, step=w["step"],
+                scalar=False, index=False, nsamples=False, out=self.outs[m], **kw))
+
+    def run(self, events=None):
+        for name, fn in self.launches():
+            if events is not None:
+                e0 = self.torch.cuda.Event(enable_timing=True)
+                e1 = self.torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                events.setdefault(name, []).append((e0, e1))
+            else:
+                fn()
+
+    def count_samples(self):
+        """Samples per render (untimed pass with the per-ray sample-count output)."""
+        shw, w = self.shw, self.w
+        per = {}
+        shw.smooth(self.cube, w["sigma"], w["radius"], out=self.s1)
+        shw.smooth(self.cube2, w["sigma"], w["radius"], out=self.s2)
+        for m in WL.MODES:
+            kw = dict(WL.MODE_PARAMS[m])
+            lut = self.rlut if m == "ratio" else self.lut
+            o = shw.render(self.s1, self.cam, m, lut=lut, vol2=self.s2 if m == "ratio" else None, step=w["step"],
+                           scalar=False, index=False, nsamples=True, **kw)
+            per[m] = int(o["nsamples"].sum(dtype=self.torch.int64).item())
+        return per
+
+
+# --------------------------------------------------------------------------- roofline
+
+def kernel_roofline(name, t_ms, nvox, samples_per, peaks, sm_mhz):
+    """Algorithmic work per launch / measured duration, against the bound of that kernel."""
+    hbm = float(peaks["hbm_gbs"])
+    if name.startswith("smooth"):
+        bytes_ = 2 * 4 * nvox  # read the cube once, write the result once
+        ach = bytes_ / (t_ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(ach / hbm, 4), "algorithmic_bytes": bytes_}
+    mode = name[len("render_"):]
+    ns = samples_per[mode]
+    flops = ALG_FLOPS_PER_SAMPLE[mode] * ns
+    peak = FP32_LANES_PER_SM * 2 * SMS * float(sm_mhz) * 1e6 / 1e12  # TFLOP/s (FMA = 2)
+    ach = flops / (t_ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+            "frac": round(ach / peak, 4), "samples": ns,
+            "gsamples_per_s": round(ns / (t_ms * 1e-3) / 1e9, 2)}
+
+
+SMS = 152
+FP32_LANES_PER_SM = 128
+# FP32 flops the method needs per trilinear sample (see the design notes): 3 fraction weights,
+# 7 lerps (sub + FMA = 3 flops), plus the transfer function's own arithmetic.
+_TRI = 3 + 7 * 3
+ALG_FLOPS_PER_SAMPLE = {"mip": _TRI + 1, "spectral": _TRI + 1, "avg": _TRI + 4,
+                        "ratio": 2 * _TRI + 2, "composite": _TRI + 2 + 8 + 6 + 3 + 2}
+
+
+# --------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_1707_00442_gb300 as shw
+    shw._lib.lib()  # the CUDA library must load: there is no fallback
+
+    W = WORKLOADS[args.workload]
+    cube, cube2 = make_inputs(W)
+    nvox = cube.size
+    cube_h = torch.from_numpy(cube).pin_memory()
+    cube2_h = torch.from_numpy(cube2).pin_memory()
+    cube_t, cube2_t = cube_h.to(dev), cube2_h.to(dev)
+    step = Step(shw, torch, cube_t, cube2_t, W)
+    samples_per = step.count_samples()
+    samples_step = sum(samples_per.values())
+    log("samples per render:", samples_per)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step.run()
+    barrier()
+
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(dev).pci_bus_id
+    except Exception:
+        bus = None
+    clocks = ClockSampler(bus_id=None if bus is None else str(bus))
+    clocks.start()
+
+    events = {}
+    launches0 = shw.launch_count()
+    barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for _ in range(args.steps):
+        step.run(events)
+    t1.record()
+    barrier()
+    launches = shw.launch_count() - launches0
+    clk = clocks.stop()
+    ms_total = t0.elapsed_time(t1)
+    if world > 1:
+        tt = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    per_kernel = {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in events.items()}
+
+    # end to end through the public API with host buffers
+    rgba_h = {m: torch.empty(step.outs[m]["rgba"].shape, dtype=torch.float32).pin_memory() for m in WL.MODES}
+    for _ in range(1):
+        cube_t.copy_(cube_h, non_blocking=True)
+        cube2_t.copy_(cube2_h, non_blocking=True)
+        step.run()
+        for m in WL.MODES:
+            rgba_h[m].copy_(step.outs[m]["rgba"], non_blocking=True)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        cube_t.copy_(cube_h, non_blocking=True)
+        cube2_t.copy_(cube2_h, non_blocking=True)
+        step.run()
+        for m in WL.MODES:
+            rgba_h[m].copy_(step.outs[m]["rgba"], non_blocking=True)
+    e1.record()
+    barrier()
+    ms_e2e = e0.elapsed_time(e1)
+    if world > 1:
+        tt = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_e2e = float(tt.item())
+    h2d = 2 * nvox * 4
+    d2h = sum(int(np.prod(rgba_h[m].shape)) * 4 for m in WL.MODES)
+
+    peaks, peaks_src = load_peaks()
+    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1485.0
+    roof = {k: kernel_roofline(k, t, nvox, samples_per, peaks, sm_mhz) for k, t in per_kernel.items()}
+    total_by_kind = {k: per_kernel[k] for k in per_kernel}
+    dom = max(total_by_kind, key=total_by_kind.get)
+
+    value = world * samples_step * args.steps / (ms_total * 1e-3) / 1e9
+    e2e_value = world * samples_step * args.steps / (ms_e2e * 1e-3) / 1e9
+    res = None
+    if rank == 0:
+        dr = dict(roof[dom])
+        dr["kernel"] = dom
+        dr["peak_source"] = f"{peaks_src} ({'MEASURED_PEAKS.json hbm_gbs' if dr['bound'] == 'hbm' else 'SMs x 128 FP32 lanes x 2 x median SM clock under load'})"
+        dr["traffic"] = TRAFFIC_PER_LAUNCH.get(dom)
+        res = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": W["name"], "cube": "x".join(map(str, W["dims"])) + " f32 + ratio cube",
+                       "image": f"{W['width']}x{W['height']} perspective yaw30 pitch20 fov45", "step_vox": W["step"],
+                       "modes": WL.MODES, "smooth": "sigma 2, radius 6, both cubes", "interp": "trilinear",
+                       "l2": "inputs larger than L2 (1 GiB cubes vs 129 MB L2)",
+                       "samples_per_step": samples_step, "parallelism": f"replicas x{world}"},
+            "fps": {m: round(1000.0 / per_kernel[f"render_{m}"], 1) for m in WL.MODES},
+            "steps_per_s": round(1000.0 * args.steps / ms_total, 2),
+            "per_kernel_ms": {k: round(v, 4) for k, v in per_kernel.items()},
+            "roofline": dr,
+            "roofline_kernels": roof,
+            "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e / args.steps, 3)},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return res, samples_per
+
+
+# ncu dram bytes per launch of the dominant kernels (null until captured for the current kernel)
+TRAFFIC_PER_LAUNCH: dict = {}
+
+
+# --------------------------------------------------------------------------- oracle (CPU) arm
+
+def oracle_sample(budget_s: float, samples_per_frame=None):
+    """Time the FP64 oracle on a bounded sample of the survey step on the host cores.
+
+    Sample: a random subset of pixels of each of the five renders (on the raw cubes; the
+    oracle's cost per sample does not depend on the values) and the smoothing of a
+    z-slab of both cubes; each part is scaled to the full step by its share of the work.
+    Returns (Gsamples/s of the whole step, description, cores)."""
+    import oracle
+    cube, cube2 = make_inputs()
+    cubed, cube2d = cube.astype(np.float64), cube2.astype(np.float64)
+    cam = WL.survey_camera()
+    npix = cam.width * cam.height
+    tot, per_ray = oracle.count_samples(WL.SURVEY["dims"], cam, step=WL.SURVEY["step"])
+    rng = np.random.default_rng(0)
+    # calibrate: a small pixel subset first
+    frac = 1.0 / 4096
+    t_render = 0.0
+    for it in range(3):
+        npx = max(64, int(npix * frac))
+        pix = rng.choice(npix, size=npx, replace=False)
+        t = time.time()
+        for m in WL.MODES:
+            kw = dict(WL.MODE_PARAMS[m])
+            lut = scene.ratio_lut() if m == "ratio" else scene.linear_lut()
+            oracle.render(cubed, cam, m, lut=lut, cube2=cube2d if m == "ratio" else None, pixels=pix,
+                          step=WL.SURVEY["step"], **kw)
+        dt = time.time() - t
+        t_render = dt / frac
+        if dt > 0.5 * budget_s or it == 2:
+            break
+        frac = min(0.25, frac * max(2.0, 0.6 * budget_s / max(dt, 1e-3)))
+    nz_s = 16
+    t = time.time()
+    w = oracle.gauss_weights(WL.SURVEY["sigma"], WL.SURVEY["radius"])
+    oracle.smooth(cubed[:nz_s], w)
+    oracle.smooth(cube2d[:nz_s], w)
+    t_smooth = (time.time() - t) * cube.shape[0] / nz_s
+    samples_step = 5 * tot if samples_per_frame is None else sum(samples_per_frame.values())
+    step_s = t_render + t_smooth
+    desc = (f"FP64 oracle: {npx} random pixels of each of the 5 renders ({frac:.2e} of 1920x1080) and "
+            f"the smoothing of {nz_s} of 1024 z-planes of both cubes, each scaled to the full step")
+    return samples_step / step_s / 1e9, desc, step_s
+
+
+def omp_cores():
+    n = os.environ.get("OMP_NUM_THREADS")
+    return int(n) if n else os.cpu_count()
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    vals = []
+    desc = ""
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; every step is timed the same way
+    for k in range(args.steps):
+        v, desc, _ = oracle_sample(budget_s=max(2.0, 60.0 / max(args.steps, 1)))
+        vals.append(v)
+    v = statistics.median(vals)
+    cores = omp_cores()
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WL.SURVEY["name"]},
+        "cpu_baseline": {"value": round(v, 6), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="survey", choices=sorted(WORKLOADS),
+                    help="survey: the headline workload; survey-small: the same step on a smaller cube "
+                         "(profiler captures)")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        log("warning: fewer than 3 warm-up steps")
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    res, samples_per = run_ours(args)
+    if res is None:
+        return
+    if res["n_gpus"] == 1 and not args.no_cpu_baseline and args.workload == "survey":
+        v, desc, _ = oracle_sample(budget_s=15.0, samples_per_frame=samples_per)
+        res["cpu_baseline"] = {"value": round(v, 6), "unit": UNIT, "cores": omp_cores(), "kind": "oracle",
+                               "sample": desc}
+    print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

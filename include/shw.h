@@ -1,0 +1,175 @@
+/*
+ * shw.h -- C ABI of the GB300 spectral-cube ray caster (libshw.so).
+ *
+ * The library renders 3-D float spectral cubes (two spatial axes x, y and one
+ * spectral axis z) by per-pixel ray casting, as in "Real-time colouring and
+ * filtering with graphics shaders" (Vohl et al. 2017): every ray takes samples
+ * at a fixed step (Algorithm 1) and folds them with one transfer function --
+ * maximum intensity (Eq. 1, Algorithm 2), average (Eq. 3), front-to-back alpha
+ * compositing through an RGBA colour map (Eq. 2, Algorithm 3), spectral-position
+ * colouring (Algorithm 4) or the per-sample ratio of two cubes (Algorithm 14) --
+ * and smooths cubes with a separable 3-D Gaussian (Eqs. 5-6, Algorithm 9).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Cube layout: C-contiguous float32 [nz][ny][nx], x fastest, z = spectral.
+ *   Voxel (i, j, k) sits at the point (i, j, k) of index space; the cube's box
+ *   is [-0.5, n-0.5] on each axis; reads outside clamp to the nearest edge voxel.
+ * - Rays: pixel (px, py) of a W x H image (row 0 at the top) has screen
+ *   coordinates xs = 2(px+1/2)/W - 1, ys = 1 - 2(py+1/2)/H (Appendix A).
+ *   Parallel projection: origin eye + xs*ortho_half_h*(W/H)*right + ys*ortho_half_h*up,
+ *   direction fwd/|fwd|.  Perspective: origin eye, direction
+ *   normalize(fwd + xs*tan_half_fovy*(W/H)*right + ys*tan_half_fovy*up).
+ *   The ray is clipped to the box and to t >= 0 giving [t0, t1]; it takes
+ *   N = floor((t1 - t0)/step) samples at t0 + (k + 1/2)*step, k = 0..N-1.
+ * - Normalisation: v_hat = clamp((v - lo)/(hi - lo), 0, 1); the colour map is
+ *   256 RGBA knots interpolated linearly at u = 255*v_hat.  A sample that is NaN
+ *   counts as DATAMIN = lo.
+ * - Pointers named *device* are CUDA device (or managed) memory owned by the
+ *   caller; the library never frees them and keeps none after a call returns
+ *   (a batch plan excepted, see shw_batch_plan_create).  Pointers named *host*
+ *   are read during the call only.
+ * - Every launch is asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *   default stream).  A call returns SHW_OK once its work is enqueued, or an
+ *   error before enqueuing anything.  Device-side faults of the CUDA runtime
+ *   surface as SHW_ECUDA from a later call or from shw_sync_status.
+ * - No call falls back to a CPU implementation.
+ */
+#ifndef SHW_H
+#define SHW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SHW_ABI_VERSION 1
+#define SHW_LUT_SIZE 256
+#define SHW_MAX_SMOOTH_RADIUS 16
+#define SHW_BRICK 32        /* brick edge of the reduced-precision storage, voxels */
+#define SHW_BRICK_APRON 1   /* replicated border kept around every brick, voxels */
+
+typedef enum {
+    SHW_OK = 0,
+    SHW_EINVAL = 1,        /* a NULL pointer, a non-positive size, an unknown enum ... */
+    SHW_EUNSUPPORTED = 2,  /* a valid request this build does not handle (size limits) */
+    SHW_ECUDA = 3,         /* the CUDA runtime reported an error */
+    SHW_ENOMEM = 4,        /* a caller buffer is too small, or a plan allocation failed */
+    SHW_ETIMEOUT = 5,      /* reserved: no kernel of this library waits on another */
+    SHW_EDEVICE = 6        /* no usable CUDA device */
+} shw_status;
+
+typedef enum {
+    SHW_MIP = 0,        /* Eq. 1 / Algorithm 2: running maximum, ">=" (the last maximum wins) */
+    SHW_AVG = 1,        /* Eq. 3: mean of the samples (zeroth moment / N on a spectral-axis view) */
+    SHW_COMPOSITE = 2,  /* Eq. 2 / Algorithm 3: front-to-back compositing through the colour map */
+    SHW_SPECTRAL = 3,   /* Algorithm 4: colour from the spectral position of the maximum */
+    SHW_RATIO = 4       /* Algorithm 14: per-sample cube2/cube1, then maximum */
+} shw_mode;
+
+typedef enum { SHW_NEAREST = 0, SHW_TRILINEAR = 1 } shw_interp;
+
+typedef enum {
+    SHW_F32 = 0,        /* linear float32 [nz][ny][nx] */
+    SHW_BF16_BRICK = 1, /* bricks written by shw_pack_bricks, bfloat16 */
+    SHW_F16_BRICK = 2   /* bricks written by shw_pack_bricks, IEEE binary16 */
+} shw_storage;
+
+/* A cube.  data: device.  For SHW_F32 it is the linear float32 array; for the
+ * brick storages it is the buffer filled by shw_pack_bricks for the same dims. */
+typedef struct {
+    const void *data;
+    int32_t nx, ny, nz;
+    int32_t storage; /* shw_storage */
+} shw_volume;
+
+/* A camera in index space (Appendix A).  right, up and fwd should be unit and
+ * mutually orthogonal; fwd is normalised by the library for parallel rays. */
+typedef struct {
+    float eye[3], right[3], up[3], fwd[3];
+    float tan_half_fovy; /* perspective: tan of half the vertical field of view */
+    float ortho_half_h;  /* parallel: half height of the view window, voxels */
+    int32_t ortho;       /* 1 = parallel projection, 0 = perspective */
+    int32_t width, height;
+} shw_camera;
+
+typedef struct {
+    int32_t mode;          /* shw_mode */
+    int32_t interp;        /* shw_interp */
+    float step;            /* sample spacing along the ray, voxels, > 0 */
+    float lo, hi;          /* colour-map domain; lo is also DATAMIN; hi > lo */
+    const float *lut;      /* device, [256][4] RGBA float32 */
+    float opacity_scale;   /* COMPOSITE: a = clamp(opacity_scale * A_lut(v_hat), 0, 1) (k of Algorithm 3) */
+    float term_alpha;      /* COMPOSITE: stop after the sample that makes alpha > term_alpha (0.99) */
+    float ratio_floor;     /* RATIO: a sample's ratio is cube2/cube1 where cube1 > ratio_floor, else DATAMIN */
+    int32_t ckpt_interval; /* COMPOSITE checkpoints for the adjoint: samples between checkpoints (64) */
+} shw_render_params;
+
+/* ---- library information (host only, no GPU needed) ---------------------- */
+
+int32_t shw_abi_version(void);
+const char *shw_status_string(int32_t status);
+/* sizeof of the ABI structs: which = 0 shw_volume, 1 shw_camera, 2 shw_render_params. */
+size_t shw_struct_size(int32_t which);
+/* Number of kernels this library has launched in this process (all devices). */
+uint64_t shw_launch_count(void);
+
+/* Wait for `stream` and report any error the CUDA runtime has latched. */
+shw_status shw_sync_status(void *stream);
+
+/* ---- smoothing (Section 4.2) ---------------------------------------------- */
+
+/* Separable 3-D Gaussian smoothing (Eq. 5 isotropic; Eq. 6 links sigma to the
+ * FWHM): out = in convolved with w (x) w (x) w, where
+ * w_k = exp(-k^2 / (2 sigma^2)) / sum_j exp(-j^2 / (2 sigma^2)), k = -radius..radius,
+ * clamp-to-edge boundary.  in, out: device float32 [nz][ny][nx], must not overlap.
+ * sigma > 0, 0 <= radius <= SHW_MAX_SMOOTH_RADIUS.  One kernel; no scratch memory. */
+shw_status shw_smooth(const float *in, float *out, int32_t nx, int32_t ny, int32_t nz,
+                      float sigma, int32_t radius, void *stream);
+
+/* The same with caller-given 1-D weights w_host[2*radius+1] (host; used as given,
+ * not renormalised), e.g. the binomial b_n filters of Section 4.2. */
+shw_status shw_smooth_weights(const float *in, float *out, int32_t nx, int32_t ny, int32_t nz,
+                              const float *w_host, int32_t radius, void *stream);
+
+/* ---- reduced-precision brick storage -------------------------------------- */
+
+/* Bytes of the brick buffer for a cube of these dims: ceil(n/32) bricks per axis,
+ * each (32+2)^3 elements of 2 bytes (a 1-voxel apron on every face).
+ * Returns 0 for invalid arguments. */
+size_t shw_bricked_bytes(int32_t nx, int32_t ny, int32_t nz, int32_t storage);
+
+/* Pack a float32 cube into bricks, rounding to nearest even.  Brick (bx, by, bz)
+ * starts at element ((bz*nby + by)*nbx + bx) * 34^3 and stores, at
+ * ((lz*34 + ly)*34 + lx), the voxel (32 bx + lx - 1, 32 by + ly - 1, 32 bz + lz - 1)
+ * clamped to the cube.  in: device float32; out: device, out_bytes >= shw_bricked_bytes. */
+shw_status shw_pack_bricks(const float *in, int32_t nx, int32_t ny, int32_t nz, int32_t storage,
+                           void *out, size_t out_bytes, void *stream);
+
+/* ---- rendering (Sections 2-4) -------------------------------------------- */
+
+/* Render one image.  vol2: the second cube for SHW_RATIO (same dims and storage),
+ * else NULL.  Outputs (device, any may be NULL except out_rgba):
+ *   out_rgba   [H][W][4] float32: MIP/AVG/RATIO: colourMap(v_hat(result));
+ *              SPECTRAL: (colourMap_rgb(t_z), v_hat(max)), t_z = (z_max + 1/2)/nz;
+ *              COMPOSITE: premultiplied (C_r, C_g, C_b, 1 - T).
+ *   out_scalar [H][W] float32: the maximum / mean / ratio maximum / 1 - T.
+ *   out_index  [H][W] int32: channel round(z) of the maximum (MIP, SPECTRAL, RATIO); -1 otherwise.
+ *   out_nsamples [H][W] int32: samples the ray processed.
+ * A ray that misses the box (or has N = 0) writes zeros and index -1.
+ * ckpt: COMPOSITE only, device buffer of ckpt_bytes >= shw_ckpt_bytes(...), or NULL:
+ * the transmittance every ckpt_interval samples, read by shw_render_backward. */
+shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_camera *cam,
+                      const shw_render_params *p, float *out_rgba, float *out_scalar,
+                      int32_t *out_index, int32_t *out_nsamples, void *ckpt, size_t ckpt_bytes,
+                      void *stream);
+
+/* Size of the checkpoint buffer for a COMPOSITE render of this volume/camera. */
+size_t shw_ckpt_bytes(const shw_volume *vol, const shw_camera *cam, const shw_render_params *p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SHW_H */

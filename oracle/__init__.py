@@ -50,7 +50,7 @@ def lib():
             L.oracle_render.argtypes = [dp, dp, C.c_int, C.c_int, C.c_int, dp, C.c_int, C.c_int, C.c_int,
                                         C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, dp,
                                         C.c_double, C.c_double, C.c_double, lp, C.c_long, C.c_double,
-                                        C.c_double, dp, dp, ip, ip, ucp]
+                                        C.c_double, C.c_double, dp, dp, ip, ip, ucp]
             L.oracle_count_samples.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_int, C.c_int, C.c_int,
                                                C.c_double, ip]
             L.oracle_count_samples.restype = C.c_longlong
@@ -85,11 +85,16 @@ def _cam_args(cam):
 
 def render(cube, cam, mode, *, interp="trilinear", step=0.5, lo=-3.0, hi=8.0, lut=None,
            opacity_scale=1.0, term_alpha=0.99, ratio_floor=0.0, cube2=None, pixels=None,
-           eps_pos=0.0, eps_val=0.0):
+           eps_pos=0.0, eps_val=0.0, eps_exit=None):
     """Render with the FP64 oracle.  Returns dict(rgba, scalar, index, nsamples, fragile).
 
     ``pixels``: optional array of row-major pixel ids; outputs then follow that list.
+    ``eps_pos`` / ``eps_val`` / ``eps_exit``: margins (voxels / values / opacity) within which a
+    discrete decision of a ray is reported as fragile (diagnostic only).  eps_exit defaults to
+    eps_val / 50.
     """
+    if eps_exit is None:
+        eps_exit = eps_val / 50.0
     L = lib()
     nz, ny, nx = cube.shape
     cubed = _d(cube)
@@ -104,7 +109,7 @@ def render(cube, cam, mode, *, interp="trilinear", step=0.5, lo=-3.0, hi=8.0, lu
                          _ptr(c14, C.c_double), ortho, W, H, MODES[mode], INTERP[interp],
                          float(step), float(lo), float(hi), _ptr(lutd, C.c_double),
                          float(opacity_scale), float(term_alpha), float(ratio_floor),
-                         _ptr(pix, C.c_long), n, float(eps_pos), float(eps_val),
+                         _ptr(pix, C.c_long), n, float(eps_pos), float(eps_val), float(eps_exit),
                          _ptr(rgba, C.c_double), _ptr(scal, C.c_double), _ptr(idx, C.c_int),
                          _ptr(ns, C.c_int), _ptr(fr, C.c_ubyte))
     if rc != 0:

@@ -134,7 +134,9 @@ static int clip_ray(const int n[3], const double o[3], const double d[3], double
     if (!(tmax > t0))
         return 0;
     double q = (tmax - t0) / h;
-    if (frag && eps > 0.0 && dist_to_int(q) < eps && q >= 0.5)
+    /* an exactly integral quotient comes from exactly representable geometry
+     * (axis-aligned views), which every implementation evaluates exactly */
+    if (frag && eps > 0.0 && dist_to_int(q) < eps && dist_to_int(q) > 0.0 && q >= 0.5)
         *frag |= FRAG_COUNT;
     return (int)floor(q);
 }
@@ -204,7 +206,7 @@ static double normalise(double v, double lo, double hi)
 
 typedef struct {
     int mode, interp;
-    double h, lo, hi, s, term_alpha, ratio_floor, eps_pos, eps_val;
+    double h, lo, hi, s, term_alpha, ratio_floor, eps_pos, eps_val, eps_exit;
     const double *lut;
 } oparams;
 
@@ -258,6 +260,7 @@ static void render_ray(const ovol *V, const ovol *V2, const ocam *c, const opara
         zs = (double *)malloc(sizeof(double) * (size_t)N);
     }
     int done = 0;
+    double near_ratio = -INFINITY; /* largest value a near-threshold sample could take */
     for (int k = 0; k < N; ++k) {
         double t = t0 + (k + 0.5) * P->h;
         double p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
@@ -266,9 +269,13 @@ static void render_ray(const ovol *V, const ovol *V2, const ocam *c, const opara
             /* Algorithm 14: val = cube2/cube1 where cube1 > 0 (threshold f), else DATAMIN */
             double c1 = fetch(V, P->interp, p, P->eps_pos, frag);
             double c2 = fetch(V2, P->interp, p, P->eps_pos, frag);
-            if (frag && P->eps_val > 0.0 && fabs(c1 - P->ratio_floor) < P->eps_val)
-                *frag |= FRAG_RATIO;
             v = (c1 > P->ratio_floor) ? c2 / c1 : P->lo;
+            if (frag && P->eps_val > 0.0 && fabs(c1 - P->ratio_floor) < P->eps_val) {
+                double alt = (c1 > P->ratio_floor) ? P->lo : c2 / c1; /* the other branch */
+                double vv = isnan(v) ? P->lo : v, aa = isnan(alt) ? P->lo : alt;
+                double hi2 = vv > aa ? vv : aa;
+                if (hi2 > near_ratio) near_ratio = hi2;
+            }
         } else {
             v = fetch(V, P->interp, p, P->eps_pos, frag);
         }
@@ -302,7 +309,7 @@ static void render_ray(const ovol *V, const ovol *V2, const ocam *c, const opara
                 C[ch] += T * a * col[ch];
             T *= (1.0 - a);
             double A = 1.0 - T;
-            if (frag && P->eps_val > 0.0 && fabs(A - P->term_alpha) < P->eps_val)
+            if (frag && P->eps_exit > 0.0 && fabs(A - P->term_alpha) < P->eps_exit)
                 *frag |= FRAG_EXIT;
             if (A > P->term_alpha)
                 k = N; /* early ray termination */
@@ -343,11 +350,22 @@ static void render_ray(const ovol *V, const ovol *V2, const ocam *c, const opara
         *scalar = 1.0 - T;
         break;
     }
+    if (frag && P->mode == OR_RATIO && near_ratio >= m - P->eps_val)
+        *frag |= FRAG_RATIO;
     if (track) {
+        /* another sample within eps of the maximum: which one wins is a rounding
+         * decision.  It matters if it changes the channel (index) or, for spectral
+         * colouring, the z position that sets the hue. */
         int ch = channel_of(zmax, V->n[2]);
-        for (int k = 0; k < N; ++k)
-            if (vals[k] >= m - P->eps_val && channel_of(zs[k], V->n[2]) != ch)
+        for (int k = 0; k < N; ++k) {
+            /* exact ties (e.g. two DATAMIN samples, equal voxel values) are resolved
+             * identically by any implementation of ">="; only near ties are fragile */
+            if (!(vals[k] >= m - P->eps_val) || vals[k] == m)
+                continue;
+            int differs = (P->mode == OR_SPECTRAL) ? (zs[k] != zmax) : (channel_of(zs[k], V->n[2]) != ch);
+            if (differs)
                 *frag |= FRAG_TIE;
+        }
         free(vals);
         free(zs);
     }
@@ -359,7 +377,7 @@ int oracle_render(const double *cube, const double *cube2, int nx, int ny, int n
                   const double *cam14, int ortho, int W, int H,
                   int mode, int interp, double step, double lo, double hi,
                   const double *lut, double opacity_scale, double term_alpha, double ratio_floor,
-                  const long *pix, long npix, double eps_pos, double eps_val,
+                  const long *pix, long npix, double eps_pos, double eps_val, double eps_exit,
                   double *out_rgba, double *out_scalar, int *out_index, int *out_nsamples,
                   unsigned char *out_fragile)
 {
@@ -369,7 +387,7 @@ int oracle_render(const double *cube, const double *cube2, int nx, int ny, int n
         return 1;
     ovol V = {cube, {nx, ny, nz}}, V2 = {cube2, {nx, ny, nz}};
     ocam c = make_cam(cam14, ortho, W, H);
-    oparams P = {mode, interp, step, lo, hi, opacity_scale, term_alpha, ratio_floor, eps_pos, eps_val, lut};
+    oparams P = {mode, interp, step, lo, hi, opacity_scale, term_alpha, ratio_floor, eps_pos, eps_val, eps_exit, lut};
     long n = pix ? npix : (long)W * H;
 #pragma omp parallel for schedule(dynamic, 64)
     for (long q = 0; q < n; ++q) {

@@ -1,0 +1,17 @@
+"""GB300-native spectral-cube ray caster (Vohl et al. 2017, "Real-time colouring
+and filtering with graphics shaders"): a C-ABI CUDA library (libshw.so, sm_103a)
+with this thin PyTorch binding.  See include/shw.h for the contract of each call.
+"""
+from .api import (  # noqa: F401
+    BrickVolume,
+    ShwError,
+    bricked_bytes,
+    ckpt_bytes,
+    launch_count,
+    pack_bricks,
+    render,
+    smooth,
+    smooth_weights,
+    sync_status,
+)
+from ._lib import LIB_PATH, MODES, INTERP, STORAGE  # noqa: F401

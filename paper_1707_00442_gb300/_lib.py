@@ -1,0 +1,98 @@
+"""ctypes view of libshw.so (the C ABI declared in include/shw.h).
+
+Argument marshalling only: every computation happens in the library's CUDA
+kernels.  Loading fails loudly when the library has not been built; there is
+no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libshw.so")
+
+SHW_OK, SHW_EINVAL, SHW_EUNSUPPORTED, SHW_ECUDA, SHW_ENOMEM, SHW_ETIMEOUT, SHW_EDEVICE = range(7)
+MODES = {"mip": 0, "avg": 1, "composite": 2, "spectral": 3, "ratio": 4}
+INTERP = {"nearest": 0, "trilinear": 1}
+STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
+ABI_VERSION = 1
+LUT_SIZE = 256
+MAX_SMOOTH_RADIUS = 16
+BRICK = 32
+BRICK_STORED = 34
+
+
+class Volume(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("storage", C.c_int32)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("eye", C.c_float * 3), ("right", C.c_float * 3), ("up", C.c_float * 3), ("fwd", C.c_float * 3),
+                ("tan_half_fovy", C.c_float), ("ortho_half_h", C.c_float), ("ortho", C.c_int32),
+                ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class RenderParams(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("interp", C.c_int32), ("step", C.c_float), ("lo", C.c_float),
+                ("hi", C.c_float), ("lut", C.c_void_p), ("opacity_scale", C.c_float),
+                ("term_alpha", C.c_float), ("ratio_floor", C.c_float), ("ckpt_interval", C.c_int32)]
+
+
+class ShwError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = int(status)
+        msg = lib().shw_status_string(self.status).decode()
+        super().__init__(f"{what}: {msg} (status {self.status})" if what else msg)
+
+
+_lock = threading.Lock()
+_lib = None
+
+# name -> (restype, argtypes)
+_vp, _i32, _f, _sz = C.c_void_p, C.c_int32, C.c_float, C.c_size_t
+_P = C.POINTER
+SIGNATURES = {
+    "shw_abi_version": (_i32, []),
+    "shw_status_string": (C.c_char_p, [_i32]),
+    "shw_struct_size": (_sz, [_i32]),
+    "shw_launch_count": (C.c_uint64, []),
+    "shw_sync_status": (_i32, [_vp]),
+    "shw_smooth": (_i32, [_vp, _vp, _i32, _i32, _i32, _f, _i32, _vp]),
+    "shw_smooth_weights": (_i32, [_vp, _vp, _i32, _i32, _i32, _P(C.c_float), _i32, _vp]),
+    "shw_bricked_bytes": (_sz, [_i32, _i32, _i32, _i32]),
+    "shw_pack_bricks": (_i32, [_vp, _i32, _i32, _i32, _i32, _vp, _sz, _vp]),
+    "shw_render": (_i32, [_P(Volume), _P(Volume), _P(Camera), _P(RenderParams), _vp, _vp, _vp, _vp, _vp, _sz,
+                          _vp]),
+    "shw_ckpt_bytes": (_sz, [_P(Volume), _P(Camera), _P(RenderParams)]),
+}
+
+
+def lib():
+    """The loaded library.  Raises if libshw.so is missing (build it with
+    ``python -m paper_1707_00442_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"{LIB_PATH} is not built: run `python -m paper_1707_00442_gb300.build` "
+                                  "(the CUDA library is required; there is no CPU fallback)")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            if L.shw_abi_version() != ABI_VERSION:
+                raise ImportError("libshw.so ABI version mismatch: rebuild it")
+            for which, st in enumerate((Volume, Camera, RenderParams)):
+                if L.shw_struct_size(which) != C.sizeof(st):
+                    raise ImportError(f"libshw.so struct layout mismatch for {st.__name__}")
+            _lib = L
+    return _lib
+
+
+def check(status: int, what: str = "") -> None:
+    if status != SHW_OK:
+        raise ShwError(status, what)

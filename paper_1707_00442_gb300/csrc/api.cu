@@ -1,0 +1,168 @@
+// api.cu -- the C ABI: argument validation, dispatch and status reporting.
+// Every check here runs on the host before anything is enqueued, so an invalid
+// call returns an error without touching the GPU.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "render_impl.cuh"
+
+namespace shw {
+
+static std::atomic<uint64_t> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static bool finite3(const float v[3]) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
+
+bool valid_volume(const shw_volume *v)
+{
+    if (!v || !v->data || v->nx <= 0 || v->ny <= 0 || v->nz <= 0) return false;
+    if (v->storage != SHW_F32 && v->storage != SHW_BF16_BRICK && v->storage != SHW_F16_BRICK) return false;
+    if (v->storage == SHW_F32 && !aligned(v->data, 4)) return false;
+    if (v->storage != SHW_F32 && !aligned(v->data, 2)) return false;
+    return true;
+}
+
+bool valid_camera(const shw_camera *c)
+{
+    if (!c || c->width <= 0 || c->height <= 0) return false;
+    if ((long long)c->width * c->height > (1LL << 31) - 1) return false;
+    if (c->width > (1 << 19) || c->height > (1 << 19)) return false;  // grid.y <= 65535 tiles
+    if (!finite3(c->eye) || !finite3(c->right) || !finite3(c->up) || !finite3(c->fwd)) return false;
+    const double nf = (double)c->fwd[0] * c->fwd[0] + (double)c->fwd[1] * c->fwd[1] + (double)c->fwd[2] * c->fwd[2];
+    if (!(nf > 0.0)) return false;
+    if (c->ortho) return std::isfinite(c->ortho_half_h) && c->ortho_half_h > 0.0f;
+    return std::isfinite(c->tan_half_fovy) && c->tan_half_fovy > 0.0f;
+}
+
+// Upper bound of N over all rays: a chord is at most the box diagonal.
+long long max_samples(const shw_volume *v, float step)
+{
+    const double diag = std::sqrt((double)v->nx * v->nx + (double)v->ny * v->ny + (double)v->nz * v->nz);
+    return (long long)std::floor(diag / (double)step) + 1;
+}
+
+bool valid_params(const shw_render_params *p, const shw_volume *v)
+{
+    if (!p || !p->lut || !aligned(p->lut, 16)) return false;
+    if (p->mode < SHW_MIP || p->mode > SHW_RATIO) return false;
+    if (p->interp != SHW_NEAREST && p->interp != SHW_TRILINEAR) return false;
+    if (!std::isfinite(p->step) || !(p->step > 0.0f)) return false;
+    if (!std::isfinite(p->lo) || !std::isfinite(p->hi) || !(p->hi > p->lo)) return false;
+    if (!std::isfinite(1.0f / (p->hi - p->lo))) return false;
+    if (!std::isfinite(p->opacity_scale) || !std::isfinite(p->term_alpha) || !std::isfinite(p->ratio_floor))
+        return false;
+    if (max_samples(v, p->step) > (1LL << 30)) return false;
+    return true;
+}
+
+long long ckpt_count(const shw_volume *v, const shw_render_params *p)
+{
+    const long long nmax = max_samples(v, p->step);
+    return (nmax + p->ckpt_interval - 1) / p->ckpt_interval;
+}
+
+}  // namespace shw
+
+using namespace shw;
+
+extern "C" {
+
+int32_t shw_abi_version(void) { return SHW_ABI_VERSION; }
+
+const char *shw_status_string(int32_t s)
+{
+    switch (s) {
+    case SHW_OK: return "ok";
+    case SHW_EINVAL: return "invalid argument";
+    case SHW_EUNSUPPORTED: return "unsupported request";
+    case SHW_ECUDA: return "CUDA runtime error";
+    case SHW_ENOMEM: return "buffer too small or out of memory";
+    case SHW_ETIMEOUT: return "timed out";
+    case SHW_EDEVICE: return "no usable CUDA device";
+    default: return "unknown status";
+    }
+}
+
+size_t shw_struct_size(int32_t which)
+{
+    switch (which) {
+    case 0: return sizeof(shw_volume);
+    case 1: return sizeof(shw_camera);
+    case 2: return sizeof(shw_render_params);
+    default: return 0;
+    }
+}
+
+uint64_t shw_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+shw_status shw_sync_status(void *stream)
+{
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return SHW_EDEVICE;
+    }
+    cudaError_t e = cudaStreamSynchronize(as_stream(stream));
+    if (e != cudaSuccess) return SHW_ECUDA;
+    return cudaGetLastError() == cudaSuccess ? SHW_OK : SHW_ECUDA;
+}
+
+size_t shw_ckpt_bytes(const shw_volume *vol, const shw_camera *cam, const shw_render_params *p)
+{
+    if (!valid_volume(vol) || !valid_camera(cam) || !p || !(p->step > 0.0f) || p->ckpt_interval <= 0) return 0;
+    const long long npix = (long long)cam->width * cam->height;
+    return (size_t)(npix * 4 + ckpt_count(vol, p) * npix * 4);
+}
+
+shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_camera *cam,
+                      const shw_render_params *p, float *out_rgba, float *out_scalar, int32_t *out_index,
+                      int32_t *out_nsamples, void *ckpt, size_t ckpt_bytes, void *stream)
+{
+    if (!valid_volume(vol) || !valid_camera(cam) || !valid_params(p, vol)) return SHW_EINVAL;
+    if (!out_rgba || !aligned(out_rgba, 16)) return SHW_EINVAL;
+    if ((out_scalar && !aligned(out_scalar, 4)) || (out_index && !aligned(out_index, 4)) ||
+        (out_nsamples && !aligned(out_nsamples, 4)))
+        return SHW_EINVAL;
+    if (p->mode == SHW_RATIO) {
+        if (!valid_volume(vol2) || vol2->nx != vol->nx || vol2->ny != vol->ny || vol2->nz != vol->nz ||
+            vol2->storage != vol->storage)
+            return SHW_EINVAL;
+    }
+    const long long npix = (long long)cam->width * cam->height;
+    RenderArgs a{};
+    a.rgba = reinterpret_cast<float4 *>(out_rgba);
+    a.scalar = out_scalar;
+    a.index = out_index;
+    a.nsamples = out_nsamples;
+    a.lut = reinterpret_cast<const float4 *>(p->lut);
+    a.width = cam->width;
+    a.height = cam->height;
+    a.step = p->step;
+    a.lo = p->lo;
+    a.inv_range = 1.0f / (p->hi - p->lo);
+    a.opacity_scale = p->opacity_scale;
+    a.term_alpha = p->term_alpha;
+    a.ratio_floor = p->ratio_floor;
+    a.nz = vol->nz;
+    a.nmax = (int)max_samples(vol, p->step);
+    a.ckpt_interval = p->ckpt_interval > 0 ? p->ckpt_interval : 64;
+    if (ckpt) {
+        if (p->mode != SHW_COMPOSITE || p->ckpt_interval <= 0 || !aligned(ckpt, 4)) return SHW_EINVAL;
+        if (ckpt_bytes < shw_ckpt_bytes(vol, cam, p)) return SHW_ENOMEM;
+        a.ckpt_K = static_cast<int *>(ckpt);
+        a.ckpt_T = reinterpret_cast<float *>(static_cast<char *>(ckpt) + npix * 4);
+        a.nckpt = (int)ckpt_count(vol, p);
+    }
+    const shw_volume *v2 = (p->mode == SHW_RATIO) ? vol2 : nullptr;
+    cudaStream_t st = as_stream(stream);
+    switch (vol->storage) {
+    case SHW_F32: return render_f32(p->mode, p->interp, *vol, v2, *cam, a, st);
+    case SHW_BF16_BRICK: return render_bf16(p->mode, p->interp, *vol, v2, *cam, a, st);
+    case SHW_F16_BRICK: return render_f16(p->mode, p->interp, *vol, v2, *cam, a, st);
+    default: return SHW_EINVAL;
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,81 @@
+// bricks.cu -- float32 cube -> 32^3 bricks of bfloat16 / binary16 with a 1-voxel
+// replicated apron (34^3 stored per brick), rounding to nearest even.
+//
+// The apron holds copies of the neighbouring bricks' border voxels (clamped at
+// the cube's faces), so that all 8 corners of any interpolation cell are in one
+// brick at fixed offsets, and the marcher needs no edge clamping of corners.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+
+namespace shw {
+
+template <typename T>
+__device__ __forceinline__ unsigned short round_store(float v);
+template <>
+__device__ __forceinline__ unsigned short round_store<__nv_bfloat16>(float v)
+{
+    return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+template <>
+__device__ __forceinline__ unsigned short round_store<__half>(float v)
+{
+    return __half_as_ushort(__float2half_rn(v));
+}
+
+// One thread per stored element; consecutive threads walk lx, so reads of a
+// brick row are contiguous in x and writes are contiguous.
+template <typename T>
+__global__ void __launch_bounds__(256) pack_kernel(const float *__restrict__ in, unsigned short *__restrict__ out,
+                                                   int nx, int ny, int nz, int nbx, int nby, long long total)
+{
+    constexpr int S = kBrickStored;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long brick = i / kBrickElems;
+        const int e = (int)(i - brick * kBrickElems);
+        const int lz = e / (S * S), ly = (e / S) % S, lx = e % S;
+        const int bx = (int)(brick % nbx), by = (int)((brick / nbx) % nby), bz = (int)(brick / ((long long)nbx * nby));
+        const int x = min(max(bx * kBrick + lx - 1, 0), nx - 1);
+        const int y = min(max(by * kBrick + ly - 1, 0), ny - 1);
+        const int z = min(max(bz * kBrick + lz - 1, 0), nz - 1);
+        out[i] = round_store<T>(__ldg(in + ((size_t)z * ny + y) * nx + x));
+    }
+}
+
+}  // namespace shw
+
+using namespace shw;
+
+extern "C" {
+
+size_t shw_bricked_bytes(int32_t nx, int32_t ny, int32_t nz, int32_t storage)
+{
+    if (nx <= 0 || ny <= 0 || nz <= 0) return 0;
+    if (storage != SHW_BF16_BRICK && storage != SHW_F16_BRICK) return 0;
+    const size_t nb = (size_t)ceil_div(nx, kBrick) * ceil_div(ny, kBrick) * ceil_div(nz, kBrick);
+    return nb * kBrickElems * 2;
+}
+
+shw_status shw_pack_bricks(const float *in, int32_t nx, int32_t ny, int32_t nz, int32_t storage, void *out,
+                           size_t out_bytes, void *stream)
+{
+    if (!in || !out || nx <= 0 || ny <= 0 || nz <= 0 || !aligned(in, 4) || !aligned(out, 2)) return SHW_EINVAL;
+    if (storage != SHW_BF16_BRICK && storage != SHW_F16_BRICK) return SHW_EINVAL;
+    const size_t need = shw_bricked_bytes(nx, ny, nz, storage);
+    if (out_bytes < need) return SHW_ENOMEM;
+    const long long total = (long long)(need / 2);
+    const int nbx = ceil_div(nx, kBrick), nby = ceil_div(ny, kBrick);
+    long long blocks = (total + 255) / 256;
+    if (blocks > 152LL * 64) blocks = 152LL * 64;  // grid-stride beyond 64 CTAs per SM
+    cudaStream_t st = as_stream(stream);
+    auto *o = static_cast<unsigned short *>(out);
+    if (storage == SHW_BF16_BRICK)
+        pack_kernel<__nv_bfloat16><<<(unsigned)blocks, 256, 0, st>>>(in, o, nx, ny, nz, nbx, nby, total);
+    else
+        pack_kernel<__half><<<(unsigned)blocks, 256, 0, st>>>(in, o, nx, ny, nz, nbx, nby, total);
+    return after_launch();
+}
+
+}  // extern "C"

@@ -1,0 +1,16 @@
+// render_f16.cu -- marcher instances for the f16 brick storage (32^3 bricks + apron).
+#include "render_impl.cuh"
+
+namespace shw {
+
+shw_status render_f16(int mode, int interp, const shw_volume &v, const shw_volume *v2, const shw_camera &cam,
+                      const RenderArgs &a, cudaStream_t st)
+{
+    SamplerBrick<__half> s{static_cast<const unsigned short *>(v.data), v.nx, v.ny, v.nz,
+                       ceil_div(v.nx, kBrick), ceil_div(v.ny, kBrick)};
+    SamplerBrick<__half> s2 = s;
+    if (v2) s2.v = static_cast<const unsigned short *>(v2->data);
+    return launch_render_modes(mode, interp, s, s2, cam, a, st);
+}
+
+}  // namespace shw

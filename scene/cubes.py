@@ -72,10 +72,11 @@ def draw_sources(rng: np.random.Generator, dims, n: int, *, peak=(5.0, 5.0),
         else:
             smaj = rng.uniform(*sig_major)
         smin = smaj * rng.uniform(0.4, 1.0)
+        def pos(n):
+            lo, hi = margin * n, max(margin * n, (1 - margin) * n - 1)
+            return rng.uniform(lo, hi)
         out.append(Source(
-            x=rng.uniform(margin * nx, (1 - margin) * nx - 1),
-            y=rng.uniform(margin * ny, (1 - margin) * ny - 1),
-            z=rng.uniform(margin * nz, (1 - margin) * nz - 1),
+            x=pos(nx), y=pos(ny), z=pos(nz),
             peak=rng.uniform(*peak), sig_major=smaj, sig_minor=smin,
             pa=rng.uniform(0.0, math.pi), sig_z=sig_z, grad=rng.uniform(-0.5, 0.5)))
     return out

@@ -1,0 +1,149 @@
+"""The C ABI on the host: the library loads, exports every symbol include/*.h declares,
+its struct layouts match the binding, and invalid calls are rejected on the host
+before any GPU work (these tests need no GPU and make no compute call)."""
+import ctypes as C
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1707_00442_gb300 import build
+    build.build()
+    from paper_1707_00442_gb300 import _lib
+    return _lib.lib()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"\b(shw_[a-z0-9_]+)\s*\(", src):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 10
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_header(L):
+    from paper_1707_00442_gb300 import _lib
+    assert set(_lib.SIGNATURES) == set(declared_functions())
+
+
+def test_struct_layout(L):
+    from paper_1707_00442_gb300 import _lib
+    assert L.shw_struct_size(0) == C.sizeof(_lib.Volume) == 24
+    assert L.shw_struct_size(1) == C.sizeof(_lib.Camera) == 68
+    assert L.shw_struct_size(2) == C.sizeof(_lib.RenderParams) == 48
+    assert L.shw_struct_size(9) == 0
+    assert L.shw_abi_version() == 1
+
+
+def test_status_strings(L):
+    for s in range(7):
+        assert L.shw_status_string(s)
+    assert L.shw_status_string(99) == b"unknown status"
+
+
+def _vol(data=0x1000, n=(8, 8, 8), storage=0):
+    from paper_1707_00442_gb300 import _lib
+    return _lib.Volume(data, *n, storage)
+
+
+def _cam(W=16, H=16, ortho=1):
+    from paper_1707_00442_gb300 import _lib
+    c = _lib.Camera()
+    c.eye[:] = [3.5, 3.5, -8]
+    c.right[:] = [1, 0, 0]
+    c.up[:] = [0, 1, 0]
+    c.fwd[:] = [0, 0, 1]
+    c.tan_half_fovy, c.ortho_half_h, c.ortho, c.width, c.height = 0.4, 4.0, ortho, W, H
+    return c
+
+
+def _params(mode=0, step=0.5, lut=0x2000, lo=-3.0, hi=8.0):
+    from paper_1707_00442_gb300 import _lib
+    return _lib.RenderParams(mode, 1, step, lo, hi, lut, 1.0, 0.99, 0.0, 64)
+
+
+def test_render_rejects_invalid_arguments_on_host(L):
+    """Every case must fail validation (EINVAL) before the library touches a device."""
+    EINVAL = 1
+    out = 0x4000
+    ok_v, ok_c, ok_p = _vol(), _cam(), _params()
+    b = C.byref
+    cases = [
+        (None, ok_c, ok_p, out),
+        (_vol(data=0), ok_c, ok_p, out),
+        (_vol(n=(0, 8, 8)), ok_c, ok_p, out),
+        (_vol(storage=7), ok_c, ok_p, out),
+        (_vol(data=0x1001), ok_c, ok_p, out),       # misaligned float32 cube
+        (ok_v, _cam(W=0), ok_p, out),
+        (ok_v, _cam(H=-3), ok_p, out),
+        (ok_v, ok_c, _params(mode=9), out),
+        (ok_v, ok_c, _params(step=0.0), out),
+        (ok_v, ok_c, _params(step=-1.0), out),
+        (ok_v, ok_c, _params(step=float("nan")), out),
+        (ok_v, ok_c, _params(lut=0), out),
+        (ok_v, ok_c, _params(lut=0x2004), out),      # colour map not 16-byte aligned
+        (ok_v, ok_c, _params(lo=1.0, hi=1.0), out),
+        (ok_v, ok_c, _params(mode=4), out),          # RATIO without a second cube
+        (ok_v, ok_c, ok_p, 0),                       # no rgba output
+        (ok_v, ok_c, ok_p, 0x4008),                  # rgba not 16-byte aligned
+    ]
+    for v, c, p, o in cases:
+        st = L.shw_render(b(v) if v is not None else None, None, b(c), b(p), o, None, None, None, None, 0, None)
+        assert st == EINVAL, (v, p)
+    # ratio with mismatched second cube
+    v2 = _vol(n=(8, 8, 9))
+    assert L.shw_render(b(ok_v), b(v2), b(ok_c), b(_params(mode=4)), out, None, None, None, None, 0, None) == EINVAL
+    # checkpoints only for compositing, and big enough
+    assert L.shw_render(b(ok_v), None, b(ok_c), b(ok_p), out, None, None, None, 0x8000, 1 << 30, None) == EINVAL
+    p2 = _params(mode=2)
+    need = L.shw_ckpt_bytes(b(ok_v), b(ok_c), b(p2))
+    assert need == 16 * 16 * 4 * (1 + -(-(int((8 * 8 * 3) ** 0.5 / 0.5) + 1) // 64))
+    assert L.shw_render(b(ok_v), None, b(ok_c), b(p2), out, None, None, None, 0x8000, need - 4, None) == 4  # ENOMEM
+
+
+def test_smooth_and_pack_reject_invalid_arguments_on_host(L):
+    EINVAL, EUNSUP, ENOMEM = 1, 2, 4
+    assert L.shw_smooth(0, 0x1000, 8, 8, 8, 1.0, 3, None) == EINVAL
+    assert L.shw_smooth(0x1000, 0x1000, 8, 8, 8, 1.0, 3, None) == EINVAL            # in place
+    assert L.shw_smooth(0x1000, 0x1000 + 100, 8, 8, 8, 1.0, 3, None) == EINVAL      # overlapping
+    assert L.shw_smooth(0x1000, 0x100000, 8, 8, 8, 0.0, 3, None) == EINVAL          # sigma
+    assert L.shw_smooth(0x1000, 0x100000, 8, 8, 8, 1.0, -1, None) == EINVAL
+    assert L.shw_smooth(0x1000, 0x100000, 8, 8, 8, 1.0, 17, None) == EUNSUP
+    assert L.shw_smooth(0x1000, 0x100000, 8, 0, 8, 1.0, 3, None) == EINVAL
+    assert L.shw_smooth_weights(0x1000, 0x100000, 8, 8, 8, None, 3, None) == EINVAL
+    assert L.shw_bricked_bytes(64, 64, 64, 1) == 8 * 34 ** 3 * 2
+    assert L.shw_bricked_bytes(65, 64, 64, 2) == 12 * 34 ** 3 * 2
+    assert L.shw_bricked_bytes(64, 64, 64, 0) == 0
+    assert L.shw_pack_bricks(0x1000, 64, 64, 64, 0, 0x100000, 1 << 30, None) == EINVAL
+    assert L.shw_pack_bricks(0x1000, 64, 64, 64, 1, 0x100000, 1000, None) == ENOMEM
+
+
+def test_no_device_is_reported(L):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    assert L.shw_sync_status(None) == 6  # SHW_EDEVICE
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_1707_00442_gb300 import _lib
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "libshw.so"))
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(ImportError):
+        _lib.lib()

@@ -1,0 +1,87 @@
+"""Parity at the full survey size (512 x 512 x 1024 float32 cube, 1920 x 1080 perspective,
+the benchmark's launch configuration): every mode on sampled pixels the oracle computes
+one by one, the smoothing on sampled voxels (direct triple sum), and the moment-map
+view's nearest MIP bit-exact over the whole image."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import scene
+from parity import TOL_F32, compare, shw, to_dev
+from scene import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def m():
+    return shw()
+
+
+@pytest.fixture(scope="module")
+def survey():
+    cube = scene.survey_cube()
+    c2 = scene.ratio_cube(cube)
+    return cube, c2, cube.astype(np.float64), c2.astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def pixels():
+    cam = W.survey_camera()
+    rng = np.random.default_rng(123)
+    n = cam.width * cam.height
+    corners = [0, cam.width - 1, n - cam.width, n - 1]
+    return np.concatenate([rng.choice(n, size=1500, replace=False), corners]).astype(np.int64)
+
+
+@pytest.mark.parametrize("mode", W.MODES)
+def test_survey_render_sampled(m, survey, pixels, mode):
+    cube, c2, cubed, c2d = survey
+    cam = W.survey_camera()
+    lut = scene.ratio_lut() if mode == "ratio" else scene.linear_lut()
+    kw = dict(W.MODE_PARAMS[mode])
+    out = m.render(to_dev(cube), cam, mode, lut=to_dev(lut), vol2=to_dev(c2) if mode == "ratio" else None,
+                   step=W.SURVEY["step"], **kw)
+    m.sync_status()
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    o = oracle.render(cubed, cam, mode, lut=lut, cube2=c2d if mode == "ratio" else None, pixels=pixels,
+                      step=W.SURVEY["step"], eps_pos=1e-6, eps_val=1e-4, **kw)
+    if mode == "ratio":
+        scale = float(o["scalar"].max() - o["scalar"].min()) or 1.0
+    elif mode == "composite":
+        scale = 1.0
+    else:
+        scale = float(cube.max() - cube.min())
+    st = compare(g, o, mode, scale=scale, pixels=pixels, what=f"survey/{mode}")
+    assert (o["nsamples"] > 0).mean() > 0.15
+    print(mode, st)
+
+
+def test_survey_moment_map_view_bit_exact(m, survey):
+    """Parallel rays down the spectral axis at 512^2, nearest: MIP == max over z for every pixel."""
+    cube = survey[0]
+    cam = W.survey_ortho_camera()
+    out = m.render(to_dev(cube), cam, "spectral", lut=to_dev(scene.linear_lut()), interp="nearest")
+    m.sync_status()
+    g = out["scalar"].cpu().numpy()
+    ref = cube.max(axis=0)[::-1]
+    assert np.array_equal(g, ref)
+    last = (cube.shape[0] - 1 - np.argmax(cube[::-1], axis=0))[::-1]
+    assert np.array_equal(out["index"].cpu().numpy(), last)
+
+
+def test_survey_smooth_sampled(m, survey):
+    cube = survey[0]
+    sig, r = W.SURVEY["sigma"], W.SURVEY["radius"]
+    g = m.smooth(to_dev(cube), sig, r)
+    m.sync_status()
+    nz, ny, nx = cube.shape
+    rng = np.random.default_rng(7)
+    ids = rng.choice(cube.size, size=3000, replace=False)
+    # faces, edges and corners (clamp-to-edge)
+    zz, yy, xx = np.meshgrid([0, 1, 5, nz - 6, nz - 1], [0, 3, ny - 1], [0, 2, nx - 4, nx - 1], indexing="ij")
+    ids = np.concatenate([ids, ((zz * ny + yy) * nx + xx).ravel()])
+    o = oracle.smooth_points(survey[2], oracle.gauss_weights(sig, r), ids)
+    gv = g.reshape(-1)[torch.from_numpy(ids).cuda()].cpu().numpy()
+    assert np.abs(gv - o).max() <= TOL_F32 * float(cube.max() - cube.min())
