@@ -111,7 +111,8 @@ typedef struct {
 
 int32_t shw_abi_version(void);
 const char *shw_status_string(int32_t status);
-/* sizeof of the ABI structs: which = 0 shw_volume, 1 shw_camera, 2 shw_render_params. */
+/* sizeof of the ABI structs: which = 0 shw_volume, 1 shw_camera, 2 shw_render_params,
+ * 3 shw_batch_item, 4 shw_batch_info. */
 size_t shw_struct_size(int32_t which);
 /* Number of kernels this library has launched in this process (all devices). */
 uint64_t shw_launch_count(void);
@@ -168,6 +169,75 @@ shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_c
 
 /* Size of the checkpoint buffer for a COMPOSITE render of this volume/camera. */
 size_t shw_ckpt_bytes(const shw_volume *vol, const shw_camera *cam, const shw_render_params *p);
+
+/* ---- adjoint of compositing ----------------------------------------------- */
+
+/* Reverse-mode gradient of a COMPOSITE render (Eq. 2 / Algorithm 3 in premultiplied
+ * form) with respect to the voxels, the colour map and the opacity scale.
+ * vol, cam, p: exactly those of the forward shw_render call that filled `ckpt`
+ * (p->mode = SHW_COMPOSITE, 1 <= p->ckpt_interval <= 64; vol->storage = SHW_F32).
+ * grad_rgba: device [H][W][4] float32, dL/d(C_r, C_g, C_b, alpha) of the forward's out_rgba.
+ * Each segment of ckpt_interval samples is recomputed from its checkpoint, then
+ * reversed.  Gradients ACCUMULATE (+=) into the device buffers grad_vol
+ * [nz][ny][nx], grad_lut [256][4] and grad_scale [1]; any of them may be NULL.
+ * Accumulation uses atomics, so the low bits of the result may vary run to run.
+ * The early-exit sample of each ray is treated as fixed; at a clamp boundary the
+ * gradient passes (closed interval). */
+shw_status shw_render_backward(const shw_volume *vol, const shw_camera *cam, const shw_render_params *p,
+                               const float *grad_rgba, const void *ckpt, size_t ckpt_bytes, float *grad_vol,
+                               float *grad_lut, float *grad_scale, void *stream);
+
+/* ---- batched rendering of many sub-cubes ----------------------------------- */
+
+/* Survey pipelines cut a sub-cube around each of many detected sources (Section 1).
+ * A plan renders all of them with ONE persistent kernel launch captured in a CUDA
+ * graph: every (item, image tile) is a work item, CTAs pop work items from a device
+ * counter, tiles of the largest items first.  Each image is the same as shw_render
+ * of that item with the shared parameters.  */
+
+typedef struct shw_batch_plan shw_batch_plan; /* opaque */
+
+#define SHW_BATCH_NO_TUNE 1 /* skip the autotuner: 16 x 16 tiles, 4 CTAs per SM */
+#define SHW_BATCH_RETUNE 2  /* re-run the autotuner even if this batch signature is cached */
+
+typedef struct {
+    shw_volume vol;  /* the sub-cube: any storage, < 2^31 voxels */
+    shw_camera cam;  /* its view; its image is cam.width x cam.height */
+    float *out_rgba; /* device [H][W][4] float32, 16-byte aligned; written by every shw_render_batch */
+    int32_t mode;    /* SHW_MIP, SHW_AVG, SHW_COMPOSITE or SHW_SPECTRAL (SHW_RATIO: SHW_EUNSUPPORTED) */
+} shw_batch_item;
+
+typedef struct {
+    int32_t n_items, n_work;     /* items, work items (tiles) */
+    int32_t tile, ctas_per_sm;   /* the chosen tile edge (pixels) and persistent CTAs per SM */
+    int32_t grid, tuned;         /* CTAs launched; 1 if the autotuner ran for this plan */
+    int32_t n_candidates;
+    int32_t cand_tile[8], cand_ctas_per_sm[8];
+    float tune_ms[8];            /* measured time of each candidate (-1 when not tuned) */
+} shw_batch_info;
+
+/* Build a plan for n items sharing the parameters p (p->mode is ignored: each item
+ * has its own; interp, step, lo, hi, lut, opacity_scale, term_alpha are shared).
+ * Allocates device memory for the item table, the work list and the counter, and
+ * captures the launch into a CUDA graph.  Unless SHW_BATCH_NO_TUNE, the first plan
+ * of a batch signature (mean size class, image size, storages, modes) times every
+ * candidate configuration on `stream` -- rendering into the items' outputs -- and
+ * keeps the fastest; later plans of the same signature reuse the choice.
+ * The plan keeps the item pointers (cubes, outputs, colour map) until destroyed.
+ * Errors: SHW_EINVAL, SHW_EUNSUPPORTED, SHW_ENOMEM (allocation), SHW_ECUDA (capture),
+ * SHW_EDEVICE.  With the environment variable SHW_FAULT containing "alloc" or
+ * "graph", the allocation or the capture is made to fail (host-side fault injection). */
+shw_status shw_batch_plan_create(shw_batch_plan **plan, const shw_batch_item *items, int32_t n,
+                                 const shw_render_params *p, int32_t flags, void *stream);
+
+/* Render every item of the plan: one graph launch on `stream` (same device as the plan).
+ * Launches of one plan must not overlap: they share the plan's work counter. */
+shw_status shw_render_batch(shw_batch_plan *plan, void *stream);
+
+shw_status shw_batch_plan_info(const shw_batch_plan *plan, shw_batch_info *info);
+
+/* Waits for the device to finish outstanding work, then frees the plan. */
+shw_status shw_batch_plan_destroy(shw_batch_plan *plan);
 
 #ifdef __cplusplus
 }

@@ -3,6 +3,7 @@ and filtering with graphics shaders"): a C-ABI CUDA library (libshw.so, sm_103a)
 with this thin PyTorch binding.  See include/shw.h for the contract of each call.
 """
 from .api import (  # noqa: F401
+    BatchPlan,
     BrickVolume,
     ShwError,
     bricked_bytes,
@@ -10,8 +11,10 @@ from .api import (  # noqa: F401
     launch_count,
     pack_bricks,
     render,
+    render_backward,
     smooth,
     smooth_weights,
     sync_status,
 )
+from .autograd import composite_render  # noqa: F401
 from ._lib import LIB_PATH, MODES, INTERP, STORAGE  # noqa: F401

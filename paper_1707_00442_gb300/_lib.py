@@ -41,6 +41,19 @@ class RenderParams(C.Structure):
                 ("term_alpha", C.c_float), ("ratio_floor", C.c_float), ("ckpt_interval", C.c_int32)]
 
 
+class BatchItem(C.Structure):
+    _fields_ = [("vol", Volume), ("cam", Camera), ("out_rgba", C.c_void_p), ("mode", C.c_int32)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("n_items", C.c_int32), ("n_work", C.c_int32), ("tile", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("grid", C.c_int32), ("tuned", C.c_int32), ("n_candidates", C.c_int32),
+                ("cand_tile", C.c_int32 * 8), ("cand_ctas_per_sm", C.c_int32 * 8), ("tune_ms", C.c_float * 8)]
+
+
+BATCH_NO_TUNE, BATCH_RETUNE = 1, 2
+
+
 class ShwError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = int(status)
@@ -67,6 +80,11 @@ SIGNATURES = {
     "shw_render": (_i32, [_P(Volume), _P(Volume), _P(Camera), _P(RenderParams), _vp, _vp, _vp, _vp, _vp, _sz,
                           _vp]),
     "shw_ckpt_bytes": (_sz, [_P(Volume), _P(Camera), _P(RenderParams)]),
+    "shw_render_backward": (_i32, [_P(Volume), _P(Camera), _P(RenderParams), _vp, _vp, _sz, _vp, _vp, _vp, _vp]),
+    "shw_batch_plan_create": (_i32, [_P(_vp), _P(BatchItem), _i32, _P(RenderParams), _i32, _vp]),
+    "shw_render_batch": (_i32, [_vp, _vp]),
+    "shw_batch_plan_info": (_i32, [_vp, _P(BatchInfo)]),
+    "shw_batch_plan_destroy": (_i32, [_vp]),
 }
 
 
@@ -86,7 +104,7 @@ def lib():
                 fn.argtypes = args
             if L.shw_abi_version() != ABI_VERSION:
                 raise ImportError("libshw.so ABI version mismatch: rebuild it")
-            for which, st in enumerate((Volume, Camera, RenderParams)):
+            for which, st in enumerate((Volume, Camera, RenderParams, BatchItem, BatchInfo)):
                 if L.shw_struct_size(which) != C.sizeof(st):
                     raise ImportError(f"libshw.so struct layout mismatch for {st.__name__}")
             _lib = L

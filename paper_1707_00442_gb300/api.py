@@ -15,8 +15,8 @@ import torch
 from . import _lib
 from ._lib import INTERP, MODES, STORAGE, ShwError, check, lib
 
-__all__ = ["BrickVolume", "ShwError", "bricked_bytes", "ckpt_bytes", "launch_count", "pack_bricks", "render",
-           "smooth", "smooth_weights", "sync_status"]
+__all__ = ["BatchPlan", "BrickVolume", "ShwError", "bricked_bytes", "ckpt_bytes", "launch_count", "pack_bricks", "render",
+           "render_backward", "smooth", "smooth_weights", "sync_status"]
 
 
 def _stream() -> int:
@@ -168,6 +168,83 @@ def render(vol, cam, mode: str, *, lut: torch.Tensor, interp="trilinear", step=0
     check(lib().shw_render(C.byref(v), C.byref(v2) if v2 is not None else None, C.byref(c), C.byref(p),
                            ptr(rgba), ptr(sc), ptr(ix), ptr(ns), ptr(ck), nck, _stream()), "shw_render")
     return out
+
+
+def render_backward(vol, cam, grad_rgba: torch.Tensor, ckpt: torch.Tensor, *, lut: torch.Tensor, interp="trilinear",
+                    step=0.5, lo=-3.0, hi=8.0, opacity_scale=1.0, term_alpha=0.99, ckpt_interval=64,
+                    grad_vol: torch.Tensor | None = None, grad_lut: torch.Tensor | None = None,
+                    grad_scale: torch.Tensor | None = None) -> None:
+    """Accumulate (+=) the gradient of a compositing render into grad_vol / grad_lut / grad_scale
+    (shw_render_backward).  ``ckpt`` is the buffer returned by ``render(..., ckpt=True)`` with the
+    same arguments."""
+    v, c = volume_struct(vol), camera_struct(cam)
+    p = params_struct("composite", lut, interp=interp, step=step, lo=lo, hi=hi, opacity_scale=opacity_scale,
+                      term_alpha=term_alpha, ckpt_interval=ckpt_interval)
+    _need_cuda(grad_rgba, "grad_rgba", torch.float32)
+    _need_cuda(ckpt, "ckpt", torch.uint8)
+    for t, name in ((grad_vol, "grad_vol"), (grad_lut, "grad_lut"), (grad_scale, "grad_scale")):
+        if t is not None:
+            _need_cuda(t, name, torch.float32)
+    ptr = lambda t: None if t is None else t.data_ptr()
+    check(lib().shw_render_backward(C.byref(v), C.byref(c), C.byref(p), grad_rgba.data_ptr(), ckpt.data_ptr(),
+                                    ckpt.numel(), ptr(grad_vol), ptr(grad_lut), ptr(grad_scale), _stream()),
+          "shw_render_backward")
+
+
+class BatchPlan:
+    """A plan rendering many sub-cubes with one CUDA-graph launch (shw_batch_plan_create).
+
+    items: sequence of (vol, cam, mode) or (vol, cam, mode, out_rgba); vol is a float32 CUDA
+    cube or a BrickVolume; mode one of "mip", "avg", "composite", "spectral".  Missing
+    outputs are allocated.  The plan keeps references to every tensor it points at."""
+
+    def __init__(self, items, *, lut: torch.Tensor, interp="trilinear", step=0.5, lo=-3.0, hi=8.0,
+                 opacity_scale=1.0, term_alpha=0.99, tune=True, retune=False):
+        self._plan = None
+        p = params_struct("mip", lut, interp=interp, step=step, lo=lo, hi=hi, opacity_scale=opacity_scale,
+                          term_alpha=term_alpha)
+        arr = (_lib.BatchItem * len(items))()
+        self.outputs, self._keep = [], [lut]
+        for i, it in enumerate(items):
+            vol, cam, mode = it[0], it[1], it[2]
+            out = it[3] if len(it) > 3 and it[3] is not None else torch.empty(
+                (int(cam.height), int(cam.width), 4), dtype=torch.float32, device=lut.device)
+            _need_cuda(out, "out_rgba", torch.float32)
+            arr[i].vol = volume_struct(vol)
+            arr[i].cam = camera_struct(cam)
+            arr[i].out_rgba = out.data_ptr()
+            arr[i].mode = MODES[mode]
+            self.outputs.append(out)
+            self._keep.append(vol)
+        flags = (0 if tune else _lib.BATCH_NO_TUNE) | (_lib.BATCH_RETUNE if retune else 0)
+        handle = C.c_void_p()
+        check(lib().shw_batch_plan_create(C.byref(handle), arr, len(items), C.byref(p), flags, _stream()),
+              "shw_batch_plan_create")
+        self._plan = handle
+
+    def render(self) -> list:
+        check(lib().shw_render_batch(self._plan, _stream()), "shw_render_batch")
+        return self.outputs
+
+    @property
+    def info(self) -> dict:
+        inf = _lib.BatchInfo()
+        check(lib().shw_batch_plan_info(self._plan, C.byref(inf)), "shw_batch_plan_info")
+        n = inf.n_candidates
+        return {"n_items": inf.n_items, "n_work": inf.n_work, "tile": inf.tile, "ctas_per_sm": inf.ctas_per_sm,
+                "grid": inf.grid, "tuned": bool(inf.tuned),
+                "candidates": [(inf.cand_tile[i], inf.cand_ctas_per_sm[i], float(inf.tune_ms[i])) for i in range(n)]}
+
+    def close(self):
+        if self._plan is not None:
+            lib().shw_batch_plan_destroy(self._plan)
+            self._plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sync_status() -> None:

@@ -91,6 +91,8 @@ size_t shw_struct_size(int32_t which)
     case 0: return sizeof(shw_volume);
     case 1: return sizeof(shw_camera);
     case 2: return sizeof(shw_render_params);
+    case 3: return sizeof(shw_batch_item);
+    case 4: return sizeof(shw_batch_info);
     default: return 0;
     }
 }

@@ -1,0 +1,426 @@
+// batch.cu -- many sub-cubes of uneven sizes rendered by one persistent launch
+// captured in a CUDA graph.
+//
+// Upcoming surveys produce sub-cubes for the many hundreds of galaxies they
+// detect (Section 1); rendering each with its own launch wastes most of the GPU on
+// launch latency and tail effects.  A plan lays out every (item, image tile) as a
+// work item, ordered longest-first (an LPT schedule: big cubes' tiles first, small
+// ones fill the tail); a persistent grid of CTAs pops work items from one atomic
+// counter -- no CTA ever waits on another -- and renders each tile with the same
+// per-ray code as shw_render.  The counter reset and the launch are captured once
+// into a CUDA graph, so a batch render is a single graph launch.  An autotuner
+// times the candidate tile shapes and CTAs-per-SM at plan creation and caches the
+// winner per batch signature.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "render_impl.cuh"
+
+namespace shw {
+
+bool valid_volume(const shw_volume *v);
+bool valid_camera(const shw_camera *c);
+long long max_samples(const shw_volume *v, float step);
+
+struct BatchItemDev {
+    const void *data;
+    float4 *rgba;
+    int nx, ny, nz, storage, mode, tiles_x, nbx, nby, nmax, pad;
+    shw_camera cam;
+};
+
+struct BatchShared {
+    const float4 *lut;
+    float step, lo, inv_range, opacity_scale, term_alpha;
+    int nwork;
+};
+
+template <int INTERP, class S>
+__device__ __forceinline__ void batch_pixel(const S &s, const BatchItemDev &it, const RenderArgs &a,
+                                            const float4 *lut_s, int px, int py)
+{
+    switch (it.mode) {
+    case SHW_MIP: render_pixel<SHW_MIP, INTERP, S>(s, s, it.cam, a, lut_s, px, py); break;
+    case SHW_AVG: render_pixel<SHW_AVG, INTERP, S>(s, s, it.cam, a, lut_s, px, py); break;
+    case SHW_COMPOSITE: render_pixel<SHW_COMPOSITE, INTERP, S>(s, s, it.cam, a, lut_s, px, py); break;
+    default: render_pixel<SHW_SPECTRAL, INTERP, S>(s, s, it.cam, a, lut_s, px, py); break;
+    }
+}
+
+template <int TILE, int INTERP>
+__global__ void __launch_bounds__(TILE *TILE) batch_kernel(const BatchItemDev *__restrict__ items,
+                                                           const int2 *__restrict__ work, int *counter, BatchShared sh)
+{
+    __shared__ float4 lut_s[kLut];
+    __shared__ int w_s;
+    for (int i = threadIdx.x; i < kLut; i += blockDim.x) lut_s[i] = sh.lut[i];
+    constexpr int WX = TILE / 8;  // warps across a tile row; each warp covers 8 x 4 pixels
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lx = (warp % WX) * 8 + (lane & 7), ly = (warp / WX) * 4 + (lane >> 3);
+    for (;;) {
+        __syncthreads();  // everyone has read w_s (and the colour map is loaded)
+        if (threadIdx.x == 0) w_s = atomicAdd(counter, 1);
+        __syncthreads();
+        const int w = w_s;
+        if (w >= sh.nwork) break;
+        const int2 wi = work[w];
+        const BatchItemDev it = items[wi.x];
+        const int px = (wi.y % it.tiles_x) * TILE + lx, py = (wi.y / it.tiles_x) * TILE + ly;
+        if (px >= it.cam.width || py >= it.cam.height) continue;
+        RenderArgs a{};
+        a.rgba = it.rgba;
+        a.lut = sh.lut;
+        a.width = it.cam.width;
+        a.height = it.cam.height;
+        a.ckpt_interval = 64;
+        a.nmax = it.nmax;
+        a.step = sh.step;
+        a.lo = sh.lo;
+        a.inv_range = sh.inv_range;
+        a.opacity_scale = sh.opacity_scale;
+        a.term_alpha = sh.term_alpha;
+        a.nz = it.nz;
+        if (it.storage == SHW_F32) {
+            const SamplerF32<int> s{static_cast<const float *>(it.data), it.nx, it.ny, it.nz, it.nx, it.nx * it.ny};
+            batch_pixel<INTERP>(s, it, a, lut_s, px, py);
+        } else if (it.storage == SHW_BF16_BRICK) {
+            const SamplerBrick<__nv_bfloat16> s{static_cast<const unsigned short *>(it.data), it.nx, it.ny, it.nz,
+                                                it.nbx, it.nby};
+            batch_pixel<INTERP>(s, it, a, lut_s, px, py);
+        } else {
+            const SamplerBrick<__half> s{static_cast<const unsigned short *>(it.data), it.nx, it.ny, it.nz, it.nbx,
+                                         it.nby};
+            batch_pixel<INTERP>(s, it, a, lut_s, px, py);
+        }
+    }
+}
+
+using BatchKernel = void (*)(const BatchItemDev *, const int2 *, int *, BatchShared);
+
+static BatchKernel pick_kernel(int tile, int interp)
+{
+    if (tile == 8) return interp == SHW_NEAREST ? batch_kernel<8, SHW_NEAREST> : batch_kernel<8, SHW_TRILINEAR>;
+    return interp == SHW_NEAREST ? batch_kernel<16, SHW_NEAREST> : batch_kernel<16, SHW_TRILINEAR>;
+}
+
+struct Candidate {
+    int tile, ctas_per_sm;
+};
+static const Candidate kCandidates[] = {{16, 2}, {16, 4}, {16, 8}, {8, 8}, {8, 16}, {8, 32}};
+constexpr int kNumCandidates = (int)(sizeof(kCandidates) / sizeof(kCandidates[0]));
+
+// process-wide cache of tuned choices, keyed by the batch signature
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune_cache;
+
+}  // namespace shw
+
+using namespace shw;
+
+struct shw_batch_plan {
+    int device = 0;
+    int n_items = 0, nwork = 0, tile = 16, ctas_per_sm = 4, grid = 0, interp = SHW_TRILINEAR;
+    int sms = 0;
+    BatchItemDev *d_items = nullptr;
+    int2 *d_work = nullptr;
+    int *d_counter = nullptr;
+    BatchShared sh{};
+    std::vector<BatchItemDev> items;
+    std::vector<int> order;  // items sorted by estimated cost, descending
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    shw_batch_info info{};
+};
+
+static void plan_free(shw_batch_plan *pl)
+{
+    if (!pl) return;
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    if (pl->cap) cudaStreamDestroy(pl->cap);
+    if (pl->d_items) cudaFree(pl->d_items);
+    if (pl->d_work) cudaFree(pl->d_work);
+    if (pl->d_counter) cudaFree(pl->d_counter);
+    delete pl;
+}
+
+static bool fault(const char *what)
+{
+    const char *f = std::getenv("SHW_FAULT");
+    return f && std::strstr(f, what) != nullptr;
+}
+
+// (re)build the work list for a tile size: tiles of the biggest items first
+static shw_status build_work(shw_batch_plan *pl, int tile)
+{
+    std::vector<int2> work;
+    for (int i : pl->order) {
+        BatchItemDev &it = pl->items[i];
+        it.tiles_x = ceil_div(it.cam.width, tile);
+        const int ty = ceil_div(it.cam.height, tile);
+        for (int t = 0; t < it.tiles_x * ty; ++t) work.push_back(make_int2(i, t));
+    }
+    if (work.size() > (size_t)0x7fffffff) return SHW_EUNSUPPORTED;
+    pl->nwork = (int)work.size();
+    pl->sh.nwork = pl->nwork;
+    if (pl->d_work) cudaFree(pl->d_work);
+    pl->d_work = nullptr;
+    if (fault("alloc") || cudaMalloc(&pl->d_work, work.size() * sizeof(int2)) != cudaSuccess) {
+        cudaGetLastError();
+        pl->d_work = nullptr;
+        return SHW_ENOMEM;
+    }
+    if (cudaMemcpy(pl->d_work, work.data(), work.size() * sizeof(int2), cudaMemcpyHostToDevice) != cudaSuccess)
+        return SHW_ECUDA;
+    if (cudaMemcpy(pl->d_items, pl->items.data(), pl->items.size() * sizeof(BatchItemDev), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+        return SHW_ECUDA;
+    pl->tile = tile;
+    return SHW_OK;
+}
+
+static shw_status launch_direct(shw_batch_plan *pl, int ctas_per_sm, cudaStream_t st)
+{
+    if (cudaMemsetAsync(pl->d_counter, 0, sizeof(int), st) != cudaSuccess) return SHW_ECUDA;
+    const int grid = pl->sms * ctas_per_sm;
+    pick_kernel(pl->tile, pl->interp)<<<grid, pl->tile * pl->tile, 0, st>>>(pl->d_items, pl->d_work, pl->d_counter,
+                                                                             pl->sh);
+    return after_launch();
+}
+
+static shw_status capture(shw_batch_plan *pl)
+{
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    pl->exec = nullptr;
+    pl->graph = nullptr;
+    if (fault("graph")) return SHW_ECUDA;
+    if (cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SHW_ECUDA;
+    cudaMemsetAsync(pl->d_counter, 0, sizeof(int), pl->cap);
+    pl->grid = pl->sms * pl->ctas_per_sm;
+    pick_kernel(pl->tile, pl->interp)<<<pl->grid, pl->tile * pl->tile, 0, pl->cap>>>(pl->d_items, pl->d_work,
+                                                                                     pl->d_counter, pl->sh);
+    cudaError_t e = cudaStreamEndCapture(pl->cap, &pl->graph);
+    if (e != cudaSuccess || !pl->graph) {
+        cudaGetLastError();
+        return SHW_ECUDA;
+    }
+    if (cudaGraphInstantiate(&pl->exec, pl->graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return SHW_ECUDA;
+    }
+    return SHW_OK;
+}
+
+static std::string signature(const shw_batch_plan *pl)
+{
+    // size class of the work: log2 of the mean item voxel count and image area, storages, modes
+    double vox = 0.0, pix = 0.0;
+    int smask = 0, mmask = 0;
+    for (const auto &it : pl->items) {
+        vox += (double)it.nx * it.ny * it.nz;
+        pix += (double)it.cam.width * it.cam.height;
+        smask |= 1 << it.storage;
+        mmask |= 1 << it.mode;
+    }
+    const int n = std::max(1, pl->n_items);
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "i%d v%d p%d n%d s%d m%d sm%d", pl->interp, (int)std::lround(std::log2(vox / n + 1)),
+                  (int)std::lround(std::log2(pix / n + 1)), (int)std::lround(std::log2((double)n)), smask, mmask,
+                  pl->sms);
+    return buf;
+}
+
+static shw_status autotune(shw_batch_plan *pl, cudaStream_t st, int *best_out)
+{
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SHW_ECUDA;
+    int best = -1;
+    float best_ms = 1e30f;
+    for (int c = 0; c < kNumCandidates; ++c) {
+        shw_status s = build_work(pl, kCandidates[c].tile);
+        if (s != SHW_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return s;
+        }
+        s = launch_direct(pl, kCandidates[c].ctas_per_sm, st);  // warm-up
+        float ms = 1e30f;
+        for (int rep = 0; rep < 2 && s == SHW_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            s = launch_direct(pl, kCandidates[c].ctas_per_sm, st);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) s = SHW_ECUDA;
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, e0, e1);
+            ms = std::min(ms, t);
+        }
+        if (s != SHW_OK) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return s;
+        }
+        pl->info.tune_ms[c] = ms;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *best_out = best;
+    return SHW_OK;
+}
+
+extern "C" {
+
+shw_status shw_batch_plan_create(shw_batch_plan **out, const shw_batch_item *items, int32_t n,
+                                 const shw_render_params *p, int32_t flags, void *stream)
+{
+    if (!out) return SHW_EINVAL;
+    *out = nullptr;
+    if (!items || n <= 0 || !p || !p->lut || !aligned(p->lut, 16)) return SHW_EINVAL;
+    if (p->interp != SHW_NEAREST && p->interp != SHW_TRILINEAR) return SHW_EINVAL;
+    if (!std::isfinite(p->step) || !(p->step > 0.0f) || !(p->hi > p->lo) || !std::isfinite(p->lo) ||
+        !std::isfinite(p->hi) || !std::isfinite(p->opacity_scale) || !std::isfinite(p->term_alpha))
+        return SHW_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        const shw_batch_item &b = items[i];
+        if (!valid_volume(&b.vol) || !valid_camera(&b.cam) || !b.out_rgba || !aligned(b.out_rgba, 16))
+            return SHW_EINVAL;
+        if (b.mode != SHW_MIP && b.mode != SHW_AVG && b.mode != SHW_COMPOSITE && b.mode != SHW_SPECTRAL)
+            return b.mode == SHW_RATIO ? SHW_EUNSUPPORTED : SHW_EINVAL;
+        if ((long long)b.vol.nx * b.vol.ny * b.vol.nz >= (1LL << 31)) return SHW_EUNSUPPORTED;
+        if (max_samples(&b.vol, p->step) > (1LL << 30)) return SHW_EINVAL;
+    }
+    shw_batch_plan *pl = new (std::nothrow) shw_batch_plan();
+    if (!pl) return SHW_ENOMEM;
+    if (cudaGetDevice(&pl->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&pl->sms, cudaDevAttrMultiProcessorCount, pl->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete pl;
+        return SHW_EDEVICE;
+    }
+    pl->n_items = n;
+    pl->interp = p->interp;
+    pl->sh.lut = reinterpret_cast<const float4 *>(p->lut);
+    pl->sh.step = p->step;
+    pl->sh.lo = p->lo;
+    pl->sh.inv_range = 1.0f / (p->hi - p->lo);
+    pl->sh.opacity_scale = p->opacity_scale;
+    pl->sh.term_alpha = p->term_alpha;
+    pl->items.resize(n);
+    std::vector<double> cost(n);
+    for (int i = 0; i < n; ++i) {
+        const shw_batch_item &b = items[i];
+        BatchItemDev &d = pl->items[i];
+        std::memset(&d, 0, sizeof d);
+        d.data = b.vol.data;
+        d.rgba = reinterpret_cast<float4 *>(b.out_rgba);
+        d.nx = b.vol.nx;
+        d.ny = b.vol.ny;
+        d.nz = b.vol.nz;
+        d.storage = b.vol.storage;
+        d.mode = b.mode;
+        d.nbx = ceil_div(b.vol.nx, kBrick);
+        d.nby = ceil_div(b.vol.ny, kBrick);
+        d.nmax = (int)max_samples(&b.vol, p->step);
+        d.cam = b.cam;
+        // expected work: pixels x mean chord (~ cube size) in samples
+        cost[i] = (double)b.cam.width * b.cam.height * std::cbrt((double)b.vol.nx * b.vol.ny * b.vol.nz) / p->step;
+    }
+    pl->order.resize(n);
+    for (int i = 0; i < n; ++i) pl->order[i] = i;
+    std::stable_sort(pl->order.begin(), pl->order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+
+    if (fault("alloc") || cudaMalloc(&pl->d_items, sizeof(BatchItemDev) * n) != cudaSuccess ||
+        cudaMalloc(&pl->d_counter, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        plan_free(pl);
+        return SHW_ENOMEM;
+    }
+    if (cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        plan_free(pl);
+        return SHW_ECUDA;
+    }
+    cudaStream_t st = as_stream(stream);
+    const std::string sig = signature(pl);
+    int choice = 1;  // {16, 4}
+    bool tuned = false;
+    if (!(flags & SHW_BATCH_NO_TUNE)) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto itc = g_tune_cache.find(sig);
+        if (itc != g_tune_cache.end() && !(flags & SHW_BATCH_RETUNE)) {
+            choice = itc->second;
+        } else {
+            int best = -1;
+            shw_status s = autotune(pl, st, &best);
+            if (s != SHW_OK) {
+                plan_free(pl);
+                return s;
+            }
+            choice = best;
+            tuned = true;
+            g_tune_cache[sig] = best;
+        }
+    }
+    pl->ctas_per_sm = kCandidates[choice].ctas_per_sm;
+    shw_status s = build_work(pl, kCandidates[choice].tile);
+    if (s == SHW_OK) s = capture(pl);
+    if (s != SHW_OK) {
+        plan_free(pl);
+        return s;
+    }
+    shw_batch_info &inf = pl->info;
+    inf.n_items = n;
+    inf.n_work = pl->nwork;
+    inf.tile = pl->tile;
+    inf.ctas_per_sm = pl->ctas_per_sm;
+    inf.grid = pl->grid;
+    inf.tuned = tuned ? 1 : 0;
+    inf.n_candidates = kNumCandidates;
+    for (int c = 0; c < kNumCandidates && c < 8; ++c) {
+        inf.cand_tile[c] = kCandidates[c].tile;
+        inf.cand_ctas_per_sm[c] = kCandidates[c].ctas_per_sm;
+        if (!tuned) inf.tune_ms[c] = -1.0f;
+    }
+    *out = pl;
+    return SHW_OK;
+}
+
+shw_status shw_render_batch(shw_batch_plan *plan, void *stream)
+{
+    if (!plan || !plan->exec) return SHW_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) return SHW_EINVAL;
+    if (cudaGraphLaunch(plan->exec, as_stream(stream)) != cudaSuccess) return SHW_ECUDA;
+    note_launch();
+    return SHW_OK;
+}
+
+shw_status shw_batch_plan_info(const shw_batch_plan *plan, shw_batch_info *info)
+{
+    if (!plan || !info) return SHW_EINVAL;
+    *info = plan->info;
+    return SHW_OK;
+}
+
+shw_status shw_batch_plan_destroy(shw_batch_plan *plan)
+{
+    if (!plan) return SHW_EINVAL;
+    cudaDeviceSynchronize();  // no launch of this plan may still be running
+    cudaGetLastError();
+    plan_free(plan);
+    return SHW_OK;
+}
+
+}  // extern "C"

@@ -63,17 +63,12 @@ __device__ __forceinline__ float fetch(const S &s, long long X, long long Y, lon
         return s.trilinear(X, Y, Z);
 }
 
+// One ray of Algorithm 1 with the transfer function MODE.  lut_c: the colour map in
+// shared memory (read per sample by COMPOSITE); a.lut: the same map in global memory.
 template <int MODE, int INTERP, class S>
-__global__ void __launch_bounds__(kRenderThreads) render_kernel(S s, S s2, shw_camera cam, RenderArgs a)
+__device__ __forceinline__ void render_pixel(const S &s, const S &s2, const shw_camera &cam, const RenderArgs &a,
+                                             const float4 *lut_c, int px, int py)
 {
-    __shared__ float4 lut_s[kLut];
-    if constexpr (MODE == SHW_COMPOSITE) {
-        for (int i = threadIdx.x; i < kLut; i += blockDim.x) lut_s[i] = a.lut[i];
-        __syncthreads();
-    }
-    int px, py;
-    tile_pixel(px, py);
-    if (px >= a.width || py >= a.height) return;
     const long long pix = (long long)py * a.width + px;
     const long long npix = (long long)a.width * a.height;
 
@@ -153,7 +148,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(S s, S s2, shw_c
             if (a.ckpt_T != nullptr && (k % I) == 0 && k / I < a.nckpt) a.ckpt_T[(long long)(k / I) * npix + pix] = T;
             float v = fetch<INTERP>(s, X, Y, Z);
             v = isnan(v) ? a.lo : v;
-            const float4 c = lut_eval(lut_s, normalise(v, a.lo, a.inv_range));
+            const float4 c = lut_eval(lut_c, normalise(v, a.lo, a.inv_range));
             const float al = fminf(fmaxf(a.opacity_scale * c.w, 0.0f), 1.0f);
             const float w = T * al;
             cr = __fmaf_rn(w, c.x, cr);
@@ -176,6 +171,20 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(S s, S s2, shw_c
     if (a.scalar) a.scalar[pix] = scalar;
     if (a.index) a.index[pix] = index;
     if (a.nsamples) a.nsamples[pix] = done;
+}
+
+template <int MODE, int INTERP, class S>
+__global__ void __launch_bounds__(kRenderThreads) render_kernel(S s, S s2, shw_camera cam, RenderArgs a)
+{
+    __shared__ float4 lut_s[kLut];
+    if constexpr (MODE == SHW_COMPOSITE) {
+        for (int i = threadIdx.x; i < kLut; i += blockDim.x) lut_s[i] = a.lut[i];
+        __syncthreads();
+    }
+    int px, py;
+    tile_pixel(px, py);
+    if (px >= a.width || py >= a.height) return;
+    render_pixel<MODE, INTERP, S>(s, s2, cam, a, lut_s, px, py);
 }
 
 // Host-side launch for one storage type (instantiated per storage in its own TU).

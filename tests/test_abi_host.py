@@ -47,6 +47,8 @@ def test_struct_layout(L):
     assert L.shw_struct_size(0) == C.sizeof(_lib.Volume) == 24
     assert L.shw_struct_size(1) == C.sizeof(_lib.Camera) == 68
     assert L.shw_struct_size(2) == C.sizeof(_lib.RenderParams) == 48
+    assert L.shw_struct_size(3) == C.sizeof(_lib.BatchItem) == 112
+    assert L.shw_struct_size(4) == C.sizeof(_lib.BatchInfo)
     assert L.shw_struct_size(9) == 0
     assert L.shw_abi_version() == 1
 
@@ -147,3 +149,30 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(_lib, "_lib", None)
     with pytest.raises(ImportError):
         _lib.lib()
+
+
+def test_batch_plan_rejects_invalid_arguments_on_host(L):
+    from paper_1707_00442_gb300 import _lib
+    b = C.byref
+    h = C.c_void_p()
+    items = (_lib.BatchItem * 2)()
+    for it in items:
+        it.vol = _vol()
+        it.cam = _cam()
+        it.out_rgba = 0x4000
+        it.mode = 0
+    p = _params()
+    assert L.shw_batch_plan_create(None, items, 2, b(p), 0, None) == 1
+    assert L.shw_batch_plan_create(b(h), items, 0, b(p), 0, None) == 1
+    assert L.shw_batch_plan_create(b(h), items, 2, b(_params(lut=0)), 0, None) == 1
+    assert L.shw_batch_plan_create(b(h), items, 2, b(_params(step=0.0)), 0, None) == 1
+    items[1].mode = 4
+    assert L.shw_batch_plan_create(b(h), items, 2, b(p), 0, None) == 2      # ratio: unsupported in a batch
+    items[1].mode = 7
+    assert L.shw_batch_plan_create(b(h), items, 2, b(p), 0, None) == 1
+    items[1].mode = 2
+    items[1].out_rgba = 0x4004
+    assert L.shw_batch_plan_create(b(h), items, 2, b(p), 0, None) == 1
+    assert h.value is None
+    assert L.shw_render_batch(None, None) == 1
+    assert L.shw_batch_plan_destroy(None) == 1
