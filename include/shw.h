@@ -239,6 +239,31 @@ shw_status shw_batch_plan_info(const shw_batch_plan *plan, shw_batch_info *info)
 /* Waits for the device to finish outstanding work, then frees the plan. */
 shw_status shw_batch_plan_destroy(shw_batch_plan *plan);
 
+/* ---- batched rendering without device allocation -------------------------- */
+
+/* The paper has no counterpart of this call.  It exists for callers that cannot
+ * let a library allocate device memory -- a host program that owns every byte of
+ * the GPU through its own pool or budget (for example a plugin inside a
+ * visualisation application), or an interactive loop that must never stall in an
+ * allocator.  It renders the same images as a batch plan (16 x 16 tiles, 4 CTAs per
+ * SM, no autotuning) but keeps the item table, the work list and the work counter
+ * in a fixed device array that is part of the library: every GPU that loads
+ * libshw.so holds SHW_NOALLOC_SCRATCH_BYTES of it until the process exits.  The
+ * call makes no cudaMalloc/cudaFree or other allocating call; the caller passes the
+ * inputs and outputs as for shw_batch_plan_create.
+ *  - Capacity: 256 + 128 * n + 8 * (total 16 x 16 tiles of all images) bytes must fit
+ *    in SHW_NOALLOC_SCRATCH_BYTES, else SHW_EUNSUPPORTED and nothing is enqueued.
+ *  - The first call on a device looks up the array's device address (with that
+ *    device current) and caches it; make that first call before any stream capture.
+ *  - Every call reuses the one array per device and overwrites the previous call's
+ *    contents (the counter is cleared on `stream` first).  Calls whose work can
+ *    overlap on the GPU -- on different streams without ordering -- race with each
+ *    other; calls on one stream are ordered.
+ *  - Other errors as for shw_batch_plan_create. */
+#define SHW_NOALLOC_SCRATCH_BYTES (8u << 20)
+shw_status shw_render_batch_noalloc(const shw_batch_item *items, int32_t n, const shw_render_params *p,
+                                    void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -85,7 +85,9 @@ SIGNATURES = {
     "shw_render_batch": (_i32, [_vp, _vp]),
     "shw_batch_plan_info": (_i32, [_vp, _P(BatchInfo)]),
     "shw_batch_plan_destroy": (_i32, [_vp]),
+    "shw_render_batch_noalloc": (_i32, [_P(BatchItem), _i32, _P(RenderParams), _vp]),
 }
+NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
 def lib():

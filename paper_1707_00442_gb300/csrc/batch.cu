@@ -424,3 +424,139 @@ shw_status shw_batch_plan_destroy(shw_batch_plan *plan)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched rendering without any device allocation.
+//
+// Some callers cannot let a library allocate device memory: a host application
+// that owns every byte of the GPU through its own pool or budget (a plugin inside
+// a visualisation program), or an interactive loop that must never stall in the
+// allocator.  For them the batch kernel above also runs from a fixed scratch
+// array that is part of the library image: every GPU that loads the library holds
+// these SHW_NOALLOC_SCRATCH_BYTES until the process exits.  Host code must not
+// take the array's address directly (in host code its name is only a stand-in for
+// the device symbol), so each device's address is fetched once with
+// cudaGetSymbolAddress while that device is current.
+
+namespace shw {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SHW_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+constexpr size_t kNoallocCounterBytes = 256;  // the work counter lives in the first aligned slot
+static std::mutex g_noalloc_mu;
+static unsigned char *g_noalloc_ptr[kNoallocMaxDevices] = {};
+static int g_noalloc_sms[kNoallocMaxDevices] = {};
+
+}  // namespace shw
+
+extern "C" shw_status shw_render_batch_noalloc(const shw_batch_item *items, int32_t n, const shw_render_params *p,
+                                               void *stream)
+{
+    if (!items || n <= 0 || !p || !p->lut || !aligned(p->lut, 16)) return SHW_EINVAL;
+    if (p->interp != SHW_NEAREST && p->interp != SHW_TRILINEAR) return SHW_EINVAL;
+    if (!std::isfinite(p->step) || !(p->step > 0.0f) || !(p->hi > p->lo) || !std::isfinite(p->lo) ||
+        !std::isfinite(p->hi) || !std::isfinite(p->opacity_scale) || !std::isfinite(p->term_alpha))
+        return SHW_EINVAL;
+    constexpr int tile = 16, ctas_per_sm = 4;
+    std::vector<double> cost(n);
+    long long nwork = 0;
+    for (int i = 0; i < n; ++i) {
+        const shw_batch_item &b = items[i];
+        if (!valid_volume(&b.vol) || !valid_camera(&b.cam) || !b.out_rgba || !aligned(b.out_rgba, 16))
+            return SHW_EINVAL;
+        if (b.mode != SHW_MIP && b.mode != SHW_AVG && b.mode != SHW_COMPOSITE && b.mode != SHW_SPECTRAL)
+            return b.mode == SHW_RATIO ? SHW_EUNSUPPORTED : SHW_EINVAL;
+        if ((long long)b.vol.nx * b.vol.ny * b.vol.nz >= (1LL << 31)) return SHW_EUNSUPPORTED;
+        if (max_samples(&b.vol, p->step) > (1LL << 30)) return SHW_EINVAL;
+        nwork += (long long)ceil_div(b.cam.width, tile) * ceil_div(b.cam.height, tile);
+        cost[i] = (double)b.cam.width * b.cam.height * std::cbrt((double)b.vol.nx * b.vol.ny * b.vol.nz) / p->step;
+    }
+    const size_t items_off = kNoallocCounterBytes;
+    const size_t work_off = items_off + sizeof(BatchItemDev) * (size_t)n;
+    const size_t bytes = work_off + sizeof(int2) * (size_t)nwork;
+    if (nwork > 0x7fffffffLL || bytes > SHW_NOALLOC_SCRATCH_BYTES) return SHW_EUNSUPPORTED;  // beyond the fixed scratch
+
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return SHW_EDEVICE;
+    }
+    if (dev < 0 || dev >= kNoallocMaxDevices) return SHW_EUNSUPPORTED;
+    unsigned char *scratch = nullptr;
+    int sms = 0;
+    {
+        // once per device, with that device current: the scratch array's device address
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+                cudaGetLastError();
+                return SHW_ECUDA;
+            }
+            int nsm = 0;
+            if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) {
+                cudaGetLastError();
+                return SHW_EDEVICE;
+            }
+            g_noalloc_ptr[dev] = static_cast<unsigned char *>(ptr);
+            g_noalloc_sms[dev] = nsm;
+        }
+        scratch = g_noalloc_ptr[dev];
+        sms = g_noalloc_sms[dev];
+    }
+
+    // the item table and the work list (largest items' tiles first), staged on the host
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<unsigned char> host(bytes - items_off);
+    BatchItemDev *hitems = reinterpret_cast<BatchItemDev *>(host.data());
+    int2 *hwork = reinterpret_cast<int2 *>(host.data() + (work_off - items_off));
+    for (int i = 0; i < n; ++i) {
+        const shw_batch_item &b = items[i];
+        BatchItemDev d;
+        std::memset(&d, 0, sizeof d);
+        d.data = b.vol.data;
+        d.rgba = reinterpret_cast<float4 *>(b.out_rgba);
+        d.nx = b.vol.nx;
+        d.ny = b.vol.ny;
+        d.nz = b.vol.nz;
+        d.storage = b.vol.storage;
+        d.mode = b.mode;
+        d.nbx = ceil_div(b.vol.nx, kBrick);
+        d.nby = ceil_div(b.vol.ny, kBrick);
+        d.nmax = (int)max_samples(&b.vol, p->step);
+        d.cam = b.cam;
+        d.tiles_x = ceil_div(b.cam.width, tile);
+        std::memcpy(hitems + i, &d, sizeof d);
+    }
+    long long w = 0;
+    for (int i : order) {
+        const int nt = ceil_div(items[i].cam.width, tile) * ceil_div(items[i].cam.height, tile);
+        for (int t = 0; t < nt; ++t) hwork[w++] = make_int2(i, t);
+    }
+    BatchShared sh{};
+    sh.lut = reinterpret_cast<const float4 *>(p->lut);
+    sh.step = p->step;
+    sh.lo = p->lo;
+    sh.inv_range = 1.0f / (p->hi - p->lo);
+    sh.opacity_scale = p->opacity_scale;
+    sh.term_alpha = p->term_alpha;
+    sh.nwork = (int)nwork;
+
+    cudaStream_t st = as_stream(stream);
+    int *counter = reinterpret_cast<int *>(scratch);
+    // the array keeps the previous call's contents: the counter must start at zero
+    if (cudaMemsetAsync(counter, 0, sizeof(int), st) != cudaSuccess) return SHW_ECUDA;
+    if (cudaMemcpyAsync(scratch + items_off, host.data(), host.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return SHW_ECUDA;
+    pick_kernel(tile, p->interp)<<<sms * ctas_per_sm, tile * tile, 0, st>>>(
+        reinterpret_cast<const BatchItemDev *>(scratch + items_off), reinterpret_cast<const int2 *>(scratch + work_off),
+        counter, sh);
+    return after_launch();
+}
+
+extern "C" {
+
+}  // extern "C"
