@@ -57,7 +57,7 @@ typedef enum {
     SHW_EUNSUPPORTED = 2,  /* a valid request this build does not handle (size limits) */
     SHW_ECUDA = 3,         /* the CUDA runtime reported an error */
     SHW_ENOMEM = 4,        /* a caller buffer is too small, or a plan allocation failed */
-    SHW_ETIMEOUT = 5,      /* reserved: no kernel of this library waits on another */
+    SHW_ETIMEOUT = 5,      /* a kernel's bounded wait for its own asynchronous copy gave up (shw_sync_status) */
     SHW_EDEVICE = 6        /* no usable CUDA device */
 } shw_status;
 
@@ -117,7 +117,8 @@ size_t shw_struct_size(int32_t which);
 /* Number of kernels this library has launched in this process (all devices). */
 uint64_t shw_launch_count(void);
 
-/* Wait for `stream` and report any error the CUDA runtime has latched. */
+/* Wait for `stream` and report any error the CUDA runtime has latched, then the
+ * library's device error word of the current device (SHW_ETIMEOUT; the word is cleared). */
 shw_status shw_sync_status(void *stream);
 
 /* ---- smoothing (Section 4.2) ---------------------------------------------- */

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kRenderThreads) backward_kernel(SamplerF32<lon
 
     float gs = 0.0f;
     int px, py;
-    tile_pixel(px, py);
+    tile_pixel(px, py, 3);
     if (px < a.width && py < a.height) {
         const long long pix = (long long)py * a.width + px;
         const long long npix = (long long)a.width * a.height;

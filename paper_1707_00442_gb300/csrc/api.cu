@@ -5,13 +5,66 @@
 #include <cmath>
 #include <cstring>
 
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "common.cuh"
 #include "render_impl.cuh"
+#include "tma.cuh"
 
 namespace shw {
 
 static std::atomic<uint64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// The device error word: kernels OR in a bit when a bounded wait gives up.
+static __device__ unsigned g_device_error;
+static std::mutex g_err_mu;
+static unsigned *g_err_ptr[64] = {};
+
+unsigned *device_error_word()
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    if (!g_err_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_device_error) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_err_ptr[dev] = static_cast<unsigned *>(p);
+    }
+    return g_err_ptr[dev];
+}
+
+bool encode_tmap_3d_f32(CUtensorMap *map, const float *base, int nx, int ny, int nz, int bx, int by)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+        cudaGetLastError();
+    });
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
 
 static bool finite3(const float v[3]) { return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]); }
 
@@ -108,7 +161,18 @@ shw_status shw_sync_status(void *stream)
     }
     cudaError_t e = cudaStreamSynchronize(as_stream(stream));
     if (e != cudaSuccess) return SHW_ECUDA;
-    return cudaGetLastError() == cudaSuccess ? SHW_OK : SHW_ECUDA;
+    if (cudaGetLastError() != cudaSuccess) return SHW_ECUDA;
+    unsigned *w = device_error_word();
+    if (w) {
+        unsigned v = 0;
+        if (cudaMemcpy(&v, w, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return SHW_ECUDA;
+        if (v != 0) {
+            const unsigned zero = 0;
+            cudaMemcpy(w, &zero, sizeof zero, cudaMemcpyHostToDevice);
+            return SHW_ETIMEOUT;
+        }
+    }
+    return SHW_OK;
 }
 
 size_t shw_ckpt_bytes(const shw_volume *vol, const shw_camera *cam, const shw_render_params *p)
@@ -149,6 +213,7 @@ shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_c
     a.ratio_floor = p->ratio_floor;
     a.nz = vol->nz;
     a.nmax = (int)max_samples(vol, p->step);
+    a.warp_shift = warp_shift_for(*cam);
     a.ckpt_interval = p->ckpt_interval > 0 ? p->ckpt_interval : 64;
     if (ckpt) {
         if (p->mode != SHW_COMPOSITE || p->ckpt_interval <= 0 || !aligned(ckpt, 4)) return SHW_EINVAL;

@@ -25,11 +25,15 @@ struct RenderArgs {
     int width, height;
     int nckpt, ckpt_interval;
     int nmax;  // upper bound of N over all rays (box diagonal / step + 1)
+    int warp_shift;
     float step, lo, inv_range, opacity_scale, term_alpha, ratio_floor;
     int nz;
 };
 
 constexpr int kTileX = 16, kTileY = 16, kRenderThreads = 256;
+#ifndef SHW_WARP_SHIFT
+#define SHW_WARP_SHIFT -1  // -1: chosen per launch from the camera; else log2 of the warp tile width
+#endif
 
 // Colour-map lookup: linear between the 256 knots at u = 255 v_hat (Section 2.1).
 __device__ __forceinline__ float4 lut_eval(const float4 *L, float vhat)
@@ -47,11 +51,15 @@ __device__ __forceinline__ float normalise(float v, float lo, float inv_range)
     return fminf(fmaxf((v - lo) * inv_range, 0.0f), 1.0f);
 }
 
-__device__ __forceinline__ void tile_pixel(int &px, int &py)
+// Pixel of this thread.  A warp covers a (2^ws) x (32 / 2^ws) pixel tile: ws = 4 (16 x 2)
+// or 1 (2 x 16) when rows or columns of the image run close to the cube's x axis
+// (the contiguous one, so a warp's loads share cache lines), ws = 3 (8 x 4) otherwise.
+__device__ __forceinline__ void tile_pixel(int &px, int &py, int ws)
 {
+    const int wtx = 1 << ws, wty = 32 >> ws, wpr = kTileX >> ws;  // warps per tile row
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    px = blockIdx.x * kTileX + (warp & 1) * 8 + (lane & 7);
-    py = blockIdx.y * kTileY + (warp >> 1) * 4 + (lane >> 3);
+    px = blockIdx.x * kTileX + (warp % wpr) * wtx + (lane & (wtx - 1));
+    py = blockIdx.y * kTileY + (warp / wpr) * wty + (lane >> ws);
 }
 
 template <int INTERP, class S>
@@ -61,6 +69,16 @@ __device__ __forceinline__ float fetch(const S &s, long long X, long long Y, lon
         return s.nearest(X, Y, Z);
     else
         return s.trilinear(X, Y, Z);
+}
+
+// the marcher's fetch: with SHW_CELL_CACHE, trilinear samples reuse the previous cell's corners
+template <int INTERP, class S>
+__device__ __forceinline__ float fetch_c(const S &s, long long X, long long Y, long long Z, CellCache &cc)
+{
+    if constexpr (INTERP == SHW_TRILINEAR && SHW_CELL_CACHE)
+        return trilinear_cached(s, X, Y, Z, cc);
+    else
+        return fetch<INTERP>(s, X, Y, Z);
 }
 
 // One ray of Algorithm 1 with the transfer function MODE.  lut_c: the colour map in
@@ -87,14 +105,15 @@ __device__ __forceinline__ void render_pixel(const S &s, const S &s2, const shw_
     if constexpr (MODE == SHW_MIP || MODE == SHW_SPECTRAL || MODE == SHW_RATIO) {
         float m = -INFINITY;
         int kmax = 0;
+        CellCache cc, cc2;
         for (int k = 0; k < N; ++k) {
             float v;
             if constexpr (MODE == SHW_RATIO) {
                 // Algorithm 14: ratio where cube1 exceeds the floor, else DATAMIN
-                const float c1 = fetch<INTERP>(s, X, Y, Z), c2 = fetch<INTERP>(s2, X, Y, Z);
+                const float c1 = fetch_c<INTERP>(s, X, Y, Z, cc), c2 = fetch_c<INTERP>(s2, X, Y, Z, cc2);
                 v = (c1 > a.ratio_floor) ? __fdiv_rn(c2, c1) : a.lo;
             } else {
-                v = fetch<INTERP>(s, X, Y, Z);
+                v = fetch_c<INTERP>(s, X, Y, Z, cc);
             }
             v = isnan(v) ? a.lo : v;
             if (v >= m) {  // Eq. 1: ">=", the last maximum along the ray wins
@@ -124,8 +143,9 @@ __device__ __forceinline__ void render_pixel(const S &s, const S &s2, const shw_
     } else if constexpr (MODE == SHW_AVG) {
         // Eq. 3 divided by N; compensated (Kahan) summation keeps FP32 exact enough
         float sum = 0.0f, comp = 0.0f;
+        CellCache cc;
         for (int k = 0; k < N; ++k) {
-            float v = fetch<INTERP>(s, X, Y, Z);
+            float v = fetch_c<INTERP>(s, X, Y, Z, cc);
             v = isnan(v) ? a.lo : v;
             const float y = __fsub_rn(v, comp);
             const float t = __fadd_rn(sum, y);
@@ -144,9 +164,10 @@ __device__ __forceinline__ void render_pixel(const S &s, const S &s2, const shw_
         float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
         const int I = a.ckpt_interval;
         int k = 0;
+        CellCache cc;
         for (; k < N;) {
             if (a.ckpt_T != nullptr && (k % I) == 0 && k / I < a.nckpt) a.ckpt_T[(long long)(k / I) * npix + pix] = T;
-            float v = fetch<INTERP>(s, X, Y, Z);
+            float v = fetch_c<INTERP>(s, X, Y, Z, cc);
             v = isnan(v) ? a.lo : v;
             const float4 c = lut_eval(lut_c, normalise(v, a.lo, a.inv_range));
             const float al = fminf(fmaxf(a.opacity_scale * c.w, 0.0f), 1.0f);
@@ -182,7 +203,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(S s, S s2, shw_c
         __syncthreads();
     }
     int px, py;
-    tile_pixel(px, py);
+    tile_pixel(px, py, a.warp_shift);
     if (px >= a.width || py >= a.height) return;
     render_pixel<MODE, INTERP, S>(s, s2, cam, a, lut_s, px, py);
 }
@@ -212,6 +233,16 @@ shw_status launch_render_modes(int mode, int interp, const S &s, const S &s2, co
 #undef SHW_CASE
 #undef SHW_LAUNCH
     return after_launch();
+}
+
+// Warp tile orientation for a camera (see tile_pixel).
+inline int warp_shift_for(const shw_camera &c)
+{
+    if (SHW_WARP_SHIFT >= 0) return SHW_WARP_SHIFT;
+    const float rx = c.right[0] < 0 ? -c.right[0] : c.right[0], ux = c.up[0] < 0 ? -c.up[0] : c.up[0];
+    if (rx >= 0.5f && rx >= ux) return 4;
+    if (ux >= 0.5f) return 1;
+    return 3;
 }
 
 // Entry points of the per-storage translation units.

@@ -42,6 +42,25 @@ struct SamplerF32 {
         return __ldg(v + ((Idx)z * sz + (Idx)y * sy + x));
     }
 
+    // corner values c[z][y][x] of the cell with base (ix, iy, iz), each in [-1, n-1]
+    __device__ __forceinline__ void corners(int ix, int iy, int iz, float c[8]) const
+    {
+        const int x0 = max(ix, 0), y0 = max(iy, 0), z0 = max(iz, 0);
+        const int dx = min(ix + 1, nx - 1) - x0;
+        const Idx dy = (Idx)(min(iy + 1, ny - 1) - y0) * sy;
+        const Idx dz = (Idx)(min(iz + 1, nz - 1) - z0) * sz;
+        const float *p00 = v + ((Idx)z0 * sz + (Idx)y0 * sy + x0);
+        const float *p01 = p00 + dy, *p10 = p00 + dz, *p11 = p10 + dy;
+        c[0] = __ldg(p00);
+        c[1] = __ldg(p00 + dx);
+        c[2] = __ldg(p01);
+        c[3] = __ldg(p01 + dx);
+        c[4] = __ldg(p10);
+        c[5] = __ldg(p10 + dx);
+        c[6] = __ldg(p11);
+        c[7] = __ldg(p11 + dx);
+    }
+
     __device__ __forceinline__ float trilinear(long long X, long long Y, long long Z) const
     {
         const int ix = clampi(fx_cell(X), -1, nx - 1), iy = clampi(fx_cell(Y), -1, ny - 1),
@@ -57,6 +76,34 @@ struct SamplerF32 {
                        __ldg(p11), __ldg(p11 + dx), fx, fy, fz);
     }
 };
+
+// 1: reuse the 8 corners of the cell a ray is in until it leaves that cell; 0: no reuse
+#ifndef SHW_CELL_CACHE
+#define SHW_CELL_CACHE 1
+#endif
+
+// The corners c[a + 2b + 4c] (a, b, c = x, y, z offsets) of the last interpolation cell
+// a ray visited.  Consecutive samples 1/2 voxel apart often stay in one cell and then
+// need no loads at all.
+struct CellCache {
+    int ix = -4, iy = -4, iz = -4;  // no cell yet: valid cells start at -1
+    float c[8];
+};
+
+template <class S>
+__device__ __forceinline__ float trilinear_cached(const S &s, long long X, long long Y, long long Z, CellCache &cc)
+{
+    const int ix = clampi(fx_cell(X), -1, s.nx - 1), iy = clampi(fx_cell(Y), -1, s.ny - 1),
+              iz = clampi(fx_cell(Z), -1, s.nz - 1);
+    if (ix != cc.ix || iy != cc.iy || iz != cc.iz) {
+        s.corners(ix, iy, iz, cc.c);
+        cc.ix = ix;
+        cc.iy = iy;
+        cc.iz = iz;
+    }
+    return trilerp(cc.c[0], cc.c[1], cc.c[2], cc.c[3], cc.c[4], cc.c[5], cc.c[6], cc.c[7], fx_frac(X), fx_frac(Y),
+                   fx_frac(Z));
+}
 
 template <typename T>
 __device__ __forceinline__ float to_f32(unsigned short raw);
@@ -99,6 +146,19 @@ struct SamplerBrick {
         const long long brick = ((long long)bz * nby + by) * nbx + bx;
         const unsigned short *p = v + (brick * kBrickElems + (((z & 31) + 1) * S + ((y & 31) + 1)) * S + (x & 31) + 1);
         return to_f32<T>(__ldg(p));
+    }
+
+    __device__ __forceinline__ void corners(int ix, int iy, int iz, float c[8]) const
+    {
+        const unsigned short *p = cell(ix, iy, iz);
+        c[0] = to_f32<T>(__ldg(p));
+        c[1] = to_f32<T>(__ldg(p + 1));
+        c[2] = to_f32<T>(__ldg(p + S));
+        c[3] = to_f32<T>(__ldg(p + S + 1));
+        c[4] = to_f32<T>(__ldg(p + S * S));
+        c[5] = to_f32<T>(__ldg(p + S * S + 1));
+        c[6] = to_f32<T>(__ldg(p + S * S + S));
+        c[7] = to_f32<T>(__ldg(p + S * S + S + 1));
     }
 
     __device__ __forceinline__ float trilinear(long long X, long long Y, long long Z) const

@@ -13,8 +13,10 @@
 //   4. z-pass from the ring once it is full, written straight to HBM.
 // Neighbouring CTAs sweep z in lockstep, so their halo reads hit L2.
 #include <cmath>
+#include <cstdlib>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace shw {
 
@@ -81,6 +83,205 @@ __global__ void __launch_bounds__(32 * (32 / YB)) smooth_kernel(const float *__r
     }
 }
 
+// ---------------------------------------------------------------------------
+// TMA pipeline (radius 1..8, nx a multiple of 4, 16-byte aligned cube).
+//
+// Per CTA: a 32 x 32 (x, y) output block and a chunk of z planes.  One thread
+// issues cp.async.bulk.tensor loads of the (32+16) x (32+2r) input tile of each
+// plane into a 3-stage shared ring, signalled through mbarriers; the box's
+// x start (x0 - 8) keeps the TMA coordinate 16-byte aligned.  Out-of-range
+// elements arrive as zeros and, in blocks touching the cube's faces, are replaced
+// by the edge values (clamp-to-edge).  Then:
+//   x-pass: each thread makes 4 consecutive outputs of a row from 5 float4 reads;
+//   y-pass: each thread makes 2 rows x 2 adjacent columns with packed FP32x2 FMAs
+//           (__ffma2_rn, rounding identical to two scalar FMAs);
+//   z-pass: from a ring of the last 2r+1 y-pass results held in registers and
+//           indexed at compile time (the z loop is unrolled 2r+1 times), written
+//           straight to HBM as float2.
+constexpr int kSmTX = 32, kSmTY = 32, kSmXP = 8, kSmBW = kSmTX + 2 * kSmXP, kSmStages = 3, kSmThreads = 256;
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// Replace the zero-filled out-of-range border of a staged tile by the edge values
+// (clamp-to-edge): first the columns outside [c_lo, c_hi], then whole rows outside
+// [r_lo, r_hi].  Only the out-of-range elements are touched.
+template <int IH>
+__device__ __forceinline__ void clamp_tile_edges(float *tile, int c_lo, int c_hi, int r_lo, int r_hi, int tid)
+{
+    const int nl = c_lo, nr = kSmBW - 1 - c_hi, ncol = nl + nr;
+    if (ncol > 0) {
+        for (int e = tid; e < IH * ncol; e += kSmThreads) {
+            const int r = e / ncol, j = e - r * ncol;
+            const int c = j < nl ? j : c_hi + 1 + (j - nl);
+            tile[r * kSmBW + c] = tile[r * kSmBW + (j < nl ? c_lo : c_hi)];
+        }
+        __syncthreads();
+    }
+    const int nt = r_lo, nb = IH - 1 - r_hi, nrow = nt + nb;
+    if (nrow > 0) {
+        for (int e = tid; e < nrow * kSmBW; e += kSmThreads) {
+            const int j = e / kSmBW, c = e - j * kSmBW;
+            const int r = j < nt ? j : r_hi + 1 + (j - nt);
+            tile[r * kSmBW + c] = tile[(j < nt ? r_lo : r_hi) * kSmBW + c];
+        }
+        __syncthreads();
+    }
+}
+
+#ifndef SHW_SMOOTH_MINB
+#define SHW_SMOOTH_MINB 2
+#endif
+
+template <int R>
+__global__ void __launch_bounds__(kSmThreads, SHW_SMOOTH_MINB)
+    smooth_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict__ out, int nx, int ny, int nz,
+                      int zchunk, SmoothWeights W, unsigned *err)
+{
+    constexpr int IH = kSmTY + 2 * R, K = 2 * R + 1;
+    constexpr int STAGE_FLOATS = IH * kSmBW;
+    constexpr uint32_t STAGE_BYTES = STAGE_FLOATS * 4;
+    extern __shared__ __align__(128) float smem[];
+    float *s_in = smem;                             // [stages][IH][BW]
+    float *s_xp = smem + kSmStages * STAGE_FLOATS;  // [2][IH][TX]
+    __shared__ __align__(8) uint64_t bars[kSmStages];
+
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * kSmTX, y0 = blockIdx.y * kSmTY;
+    const int zb = blockIdx.z * zchunk, ze = min(zb + zchunk, nz);
+    const int zfirst = zb - R, nplanes = (ze + R) - zfirst;
+    const size_t plane = (size_t)nx * ny;
+
+    if (tid == 0) {
+        for (int s = 0; s < kSmStages; ++s) mbar_init(&bars[s], 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int s = 0; s < kSmStages && s < nplanes; ++s) {
+            mbar_arrive_expect_tx(&bars[s], STAGE_BYTES);
+            tma_load_3d(s_in + s * STAGE_FLOATS, &tmap, x0 - kSmXP, y0 - R, min(max(zfirst + s, 0), nz - 1),
+                        &bars[s]);
+        }
+    }
+    // clamp-to-edge bounds inside the tile (columns / rows that hold real data)
+    const int c_lo = max(0, kSmXP - x0), c_hi = min(kSmBW - 1, nx - 1 - (x0 - kSmXP));
+    const int r_lo = max(0, R - y0), r_hi = min(IH - 1, ny - 1 - (y0 - R));
+    const bool edge = c_lo > 0 || c_hi < kSmBW - 1 || r_lo > 0 || r_hi < IH - 1;
+
+    // y/z passes: each thread owns columns 2cp, 2cp+1 of rows 2rg, 2rg+1, kept as
+    // float2 pairs so that packed FP32x2 FMAs need no operand shuffling
+    const int lane = tid & 31, cp = lane & 15, rg = (lane >> 4) + 2 * (tid >> 5);
+    const int gx = x0 + 2 * cp;
+    float2 ring[2][K];
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int k = 0; k < K; ++k) ring[j][k] = make_float2(0.0f, 0.0f);
+
+    bool failed = false;
+    for (int base = 0; base < nplanes && !failed; base += K) {
+#pragma unroll
+        for (int slot = 0; slot < K; ++slot) {
+            const int i = base + slot;
+            if (i >= nplanes) break;
+            const int stage = i % kSmStages;
+            const bool ok = mbar_wait(&bars[stage], (uint32_t)((i / kSmStages) & 1), err);
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            float *tile = s_in + stage * STAGE_FLOATS;
+            if (edge) clamp_tile_edges<IH>(tile, c_lo, c_hi, r_lo, r_hi, tid);
+            float *xp = s_xp + (i & 1) * IH * kSmTX;
+            // x-pass: unit u -> row u/8, outputs 4q .. 4q+3 with q = u%8
+            for (int u = tid; u < IH * 8; u += kSmThreads) {
+                const int r = u >> 3, q = u & 7;
+                const float4 *src = reinterpret_cast<const float4 *>(tile + r * kSmBW + 4 * q);
+                float v[20];
+#pragma unroll
+                for (int t = 0; t < 5; ++t) {
+                    const float4 f = src[t];
+                    v[4 * t] = f.x;
+                    v[4 * t + 1] = f.y;
+                    v[4 * t + 2] = f.z;
+                    v[4 * t + 3] = f.w;
+                }
+                float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[j] = __fmaf_rn(W.w[k], v[kSmXP - R + j + k], acc[j]);
+                *reinterpret_cast<float4 *>(xp + r * kSmTX + 4 * q) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+            }
+            __syncthreads();
+            // the stage is consumed: refill it with plane i + stages
+            if (tid == 0 && i + kSmStages < nplanes) {
+                mbar_arrive_expect_tx(&bars[stage], STAGE_BYTES);
+                tma_load_3d(tile, &tmap, x0 - kSmXP, y0 - R, min(max(zfirst + i + kSmStages, 0), nz - 1),
+                            &bars[stage]);
+            }
+            // y-pass into the ring slot of this plane
+            const float2 *xp2 = reinterpret_cast<const float2 *>(xp);
+            float2 col[2 + 2 * R];
+#pragma unroll
+            for (int m = 0; m < 2 + 2 * R; ++m) col[m] = xp2[(2 * rg + m) * (kSmTX / 2) + cp];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int k = 0; k < K; ++k) acc = __ffma2_rn(f2(W.w[k]), col[j + k], acc);
+                ring[j][slot] = acc;
+            }
+            // z-pass: the ring holds planes i-2R .. i (oldest in slot (slot+1) mod K)
+            if (i >= 2 * R) {
+                const int zo = zfirst + i - R;
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int gy = y0 + 2 * rg + j;
+                    float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+                    for (int k = 0; k < K; ++k) acc = __ffma2_rn(f2(W.w[k]), ring[j][(slot + 1 + k) % K], acc);
+                    if (gx < nx && gy < ny)
+                        *reinterpret_cast<float2 *>(out + (size_t)zo * plane + (size_t)gy * nx + gx) = acc;
+                }
+            }
+        }
+    }
+    if (failed && tid == 0) {
+        // drain: wait (bounded) for this CTA's copies still in flight before leaving
+        for (int s = 0; s < kSmStages; ++s) mbar_wait(&bars[s], 0u, nullptr), mbar_wait(&bars[s], 1u, nullptr);
+    }
+}
+
+template <int R>
+static size_t smooth_tma_smem()
+{
+    return (size_t)(kSmStages * (kSmTY + 2 * R) * kSmBW + 2 * (kSmTY + 2 * R) * kSmTX) * 4;
+}
+
+static int smooth_zchunk(int nx, int ny, int nz, int r)
+{
+    const long long tiles = (long long)ceil_div(nx, 32) * ceil_div(ny, 32);
+    int zc = nz < 128 ? nz : 128;
+    const int zmin = (4 * r > 16) ? 4 * r : 16;
+    while (tiles * ceil_div(nz, zc) < 608 && zc / 2 >= zmin) zc /= 2;
+    return zc;
+}
+
+template <int R>
+static bool launch_smooth_tma(const float *in, float *out, int nx, int ny, int nz, const SmoothWeights &w,
+                              cudaStream_t st)
+{
+    CUtensorMap map;
+    if (!encode_tmap_3d_f32(&map, in, nx, ny, nz, kSmBW, kSmTY + 2 * R)) return false;
+    unsigned *err = device_error_word();
+    const size_t smem = smooth_tma_smem<R>();
+    const int zc = smooth_zchunk(nx, ny, nz, R);
+    const dim3 grid((unsigned)ceil_div(nx, kSmTX), (unsigned)ceil_div(ny, kSmTY), (unsigned)ceil_div(nz, zc));
+    smooth_tma_kernel<R><<<grid, kSmThreads, smem, st>>>(map, out, nx, ny, nz, zc, w, err);
+    return true;
+}
+
 template <int R>
 static void launch_smooth_r(const float *in, float *out, int nx, int ny, int nz, const SmoothWeights &w,
                             cudaStream_t st)
@@ -98,6 +299,17 @@ static void launch_smooth_r(const float *in, float *out, int nx, int ny, int nz,
 static shw_status smooth_dispatch(const float *in, float *out, int nx, int ny, int nz, const SmoothWeights &w,
                                   int r, cudaStream_t st)
 {
+    // TMA pipeline where its alignment rules hold, the staged kernel otherwise
+    if (r >= 1 && r <= 8 && nx % 4 == 0 && aligned(in, 16) && !std::getenv("SHW_SMOOTH_NO_TMA")) {
+        bool ok = false;
+        switch (r) {
+#define SHW_T(n) \
+    case n: ok = launch_smooth_tma<n>(in, out, nx, ny, nz, w, st); break;
+            SHW_T(1) SHW_T(2) SHW_T(3) SHW_T(4) SHW_T(5) SHW_T(6) SHW_T(7) SHW_T(8)
+#undef SHW_T
+        }
+        if (ok) return after_launch();
+    }
     switch (r) {
 #define SHW_R(n) \
     case n: launch_smooth_r<n>(in, out, nx, ny, nz, w, st); break;

@@ -1,0 +1,77 @@
+// tma.cuh -- Tensor Memory Accelerator loads (cp.async.bulk.tensor) with mbarrier
+// completion, written as inline PTX, plus the host-side tensor-map encoder.
+//
+// Every wait is bounded: if a barrier phase does not complete within the limit the
+// waiting thread records it in the library's device error word (reported by
+// shw_sync_status as SHW_ETIMEOUT) and the caller abandons its work.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace shw {
+
+constexpr unsigned kErrWaitTimeout = 1u;
+constexpr int kWaitSpins = 1 << 22;  // try_wait already suspends in hardware between polls
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// make barrier initialisation visible to the async (TMA) proxy
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// One 3-D box of a tensor map into shared memory; completion is signalled on `bar`.
+// The innermost coordinate x times the element size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of `bar`; false (and the error word set) after kWaitSpins polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned *err)
+{
+    for (int i = 0; i < kWaitSpins; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    if (err) atomicOr(err, kErrWaitTimeout);
+    return false;
+}
+
+// host: the library's device error word on the current device (nullptr if unavailable)
+unsigned *device_error_word();
+
+// host: encode a 3-D float32 tile map over a [nz][ny][nx] array with box {bx, by, 1};
+// out-of-bounds elements of a box read as zero.  Returns false if the driver refuses.
+bool encode_tmap_3d_f32(CUtensorMap *map, const float *base, int nx, int ny, int nz, int bx, int by);
+
+}  // namespace shw

@@ -20,9 +20,12 @@ def _gpu_smooth(m, cube, sigma, r):
     return out.cpu().numpy()
 
 
+# (nx % 4 == 0 and 1 <= r <= 8 take the TMA pipeline; the others the staged kernel)
 @pytest.mark.parametrize("dims,sigma,r", [((45, 37, 29), 1.0, 3), ((64, 64, 64), 1.0, 3), ((70, 33, 90), 2.0, 6),
                                          ((31, 40, 17), 0.8, 0), ((50, 50, 50), 5.0, 16), ((33, 65, 40), 3.0, 9),
-                                         ((5, 3, 2), 1.5, 4)])
+                                         ((5, 3, 2), 1.5, 4), ((44, 37, 29), 1.0, 3), ((68, 33, 90), 2.0, 6),
+                                         ((36, 70, 20), 2.7, 8), ((4, 5, 3), 0.6, 1), ((12, 64, 130), 1.7, 5),
+                                         ((96, 40, 300), 2.0, 6), ((8, 8, 8), 3.0, 8)])
 def test_smooth_parity(m, dims, sigma, r):
     cube = scene.tiny_cube(config_id=21, dims=dims, n_sources=2)
     g = _gpu_smooth(m, cube, sigma, r)
@@ -61,3 +64,11 @@ def test_smooth_nan_propagates_locally(m):
     assert np.array_equal(np.isnan(g), np.isnan(o))
     ok = ~np.isnan(o)
     assert np.abs(g[ok] - o[ok]).max() <= TOL_F32 * float(np.nanmax(cube) - np.nanmin(cube))
+
+
+def test_smooth_tma_and_staged_paths_agree(m, monkeypatch):
+    cube = scene.tiny_cube(config_id=24, dims=(68, 52, 75), n_sources=2)
+    a = _gpu_smooth(m, cube, 2.0, 6)
+    monkeypatch.setenv("SHW_SMOOTH_NO_TMA", "1")
+    b = _gpu_smooth(m, cube, 2.0, 6)
+    assert np.abs(a - b).max() <= 1e-6 * float(cube.max() - cube.min())
