@@ -120,6 +120,9 @@ static int clip_ray(const int n[3], const double o[3], const double d[3], double
     for (int a = 0; a < 3; ++a) {
         double lo = -0.5, hi = n[a] - 0.5;
         if (d[a] == 0.0) {
+            /* a ray lying on a face of the box: inside or outside is a rounding decision */
+            if (frag && eps > 0.0 && (fabs(o[a] - lo) < eps || fabs(o[a] - hi) < eps))
+                *frag |= FRAG_COUNT;
             if (o[a] < lo || o[a] > hi)
                 return 0;
             continue;
@@ -210,9 +213,32 @@ typedef struct {
     const double *lut;
 } oparams;
 
+/* A trilinear sample is NaN when any corner of its cell is; at a cell face next to a
+ * NaN voxel, which cell the position falls in -- and so whether the sample is NaN --
+ * is a rounding decision.  Flag samples within eps of such a face. */
+static void nan_face_check(const ovol *V, const double p[3], double v, double eps, int *frag)
+{
+    for (int a = 0; a < 3; ++a) {
+        if (dist_to_int(p[a]) >= eps)
+            continue;
+        double q[3] = {p[0], p[1], p[2]};
+        q[a] = p[a] + eps;
+        int n1 = isnan(sample_trilinear(V, q));
+        q[a] = p[a] - eps;
+        int n2 = isnan(sample_trilinear(V, q));
+        if (n1 != isnan(v) || n2 != isnan(v))
+            *frag |= FRAG_ROUND;
+    }
+}
+
 static double fetch(const ovol *V, int interp, const double p[3], double eps, int *frag)
 {
-    return interp == OR_NEAREST ? sample_nearest(V, p, eps, frag) : sample_trilinear(V, p);
+    if (interp == OR_NEAREST)
+        return sample_nearest(V, p, eps, frag);
+    double v = sample_trilinear(V, p);
+    if (frag && eps > 0.0)
+        nan_face_check(V, p, v, eps, frag);
+    return v;
 }
 
 /* The sample's z coordinate as used by spectral-position colouring: the channel of
