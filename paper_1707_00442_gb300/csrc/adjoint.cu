@@ -21,6 +21,14 @@
 namespace shw {
 
 constexpr int kMaxCkptInterval = 64;
+constexpr int kBwdThreads = 256, kBwdTile = 16;  // 16 x 16 pixels per CTA, 8 x 4 per warp
+
+__device__ __forceinline__ void bwd_pixel(int &px, int &py)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    px = blockIdx.x * kBwdTile + (warp & 1) * 8 + (lane & 7);
+    py = blockIdx.y * kBwdTile + (warp >> 1) * 4 + (lane >> 3);
+}
 
 struct BackwardArgs {
     const float4 *grad_rgba;  // [H][W]
@@ -55,7 +63,7 @@ __device__ __forceinline__ void scatter_trilinear(float *gv, int nx, int ny, int
 }
 
 template <int INTERP>
-__global__ void __launch_bounds__(kRenderThreads) backward_kernel(SamplerF32<long long> s, shw_camera cam,
+__global__ void __launch_bounds__(kBwdThreads) backward_kernel(SamplerF32<long long> s, shw_camera cam,
                                                                    BackwardArgs a)
 {
     __shared__ float4 lut_s[kLut];
@@ -68,7 +76,7 @@ __global__ void __launch_bounds__(kRenderThreads) backward_kernel(SamplerF32<lon
 
     float gs = 0.0f;
     int px, py;
-    tile_pixel(px, py, 3);
+    bwd_pixel(px, py);
     if (px < a.width && py < a.height) {
         const long long pix = (long long)py * a.width + px;
         const long long npix = (long long)a.width * a.height;
@@ -207,11 +215,11 @@ extern "C" shw_status shw_render_backward(const shw_volume *vol, const shw_camer
     a.opacity_scale = p->opacity_scale;
     SamplerF32<long long> s{static_cast<const float *>(vol->data), vol->nx, vol->ny, vol->nz, (long long)vol->nx,
                             (long long)vol->nx * vol->ny};
-    const dim3 grid((unsigned)ceil_div(cam->width, kTileX), (unsigned)ceil_div(cam->height, kTileY));
+    const dim3 grid((unsigned)ceil_div(cam->width, kBwdTile), (unsigned)ceil_div(cam->height, kBwdTile));
     cudaStream_t st = as_stream(stream);
     if (p->interp == SHW_NEAREST)
-        backward_kernel<SHW_NEAREST><<<grid, kRenderThreads, 0, st>>>(s, *cam, a);
+        backward_kernel<SHW_NEAREST><<<grid, kBwdThreads, 0, st>>>(s, *cam, a);
     else
-        backward_kernel<SHW_TRILINEAR><<<grid, kRenderThreads, 0, st>>>(s, *cam, a);
+        backward_kernel<SHW_TRILINEAR><<<grid, kBwdThreads, 0, st>>>(s, *cam, a);
     return after_launch();
 }

@@ -224,6 +224,9 @@ shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_c
     }
     const shw_volume *v2 = (p->mode == SHW_RATIO) ? vol2 : nullptr;
     cudaStream_t st = as_stream(stream);
+    // orthographic views down the spectral axis: the plane sweep, when it applies
+    const shw_status sa = render_axis(p->mode, p->interp, *vol, *cam, a, st);
+    if (sa != SHW_EUNSUPPORTED) return sa;
     switch (vol->storage) {
     case SHW_F32: return render_f32(p->mode, p->interp, *vol, v2, *cam, a, st);
     case SHW_BF16_BRICK: return render_bf16(p->mode, p->interp, *vol, v2, *cam, a, st);

@@ -1,9 +1,15 @@
 // render_impl.cuh -- the ray marcher: one thread per pixel (= one ray, the
 // fragment of Section 2.3), Algorithm 1's loop with one transfer function.
 //
-// Thread layout: a CTA of 256 threads renders a 16 x 16 pixel tile; each warp
-// owns an 8 x 4 sub-tile so that its 32 rays stay close in 3-D and their loads
-// share cache lines.
+// Thread layout: a CTA of 64 threads (two warps) renders a small pixel tile, so the
+// hardware's CTA scheduler balances rays of very different lengths finely.  A warp
+// covers a 16 x 2, 2 x 16 or 8 x 4 pixel tile, elongated along the image axis that
+// runs closest to the cube's contiguous x axis so its loads share cache lines.
+//
+// Per ray: an FP32 test rejects rays that clearly miss the box; the exact set-up
+// (float-float, ray.cuh) gives N and the fixed-point start and step; the samples
+// are split into a clamped head, a clamp-free interior (cells in [0, n-2] on
+// every axis, verified exactly in integer arithmetic) and a clamped tail.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -24,13 +30,21 @@ struct RenderArgs {
     const float4 *lut;  // [256]
     int width, height;
     int nckpt, ckpt_interval;
-    int nmax;  // upper bound of N over all rays (box diagonal / step + 1)
-    int warp_shift;
+    int nmax;        // upper bound of N over all rays (box diagonal / step + 1)
+    int warp_shift;  // log2 of the warp tile's width
+    int tiles_x, tiles_y;  // CTA tiles per image row / column
+    int ctx, cty;          // the tile holding the projected cube centre (dispatched first)
     float step, lo, inv_range, opacity_scale, term_alpha, ratio_floor;
     int nz;
 };
 
-constexpr int kTileX = 16, kTileY = 16, kRenderThreads = 256;
+#ifndef SHW_CTA_WARPS
+#define SHW_CTA_WARPS 2
+#endif
+#ifndef SHW_LUT_SMEM
+#define SHW_LUT_SMEM 0  // 1: compositing stages the colour map in shared memory; 0: reads it through L1
+#endif
+constexpr int kCtaWarps = SHW_CTA_WARPS, kRenderThreads = 32 * SHW_CTA_WARPS;
 #ifndef SHW_WARP_SHIFT
 #define SHW_WARP_SHIFT -1  // -1: chosen per launch from the camera; else log2 of the warp tile width
 #endif
@@ -51,34 +65,221 @@ __device__ __forceinline__ float normalise(float v, float lo, float inv_range)
     return fminf(fmaxf((v - lo) * inv_range, 0.0f), 1.0f);
 }
 
-// Pixel of this thread.  A warp covers a (2^ws) x (32 / 2^ws) pixel tile: ws = 4 (16 x 2)
-// or 1 (2 x 16) when rows or columns of the image run close to the cube's x axis
-// (the contiguous one, so a warp's loads share cache lines), ws = 3 (8 x 4) otherwise.
-__device__ __forceinline__ void tile_pixel(int &px, int &py, int ws)
+// CTA tile: the CTA's warps stacked across the warp tile's short side.
+__host__ __device__ __forceinline__ void cta_tile(int ws, int &tw, int &th)
 {
-    const int wtx = 1 << ws, wty = 32 >> ws, wpr = kTileX >> ws;  // warps per tile row
+    const int wtx = 1 << ws, wty = 32 >> ws;
+    tw = wtx >= wty ? wtx : kCtaWarps * wtx;
+    th = wtx >= wty ? kCtaWarps * wty : wty;
+}
+
+// k-th element of c, c-1, c+1, c-2, c+2, ... restricted to [0, n): a centre-out order
+__host__ __device__ __forceinline__ int centre_out(int k, int c, int n)
+{
+    const int m = c < n - 1 - c ? c : n - 1 - c;  // rings that fit on both sides
+    if (k <= 2 * m) return (k & 1) ? c - (k + 1) / 2 : c + k / 2;
+    const int rest = k - 2 * m;  // then the longer side, moving outwards
+    return c - m > 0 ? c - m - rest : c + m + rest;
+}
+
+// Tiles are dispatched centre-out (rows, then columns within a row, from the tile
+// under the projected cube centre), so the longest rays start first and short or
+// empty tiles fill the end of the launch.
+__device__ __forceinline__ void tile_pixel(int &px, int &py, const RenderArgs &a)
+{
+    const int ws = a.warp_shift, wtx = 1 << ws, wty = 32 >> ws;
+    int tw, th;
+    cta_tile(ws, tw, th);
+    const int rank = blockIdx.x, rr = rank / a.tiles_x, cr = rank - rr * a.tiles_x;
+    const int ty = centre_out(rr, a.cty, a.tiles_y), tx = centre_out(cr, a.ctx, a.tiles_x);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    px = blockIdx.x * kTileX + (warp % wpr) * wtx + (lane & (wtx - 1));
-    py = blockIdx.y * kTileY + (warp / wpr) * wty + (lane >> ws);
+    px = tx * tw + (wtx >= wty ? 0 : warp * wtx) + (lane & (wtx - 1));
+    py = ty * th + (wtx >= wty ? warp * wty : 0) + (lane >> ws);
+}
+
+// Conservative FP32 rejection: true only if the ray surely misses the box (the box
+// is widened by a margin far larger than the FP32 error of the ray).
+__device__ __forceinline__ bool quick_miss(const shw_camera &c, int px, int py, int nx, int ny, int nz)
+{
+    const float W = (float)c.width, H = (float)c.height;
+    const float xs = (float)(2 * px + 1 - c.width) / W, ys = (float)(c.height - 2 * py - 1) / H;
+    const float aspect = W / H;
+    float o[3], d[3];
+    if (c.ortho) {
+        const float sx = xs * c.ortho_half_h * aspect, sy = ys * c.ortho_half_h;
+        for (int k = 0; k < 3; ++k) {
+            o[k] = c.eye[k] + sx * c.right[k] + sy * c.up[k];
+            d[k] = c.fwd[k];
+        }
+    } else {
+        const float tx = xs * c.tan_half_fovy * aspect, ty = ys * c.tan_half_fovy;
+        for (int k = 0; k < 3; ++k) {
+            o[k] = c.eye[k];
+            d[k] = c.fwd[k] + tx * c.right[k] + ty * c.up[k];
+        }
+    }
+    const int n[3] = {nx, ny, nz};
+    float tmin = -INFINITY, tmax = INFINITY;
+    for (int k = 0; k < 3; ++k) {
+        const float m = 0.05f + 1e-5f * fabsf(o[k]);
+        const float lo = -0.5f - m, hi = (float)n[k] - 0.5f + m;
+        if (d[k] == 0.0f) {
+            if (o[k] < lo || o[k] > hi) return true;
+            continue;
+        }
+        const float t1 = (lo - o[k]) / d[k], t2 = (hi - o[k]) / d[k];
+        tmin = fmaxf(tmin, fminf(t1, t2));
+        tmax = fminf(tmax, fmaxf(t1, t2));
+    }
+    return tmax < tmin || tmax < 0.0f;
+}
+
+// Samples k in [ka, kb) whose cells lie in [0, n-2] on every axis.  An FP32
+// estimate, then exact integer checks of both ends (cells move monotonically along
+// a ray, so valid ends make the whole range valid).  Empty range: ka = kb = N.
+__device__ __forceinline__ void interior_range(const RayFx &r, int nx, int ny, int nz, int N, int &ka, int &kb)
+{
+    const int n[3] = {nx, ny, nz};
+    ka = 0;
+    kb = N;
+    for (int a = 0; a < 3; ++a) {
+        const long long P = r.P[a], D = r.D[a], U = (long long)(n[a] - 1) << 32;
+        if (D == 0) {
+            if (!(P >= 0 && P < U)) {
+                ka = kb = N;
+                return;
+            }
+            continue;
+        }
+        const float p = __ll2float_rn(P) * 2.3283064365386963e-10f, d = __ll2float_rn(D) * 2.3283064365386963e-10f;
+        const float u = (float)(n[a] - 1);
+        const float t0 = (d > 0.0f ? -p : u - p) / d, t1 = (d > 0.0f ? u - p : -p) / d;
+        ka = max(ka, (int)fminf(fmaxf(ceilf(t0), 0.0f), (float)N));
+        kb = min(kb, (int)fminf(fmaxf(ceilf(t1), 0.0f), (float)N));
+    }
+    auto inside = [&](int k) {
+        bool ok = true;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const long long q = r.P[a] + (long long)k * r.D[a];
+            ok = ok && q >= 0 && q < ((long long)(n[a] - 1) << 32);
+        }
+        return ok;
+    };
+    for (int i = 0; i < 4 && ka < kb && !inside(ka); ++i) ++ka;
+    for (int i = 0; i < 4 && kb > ka && !inside(kb - 1); ++i) --kb;
+    if (ka >= kb || !inside(ka) || !inside(kb - 1)) ka = kb = N;
 }
 
 template <int INTERP, class S>
 __device__ __forceinline__ float fetch(const S &s, long long X, long long Y, long long Z)
 {
     if constexpr (INTERP == SHW_NEAREST)
-        return s.nearest(X, Y, Z);
+        return s.template nearest<true>(X, Y, Z);
     else
         return s.trilinear(X, Y, Z);
 }
 
-// the marcher's fetch: with SHW_CELL_CACHE, trilinear samples reuse the previous cell's corners
-template <int INTERP, class S>
-__device__ __forceinline__ float fetch_c(const S &s, long long X, long long Y, long long Z, CellCache &cc)
+template <bool CLAMP, int INTERP, class S>
+__device__ __forceinline__ float sample(const S &s, long long X, long long Y, long long Z, CellCache &cc)
 {
-    if constexpr (INTERP == SHW_TRILINEAR && SHW_CELL_CACHE)
-        return trilinear_cached(s, X, Y, Z, cc);
+    if constexpr (INTERP == SHW_NEAREST)
+        return s.template nearest<CLAMP>(X, Y, Z);
     else
-        return fetch<INTERP>(s, X, Y, Z);
+        return trilinear_cached<CLAMP>(s, X, Y, Z, cc);
+}
+
+// ---- transfer-function state per mode --------------------------------------
+
+// Eq. 1 / Algorithms 2, 4, 14: running maximum with ">=" (the last maximum wins)
+struct MaxState {
+    float m = -INFINITY;
+    int kmax = 0;
+    __device__ __forceinline__ bool update(float v, int k)
+    {
+        if (v >= m) {
+            m = v;
+            kmax = k;
+        }
+        return false;
+    }
+};
+
+// Eq. 3 divided by N; compensated (Kahan) summation keeps FP32 accurate
+struct AvgState {
+    float sum = 0.0f, comp = 0.0f;
+    __device__ __forceinline__ bool update(float v, int)
+    {
+        const float y = __fsub_rn(v, comp);
+        const float t = __fadd_rn(sum, y);
+        comp = __fsub_rn(__fsub_rn(t, sum), y);
+        sum = t;
+        return false;
+    }
+};
+
+// Algorithm 3 in premultiplied form; stops after the sample that makes alpha > term
+struct CompositeState {
+    float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
+    const float4 *lut;
+    float lo, inv_range, s, term;
+    float *ckpt;  // this ray's first checkpoint slot, or null
+    long long ckpt_stride;
+    int I, nckpt;
+    __device__ __forceinline__ bool update(float v, int k)
+    {
+        if (ckpt != nullptr && (k % I) == 0 && k / I < nckpt) ckpt[(long long)(k / I) * ckpt_stride] = T;
+        const float4 c = lut_eval(lut, normalise(v, lo, inv_range));
+        const float al = fminf(fmaxf(s * c.w, 0.0f), 1.0f);
+        const float w = T * al;
+        cr = __fmaf_rn(w, c.x, cr);
+        cg = __fmaf_rn(w, c.y, cg);
+        cb = __fmaf_rn(w, c.z, cb);
+        T = T * (1.0f - al);
+        return 1.0f - T > term;
+    }
+};
+
+template <int MODE>
+struct StateOf {
+    using type = MaxState;
+};
+template <>
+struct StateOf<SHW_AVG> {
+    using type = AvgState;
+};
+template <>
+struct StateOf<SHW_COMPOSITE> {
+    using type = CompositeState;
+};
+
+// Samples [k0, k1) of one ray; true if the transfer function stopped the ray
+// (then kdone = samples processed).  X, Y, Z advance with the samples.
+template <bool CLAMP, int MODE, int INTERP, class S, class St>
+__device__ __forceinline__ bool march(const S &s, const S &s2, const RenderArgs &a, St &st, CellCache &cc,
+                                      CellCache &cc2, long long &X, long long &Y, long long &Z, long long DX,
+                                      long long DY, long long DZ, int k0, int k1, int &kdone)
+{
+    for (int k = k0; k < k1; ++k) {
+        float v;
+        if constexpr (MODE == SHW_RATIO) {
+            // Algorithm 14: ratio where cube1 exceeds the floor, else DATAMIN
+            const float c1 = sample<CLAMP, INTERP>(s, X, Y, Z, cc), c2 = sample<CLAMP, INTERP>(s2, X, Y, Z, cc2);
+            v = (c1 > a.ratio_floor) ? __fdiv_rn(c2, c1) : a.lo;
+        } else {
+            v = sample<CLAMP, INTERP>(s, X, Y, Z, cc);
+        }
+        v = isnan(v) ? a.lo : v;  // a NaN sample counts as DATAMIN
+        if (st.update(v, k)) {
+            kdone = k + 1;
+            return true;
+        }
+        X += DX;
+        Y += DY;
+        Z += DZ;
+    }
+    kdone = k1;
+    return false;
 }
 
 // One ray of Algorithm 1 with the transfer function MODE.  lut_c: the colour map in
@@ -91,103 +292,60 @@ __device__ __forceinline__ void render_pixel(const S &s, const S &s2, const shw_
     const long long npix = (long long)a.width * a.height;
 
     RayFx r;
-    const bool hit = setup_ray(cam, px, py, s.nx, s.ny, s.nz, a.step, r);
+    const bool hit = !quick_miss(cam, px, py, s.nx, s.ny, s.nz) && setup_ray(cam, px, py, s.nx, s.ny, s.nz, a.step, r);
     const int N = hit ? min(r.N, a.nmax) : 0;
-
-    long long X = r.P[0], Y = r.P[1], Z = r.P[2];
-    const long long DX = r.D[0], DY = r.D[1], DZ = r.D[2];
 
     float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
     float scalar = 0.0f;
     int index = -1;
     int done = 0;
-
-    if constexpr (MODE == SHW_MIP || MODE == SHW_SPECTRAL || MODE == SHW_RATIO) {
-        float m = -INFINITY;
-        int kmax = 0;
-        CellCache cc, cc2;
-        for (int k = 0; k < N; ++k) {
-            float v;
-            if constexpr (MODE == SHW_RATIO) {
-                // Algorithm 14: ratio where cube1 exceeds the floor, else DATAMIN
-                const float c1 = fetch_c<INTERP>(s, X, Y, Z, cc), c2 = fetch_c<INTERP>(s2, X, Y, Z, cc2);
-                v = (c1 > a.ratio_floor) ? __fdiv_rn(c2, c1) : a.lo;
-            } else {
-                v = fetch_c<INTERP>(s, X, Y, Z, cc);
-            }
-            v = isnan(v) ? a.lo : v;
-            if (v >= m) {  // Eq. 1: ">=", the last maximum along the ray wins
-                m = v;
-                kmax = k;
-            }
-            X += DX;
-            Y += DY;
-            Z += DZ;
+    if (N > 0) {
+        int ka, kb;
+        interior_range(r, s.nx, s.ny, s.nz, N, ka, kb);
+        long long X = r.P[0], Y = r.P[1], Z = r.P[2];
+        const long long DX = r.D[0], DY = r.D[1], DZ = r.D[2];
+        typename StateOf<MODE>::type st;
+        if constexpr (MODE == SHW_COMPOSITE) {
+            st.lut = lut_c;
+            st.lo = a.lo;
+            st.inv_range = a.inv_range;
+            st.s = a.opacity_scale;
+            st.term = a.term_alpha;
+            st.ckpt = a.ckpt_T != nullptr ? a.ckpt_T + pix : nullptr;
+            st.ckpt_stride = npix;
+            st.I = a.ckpt_interval;
+            st.nckpt = a.nckpt;
         }
-        done = N;
-        if (N > 0) {
-            const long long Zm = r.P[2] + (long long)kmax * DZ;
+        CellCache cc, cc2;
+        bool stop = march<true, MODE, INTERP>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, 0, ka, done);
+        if (!stop) stop = march<false, MODE, INTERP>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, ka, kb, done);
+        if (!stop) march<true, MODE, INTERP>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, kb, N, done);
+
+        if constexpr (MODE == SHW_MIP || MODE == SHW_SPECTRAL || MODE == SHW_RATIO) {
+            const long long Zm = r.P[2] + (long long)st.kmax * DZ;
             index = clampi(fx_round(Zm), 0, a.nz - 1);
-            scalar = m;
-            const float vh = normalise(m, a.lo, a.inv_range);
+            scalar = st.m;
+            const float vh = normalise(st.m, a.lo, a.inv_range);
             if constexpr (MODE == SHW_SPECTRAL) {
                 // Algorithm 4: colour from the spectral position, alpha from the value
-                const float zmax = (INTERP == SHW_NEAREST) ? (float)index : __ll2float_rn(Zm) * 2.3283064365386963e-10f;
+                const float zmax =
+                    (INTERP == SHW_NEAREST) ? (float)index : __ll2float_rn(Zm) * 2.3283064365386963e-10f;
                 const float tz = fminf(fmaxf((zmax + 0.5f) / (float)a.nz, 0.0f), 1.0f);
                 const float4 c = lut_eval(a.lut, tz);
                 out = make_float4(c.x, c.y, c.z, vh);
             } else {
                 out = lut_eval(a.lut, vh);
             }
-        }
-    } else if constexpr (MODE == SHW_AVG) {
-        // Eq. 3 divided by N; compensated (Kahan) summation keeps FP32 exact enough
-        float sum = 0.0f, comp = 0.0f;
-        CellCache cc;
-        for (int k = 0; k < N; ++k) {
-            float v = fetch_c<INTERP>(s, X, Y, Z, cc);
-            v = isnan(v) ? a.lo : v;
-            const float y = __fsub_rn(v, comp);
-            const float t = __fadd_rn(sum, y);
-            comp = __fsub_rn(__fsub_rn(t, sum), y);
-            sum = t;
-            X += DX;
-            Y += DY;
-            Z += DZ;
-        }
-        done = N;
-        if (N > 0) {
-            scalar = __fdiv_rn(sum, (float)N);
+        } else if constexpr (MODE == SHW_AVG) {
+            scalar = __fdiv_rn(st.sum, (float)N);
             out = lut_eval(a.lut, normalise(scalar, a.lo, a.inv_range));
+        } else {
+            out = make_float4(st.cr, st.cg, st.cb, 1.0f - st.T);
+            scalar = 1.0f - st.T;
         }
-    } else {  // SHW_COMPOSITE: Algorithm 3 in premultiplied form
-        float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
-        const int I = a.ckpt_interval;
-        int k = 0;
-        CellCache cc;
-        for (; k < N;) {
-            if (a.ckpt_T != nullptr && (k % I) == 0 && k / I < a.nckpt) a.ckpt_T[(long long)(k / I) * npix + pix] = T;
-            float v = fetch_c<INTERP>(s, X, Y, Z, cc);
-            v = isnan(v) ? a.lo : v;
-            const float4 c = lut_eval(lut_c, normalise(v, a.lo, a.inv_range));
-            const float al = fminf(fmaxf(a.opacity_scale * c.w, 0.0f), 1.0f);
-            const float w = T * al;
-            cr = __fmaf_rn(w, c.x, cr);
-            cg = __fmaf_rn(w, c.y, cg);
-            cb = __fmaf_rn(w, c.z, cb);
-            T = T * (1.0f - al);
-            ++k;
-            if (1.0f - T > a.term_alpha) break;  // early ray termination
-            X += DX;
-            Y += DY;
-            Z += DZ;
-        }
-        done = k;
-        out = make_float4(cr, cg, cb, 1.0f - T);
-        scalar = 1.0f - T;
-        if (a.ckpt_K != nullptr) a.ckpt_K[pix] = k;
     }
-
+    if constexpr (MODE == SHW_COMPOSITE)
+        if (a.ckpt_K != nullptr) a.ckpt_K[pix] = done;
     a.rgba[pix] = out;
     if (a.scalar) a.scalar[pix] = scalar;
     if (a.index) a.index[pix] = index;
@@ -198,28 +356,60 @@ template <int MODE, int INTERP, class S>
 __global__ void __launch_bounds__(kRenderThreads) render_kernel(S s, S s2, shw_camera cam, RenderArgs a)
 {
     __shared__ float4 lut_s[kLut];
-    if constexpr (MODE == SHW_COMPOSITE) {
+    const float4 *lut_c = a.lut;
+    if constexpr (MODE == SHW_COMPOSITE && SHW_LUT_SMEM) {
         for (int i = threadIdx.x; i < kLut; i += blockDim.x) lut_s[i] = a.lut[i];
         __syncthreads();
+        lut_c = lut_s;
     }
     int px, py;
-    tile_pixel(px, py, a.warp_shift);
+    tile_pixel(px, py, a);
     if (px >= a.width || py >= a.height) return;
-    render_pixel<MODE, INTERP, S>(s, s2, cam, a, lut_s, px, py);
+    render_pixel<MODE, INTERP, S>(s, s2, cam, a, lut_c, px, py);
+}
+
+// Pixel coordinates of the cube centre's projection (image centre if behind the eye).
+inline void project_centre(const shw_camera &c, int nx, int ny, int nz, float &px, float &py)
+{
+    const float q[3] = {0.5f * (nx - 1) - c.eye[0], 0.5f * (ny - 1) - c.eye[1], 0.5f * (nz - 1) - c.eye[2]};
+    const float r = q[0] * c.right[0] + q[1] * c.right[1] + q[2] * c.right[2];
+    const float u = q[0] * c.up[0] + q[1] * c.up[1] + q[2] * c.up[2];
+    const float f = q[0] * c.fwd[0] + q[1] * c.fwd[1] + q[2] * c.fwd[2];
+    const float aspect = (float)c.width / (float)c.height;
+    float xs = 0.0f, ys = 0.0f;
+    if (c.ortho) {
+        xs = r / (c.ortho_half_h * aspect);
+        ys = u / c.ortho_half_h;
+    } else if (f > 0.0f) {
+        xs = r / (f * c.tan_half_fovy * aspect);
+        ys = u / (f * c.tan_half_fovy);
+    }
+    px = 0.5f * (xs + 1.0f) * c.width;
+    py = 0.5f * (1.0f - ys) * c.height;
 }
 
 // Host-side launch for one storage type (instantiated per storage in its own TU).
 template <class S>
 shw_status launch_render_modes(int mode, int interp, const S &s, const S &s2, const shw_camera &cam,
-                               const RenderArgs &a, cudaStream_t st)
+                               const RenderArgs &a0, cudaStream_t st)
 {
-    const dim3 grid((unsigned)ceil_div(cam.width, kTileX), (unsigned)ceil_div(cam.height, kTileY));  // height <= 2^19
+    RenderArgs a = a0;
+    int tw, th;
+    cta_tile(a.warp_shift, tw, th);
+    a.tiles_x = ceil_div(cam.width, tw);
+    a.tiles_y = ceil_div(cam.height, th);
+    const long long tiles = (long long)a.tiles_x * a.tiles_y;
+    float cpx, cpy;
+    project_centre(cam, s.nx, s.ny, s.nz, cpx, cpy);
+    a.ctx = (int)fminf(fmaxf(cpx / tw, 0.0f), (float)(a.tiles_x - 1));
+    a.cty = (int)fminf(fmaxf(cpy / th, 0.0f), (float)(a.tiles_y - 1));
+    const dim3 grid((unsigned)tiles);
     const dim3 block(kRenderThreads);
 #define SHW_LAUNCH(M, I) render_kernel<M, I, S><<<grid, block, 0, st>>>(s, s2, cam, a)
-#define SHW_CASE(M)                                          \
-    case M:                                                  \
+#define SHW_CASE(M)                                            \
+    case M:                                                    \
         if (interp == SHW_NEAREST) SHW_LAUNCH(M, SHW_NEAREST); \
-        else SHW_LAUNCH(M, SHW_TRILINEAR);                   \
+        else SHW_LAUNCH(M, SHW_TRILINEAR);                     \
         break;
     switch (mode) {
         SHW_CASE(SHW_MIP)
@@ -235,7 +425,7 @@ shw_status launch_render_modes(int mode, int interp, const S &s, const S &s2, co
     return after_launch();
 }
 
-// Warp tile orientation for a camera (see tile_pixel).
+// Warp tile orientation for a camera (see the layout note at the top).
 inline int warp_shift_for(const shw_camera &c)
 {
     if (SHW_WARP_SHIFT >= 0) return SHW_WARP_SHIFT;
@@ -252,5 +442,8 @@ shw_status render_bf16(int mode, int interp, const shw_volume &v, const shw_volu
                        const RenderArgs &a, cudaStream_t st);
 shw_status render_f16(int mode, int interp, const shw_volume &v, const shw_volume *v2, const shw_camera &cam,
                       const RenderArgs &a, cudaStream_t st);
+// the plane sweep for orthographic spectral-axis views (render_axis.cu); SHW_EUNSUPPORTED if it does not apply
+shw_status render_axis(int mode, int interp, const shw_volume &v, const shw_camera &cam, const RenderArgs &a,
+                       cudaStream_t st);
 
 }  // namespace shw

@@ -3,7 +3,9 @@
 // Positions arrive as 32.32 fixed-point coordinates (ray.cuh).  Trilinear
 // interpolation is written by hand in FP32 from point loads: the texture unit's
 // linear filter uses low-precision fixed-point weights and cannot meet the
-// accuracy target.  Indices clamp to the edge voxel.
+// accuracy target.  Indices clamp to the edge voxel.  Every accessor has a
+// clamp-free form (CLAMP = false) for samples whose cell is known to lie in
+// [0, n-2] on every axis, where both corners of each axis are inside the cube.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -19,13 +21,27 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v,
 
 __device__ __forceinline__ float lerp(float a, float b, float t) { return __fmaf_rn(t, b - a, a); }
 
-// Tensor-product interpolation of the 8 corner values c[z][y][x].
-__device__ __forceinline__ float trilerp(float c000, float c001, float c010, float c011, float c100, float c101,
-                                         float c110, float c111, float fx, float fy, float fz)
+// two lerps at once with packed FP32x2 arithmetic (same rounding as two scalar lerps)
+__device__ __forceinline__ float2 lerp2(float2 a, float2 b, float t)
 {
-    const float c00 = lerp(c000, c001, fx), c01 = lerp(c010, c011, fx);
-    const float c10 = lerp(c100, c101, fx), c11 = lerp(c110, c111, fx);
-    return lerp(lerp(c00, c01, fy), lerp(c10, c11, fy), fz);
+    const float2 d = __fadd2_rn(b, make_float2(-a.x, -a.y));
+    return __ffma2_rn(make_float2(t, t), d, a);
+}
+
+// Corners of one cell, c[a + 2b + 4c] with a, b, c the x, y, z offsets.
+// Tensor-product interpolation: x first (packed pairwise), then y, then z.
+__device__ __forceinline__ float trilerp(const float c[8], float fx, float fy, float fz)
+{
+    const float2 x0 = lerp2(make_float2(c[0], c[2]), make_float2(c[1], c[3]), fx);  // (c00, c01) of plane z0
+    const float2 x1 = lerp2(make_float2(c[4], c[6]), make_float2(c[5], c[7]), fx);  // (c10, c11) of plane z1
+    const float2 y = lerp2(make_float2(x0.x, x1.x), make_float2(x0.y, x1.y), fy);   // (c0, c1)
+    return lerp(y.x, y.y, fz);
+}
+
+template <bool CLAMP>
+__device__ __forceinline__ int cell_of(long long p, int n)
+{
+    return CLAMP ? clampi(fx_cell(p), -1, n - 1) : fx_cell(p);
 }
 
 // Linear float32 cube [nz][ny][nx].  Idx: int for < 2^31 voxels, long long beyond.
@@ -35,20 +51,32 @@ struct SamplerF32 {
     int nx, ny, nz;
     Idx sy, sz;  // strides of y and z in elements
 
+    template <bool CLAMP = true>
     __device__ __forceinline__ float nearest(long long X, long long Y, long long Z) const
     {
-        const int x = clampi(fx_round(X), 0, nx - 1), y = clampi(fx_round(Y), 0, ny - 1),
-                  z = clampi(fx_round(Z), 0, nz - 1);
+        int x = fx_round(X), y = fx_round(Y), z = fx_round(Z);
+        if (CLAMP) {
+            x = clampi(x, 0, nx - 1);
+            y = clampi(y, 0, ny - 1);
+            z = clampi(z, 0, nz - 1);
+        }
         return __ldg(v + ((Idx)z * sz + (Idx)y * sy + x));
     }
 
-    // corner values c[z][y][x] of the cell with base (ix, iy, iz), each in [-1, n-1]
+    // corners of the cell with base (ix, iy, iz); CLAMP: each index in [-1, n-1]
+    template <bool CLAMP = true>
     __device__ __forceinline__ void corners(int ix, int iy, int iz, float c[8]) const
     {
-        const int x0 = max(ix, 0), y0 = max(iy, 0), z0 = max(iz, 0);
-        const int dx = min(ix + 1, nx - 1) - x0;
-        const Idx dy = (Idx)(min(iy + 1, ny - 1) - y0) * sy;
-        const Idx dz = (Idx)(min(iz + 1, nz - 1) - z0) * sz;
+        int x0 = ix, y0 = iy, z0 = iz, dx = 1;
+        Idx dy = sy, dz = sz;
+        if (CLAMP) {
+            x0 = max(ix, 0);
+            y0 = max(iy, 0);
+            z0 = max(iz, 0);
+            dx = min(ix + 1, nx - 1) - x0;
+            dy = (Idx)(min(iy + 1, ny - 1) - y0) * sy;
+            dz = (Idx)(min(iz + 1, nz - 1) - z0) * sz;
+        }
         const float *p00 = v + ((Idx)z0 * sz + (Idx)y0 * sy + x0);
         const float *p01 = p00 + dy, *p10 = p00 + dz, *p11 = p10 + dy;
         c[0] = __ldg(p00);
@@ -63,47 +91,11 @@ struct SamplerF32 {
 
     __device__ __forceinline__ float trilinear(long long X, long long Y, long long Z) const
     {
-        const int ix = clampi(fx_cell(X), -1, nx - 1), iy = clampi(fx_cell(Y), -1, ny - 1),
-                  iz = clampi(fx_cell(Z), -1, nz - 1);
-        const float fx = fx_frac(X), fy = fx_frac(Y), fz = fx_frac(Z);
-        const int x0 = max(ix, 0), y0 = max(iy, 0), z0 = max(iz, 0);
-        const int dx = min(ix + 1, nx - 1) - x0;
-        const Idx dy = (Idx)(min(iy + 1, ny - 1) - y0) * sy;
-        const Idx dz = (Idx)(min(iz + 1, nz - 1) - z0) * sz;
-        const float *p00 = v + ((Idx)z0 * sz + (Idx)y0 * sy + x0);
-        const float *p01 = p00 + dy, *p10 = p00 + dz, *p11 = p10 + dy;
-        return trilerp(__ldg(p00), __ldg(p00 + dx), __ldg(p01), __ldg(p01 + dx), __ldg(p10), __ldg(p10 + dx),
-                       __ldg(p11), __ldg(p11 + dx), fx, fy, fz);
+        float c[8];
+        corners<true>(cell_of<true>(X, nx), cell_of<true>(Y, ny), cell_of<true>(Z, nz), c);
+        return trilerp(c, fx_frac(X), fx_frac(Y), fx_frac(Z));
     }
 };
-
-// 1: reuse the 8 corners of the cell a ray is in until it leaves that cell; 0: no reuse
-#ifndef SHW_CELL_CACHE
-#define SHW_CELL_CACHE 1
-#endif
-
-// The corners c[a + 2b + 4c] (a, b, c = x, y, z offsets) of the last interpolation cell
-// a ray visited.  Consecutive samples 1/2 voxel apart often stay in one cell and then
-// need no loads at all.
-struct CellCache {
-    int ix = -4, iy = -4, iz = -4;  // no cell yet: valid cells start at -1
-    float c[8];
-};
-
-template <class S>
-__device__ __forceinline__ float trilinear_cached(const S &s, long long X, long long Y, long long Z, CellCache &cc)
-{
-    const int ix = clampi(fx_cell(X), -1, s.nx - 1), iy = clampi(fx_cell(Y), -1, s.ny - 1),
-              iz = clampi(fx_cell(Z), -1, s.nz - 1);
-    if (ix != cc.ix || iy != cc.iy || iz != cc.iz) {
-        s.corners(ix, iy, iz, cc.c);
-        cc.ix = ix;
-        cc.iy = iy;
-        cc.iz = iz;
-    }
-    return trilerp(cc.c[0], cc.c[1], cc.c[2], cc.c[3], cc.c[4], cc.c[5], cc.c[6], cc.c[7], fx_frac(X), fx_frac(Y),
-                   fx_frac(Z));
-}
 
 template <typename T>
 __device__ __forceinline__ float to_f32(unsigned short raw);
@@ -129,7 +121,7 @@ struct SamplerBrick {
 
     static constexpr int S = kBrickStored;
 
-    __device__ __forceinline__ const unsigned short *cell(int ix, int iy, int iz) const
+    __device__ __forceinline__ const unsigned short *cell_ptr(int ix, int iy, int iz) const
     {
         // ix in [-1, n-1]: brick of max(ix, 0), local index ix - 32 b + 1 in [0, 32]
         const int bx = max(ix, 0) >> 5, by = max(iy, 0) >> 5, bz = max(iz, 0) >> 5;
@@ -138,19 +130,25 @@ struct SamplerBrick {
         return v + (brick * kBrickElems + (lz * S + ly) * S + lx);
     }
 
+    template <bool CLAMP = true>
     __device__ __forceinline__ float nearest(long long X, long long Y, long long Z) const
     {
-        const int x = clampi(fx_round(X), 0, nx - 1), y = clampi(fx_round(Y), 0, ny - 1),
-                  z = clampi(fx_round(Z), 0, nz - 1);
+        int x = fx_round(X), y = fx_round(Y), z = fx_round(Z);
+        if (CLAMP) {
+            x = clampi(x, 0, nx - 1);
+            y = clampi(y, 0, ny - 1);
+            z = clampi(z, 0, nz - 1);
+        }
         const int bx = x >> 5, by = y >> 5, bz = z >> 5;
         const long long brick = ((long long)bz * nby + by) * nbx + bx;
         const unsigned short *p = v + (brick * kBrickElems + (((z & 31) + 1) * S + ((y & 31) + 1)) * S + (x & 31) + 1);
         return to_f32<T>(__ldg(p));
     }
 
+    template <bool CLAMP = true>
     __device__ __forceinline__ void corners(int ix, int iy, int iz, float c[8]) const
     {
-        const unsigned short *p = cell(ix, iy, iz);
+        const unsigned short *p = cell_ptr(ix, iy, iz);
         c[0] = to_f32<T>(__ldg(p));
         c[1] = to_f32<T>(__ldg(p + 1));
         c[2] = to_f32<T>(__ldg(p + S));
@@ -163,14 +161,35 @@ struct SamplerBrick {
 
     __device__ __forceinline__ float trilinear(long long X, long long Y, long long Z) const
     {
-        const int ix = clampi(fx_cell(X), -1, nx - 1), iy = clampi(fx_cell(Y), -1, ny - 1),
-                  iz = clampi(fx_cell(Z), -1, nz - 1);
-        const float fx = fx_frac(X), fy = fx_frac(Y), fz = fx_frac(Z);
-        const unsigned short *p = cell(ix, iy, iz);
-        return trilerp(to_f32<T>(__ldg(p)), to_f32<T>(__ldg(p + 1)), to_f32<T>(__ldg(p + S)),
-                       to_f32<T>(__ldg(p + S + 1)), to_f32<T>(__ldg(p + S * S)), to_f32<T>(__ldg(p + S * S + 1)),
-                       to_f32<T>(__ldg(p + S * S + S)), to_f32<T>(__ldg(p + S * S + S + 1)), fx, fy, fz);
+        float c[8];
+        corners<true>(cell_of<true>(X, nx), cell_of<true>(Y, ny), cell_of<true>(Z, nz), c);
+        return trilerp(c, fx_frac(X), fx_frac(Y), fx_frac(Z));
     }
 };
+
+// 1: reuse the 8 corners of the cell a ray is in until it leaves that cell; 0: no reuse
+#ifndef SHW_CELL_CACHE
+#define SHW_CELL_CACHE 1
+#endif
+
+// The corners of the last interpolation cell a ray visited.  Consecutive samples
+// 1/2 voxel apart often stay in one cell and then need no loads at all.
+struct CellCache {
+    int ix = -4, iy = -4, iz = -4;  // no cell yet: valid cells start at -1
+    float c[8];
+};
+
+template <bool CLAMP, class S>
+__device__ __forceinline__ float trilinear_cached(const S &s, long long X, long long Y, long long Z, CellCache &cc)
+{
+    const int ix = cell_of<CLAMP>(X, s.nx), iy = cell_of<CLAMP>(Y, s.ny), iz = cell_of<CLAMP>(Z, s.nz);
+    if (!SHW_CELL_CACHE || ix != cc.ix || iy != cc.iy || iz != cc.iz) {
+        s.template corners<CLAMP>(ix, iy, iz, cc.c);
+        cc.ix = ix;
+        cc.iy = iy;
+        cc.iz = iz;
+    }
+    return trilerp(cc.c, fx_frac(X), fx_frac(Y), fx_frac(Z));
+}
 
 }  // namespace shw

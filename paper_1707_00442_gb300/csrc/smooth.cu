@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(kSmThreads, SHW_SMOOTH_MINB)
 {
     constexpr int IH = kSmTY + 2 * R, K = 2 * R + 1;
     constexpr int STAGE_FLOATS = IH * kSmBW;
+    static_assert((STAGE_FLOATS * 4) % 128 == 0, "TMA stage buffers must start on 128 bytes");
     constexpr uint32_t STAGE_BYTES = STAGE_FLOATS * 4;
     extern __shared__ __align__(128) float smem[];
     float *s_in = smem;                             // [stages][IH][BW]
@@ -151,11 +152,15 @@ __global__ void __launch_bounds__(kSmThreads, SHW_SMOOTH_MINB)
     const int zfirst = zb - R, nplanes = (ze + R) - zfirst;
     const size_t plane = (size_t)nx * ny;
 
+    __shared__ int s_bad;
     if (tid == 0) {
+        s_bad = 0;
+        for (int s = 0; s < kSmStages; ++s) s_bad |= !tma_dst_ok(s_in + s * STAGE_FLOATS, err);
         for (int s = 0; s < kSmStages; ++s) mbar_init(&bars[s], 1);
         fence_barrier_init();
     }
     __syncthreads();
+    if (s_bad) return;  // reported in the error word; nothing was issued
     if (tid == 0) {
         for (int s = 0; s < kSmStages && s < nplanes; ++s) {
             mbar_arrive_expect_tx(&bars[s], STAGE_BYTES);
@@ -213,6 +218,7 @@ __global__ void __launch_bounds__(kSmThreads, SHW_SMOOTH_MINB)
                     for (int j = 0; j < 4; ++j) acc[j] = __fmaf_rn(W.w[k], v[kSmXP - R + j + k], acc[j]);
                 *reinterpret_cast<float4 *>(xp + r * kSmTX + 4 * q) = make_float4(acc[0], acc[1], acc[2], acc[3]);
             }
+            if (edge) fence_proxy_async();  // the edge clamp wrote the stage that a tensor copy refills next
             __syncthreads();
             // the stage is consumed: refill it with plane i + stages
             if (tid == 0 && i + kSmStages < nplanes) {

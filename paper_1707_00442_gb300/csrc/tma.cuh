@@ -15,6 +15,7 @@
 namespace shw {
 
 constexpr unsigned kErrWaitTimeout = 1u;
+constexpr unsigned kErrTmaAlign = 2u;
 constexpr int kWaitSpins = 1 << 22;  // try_wait already suspends in hardware between polls
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -36,6 +37,19 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  : "memory");
 }
 
+// order this thread's generic-proxy shared-memory writes before later async-proxy
+// (tensor copy) accesses of the same bytes
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// plain arrival (release semantics at CTA scope): a consumer hands a stage back
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // One 3-D box of a tensor map into shared memory; completion is signalled on `bar`.
 // The innermost coordinate x times the element size must be a multiple of 16 bytes.
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
@@ -45,6 +59,15 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
         "[%5];" ::"r"(smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
+}
+
+// A tensor copy's shared-memory destination must start on 128 bytes: refuse (and
+// report) a copy that would not, instead of issuing it.
+__device__ __forceinline__ bool tma_dst_ok(const void *dst, unsigned *err)
+{
+    if ((smem_u32(dst) & 127u) == 0u) return true;
+    if (err) atomicOr(err, kErrTmaAlign);
+    return false;
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)

@@ -66,9 +66,11 @@ def test_survey_moment_map_view_bit_exact(m, survey):
     m.sync_status()
     g = out["scalar"].cpu().numpy()
     ref = cube.max(axis=0)[::-1]
-    assert np.array_equal(g, ref)
+    bad = np.argwhere(g != ref)
+    assert bad.size == 0, f"{len(bad)} pixels differ, first {bad[:8].tolist()}"
     last = (cube.shape[0] - 1 - np.argmax(cube[::-1], axis=0))[::-1]
-    assert np.array_equal(out["index"].cpu().numpy(), last)
+    bad = np.argwhere(out["index"].cpu().numpy() != last)
+    assert bad.size == 0, f"{len(bad)} indices differ, first {bad[:8].tolist()}"
 
 
 def test_survey_smooth_sampled(m, survey):
