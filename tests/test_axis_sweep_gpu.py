@@ -38,6 +38,9 @@ CASES = [
     dict(dims=(60, 50, 33), W=70, H=61, angle_deg=23.0),       # rotated in the image plane
     dict(dims=(60, 50, 33), W=70, H=61, down=True),            # looking down -z
     dict(dims=(60, 50, 33), W=53, H=77, down=True, angle_deg=-71.0, spacing=0.7),
+    dict(dims=(64, 48, 40), W=64, H=48, step=0.25),           # four samples per cell
+    dict(dims=(60, 50, 33), W=70, H=61, down=True, step=1.0),  # one sample per cell
+    dict(dims=(60, 50, 33), W=53, H=40, step=0.3),             # no fixed pattern of samples per cell
 ]
 
 
@@ -63,7 +66,7 @@ def test_sweep_equals_general_marcher(m, monkeypatch, case, mode, interp):
     cam = _cam_z(dims, c["W"], c["H"], down=c.get("down", False), angle_deg=c.get("angle_deg", 0.0),
                  spacing=c.get("spacing", 1.0))
     lut = to_dev(scene.linear_lut())
-    kw = dict(interp=interp, opacity_scale=0.05)
+    kw = dict(interp=interp, opacity_scale=0.05, step=c.get("step", 0.5))
     if mode == "composite":
         kw["ckpt"] = True
         kw["ckpt_interval"] = 7
@@ -84,8 +87,9 @@ def test_sweep_equals_general_marcher(m, monkeypatch, case, mode, interp):
         assert torch.equal(ta[used], tb[used])
         assert int(ka.max()) > 0
     if mode != "composite":
+        # the oracle takes the step the library received: the float32 nearest to it
         o = oracle.render(cube, cam, mode, interp=interp, lut=scene.linear_lut(), opacity_scale=0.05,
-                          eps_pos=1e-6, eps_val=1e-4)
+                          step=float(np.float32(c.get("step", 0.5))), eps_pos=1e-6, eps_val=1e-4)
         g = {k: v.cpu().numpy() for k, v in a.items()}
         compare(g, o, mode, scale=float(np.nanmax(cube) - np.nanmin(cube)),
                 max_fragile=0.15 if interp == "trilinear" else 1.0,
@@ -101,3 +105,22 @@ def test_sweep_early_exit(m, monkeypatch):
         assert torch.equal(a[k], b[k])
     k = next(k for k in range(1, 200) if 1 - 0.7 ** k > 0.99)
     assert (a["nsamples"].cpu().numpy() == k).all()
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+@pytest.mark.parametrize("interp", ["trilinear", "nearest"])
+def test_sweep_mip_without_index(m, monkeypatch, case, interp):
+    """MIP with no argmax output keeps the running maximum alone; values match the marcher."""
+    c = CASES[case]
+    dims = c["dims"]
+    cube = scene.tiny_cube(config_id=70 + case, dims=dims, n_sources=2)
+    cube[5, 9, 11] = np.nan
+    cube[2, 3, 4] = 0.0
+    cam = _cam_z(dims, c["W"], c["H"], down=c.get("down", False), angle_deg=c.get("angle_deg", 0.0),
+                 spacing=c.get("spacing", 1.0))
+    lut = to_dev(scene.linear_lut())
+    a, b = _both(m, monkeypatch, to_dev(cube), cam, "mip", lut, interp=interp, step=c.get("step", 0.5),
+                 index=False)
+    assert set(a) == set(b) and "index" not in a
+    for k in a:
+        assert torch.equal(a[k], b[k]), (k, interp, case)
