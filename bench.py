@@ -333,6 +333,8 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clk,
         }
+        if args.variants:
+            res["variants"] = run_variants(shw, torch, step, W, per_kernel, samples_per, peaks)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -341,6 +343,122 @@ def run_ours(args):
 
 # ncu dram bytes per launch of the dominant kernels (null until captured for the current kernel)
 TRAFFIC_PER_LAUNCH: dict = {}
+
+
+# --------------------------------------------------------------------------- variants
+
+def _timeit(torch, fn, reps=5, warm=2):
+    """Median CUDA-event time (ms) of fn on the current stream."""
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def run_variants(shw, torch, step, W, per_kernel, samples_per, peaks):
+    """The method's variants on the same GPU (reported beside the headline, not part of it):
+    the moment-map view of the same cube (the HBM-bound sweep), BF16/FP16 bricks against
+    the float32 path, the batched persistent launch against one launch per sub-cube, and
+    the adjoint of the compositing render."""
+    dev = step.s1.device
+    hbm = float(peaks["hbm_gbs"])
+    nvox = step.s1.numel()
+    res = {}
+
+    # moment-map view: orthographic down the spectral axis, one pixel per voxel column
+    ocam = WL.survey_ortho_camera()
+    mm = {}
+    for m in ("mip", "avg", "spectral", "composite"):
+        kw = dict(WL.MODE_PARAMS[m])
+        o = {"rgba": torch.empty((ocam.height, ocam.width, 4), dtype=torch.float32, device=dev)}
+        ns = int(shw.render(step.s1, ocam, m, lut=step.lut, step=W["step"], scalar=False, index=False, **kw)
+                 ["nsamples"].sum(dtype=torch.int64).item())
+        t = _timeit(torch, lambda: shw.render(step.s1, ocam, m, lut=step.lut, step=W["step"], scalar=False,
+                                              index=False, nsamples=False, out=o, **kw))
+        gbs = 4 * nvox / (t * 1e-3) / 1e9
+        mm[m] = {"ms": round(t, 4), "gsamples_per_s": round(ns / (t * 1e-3) / 1e9, 2),
+                 "hbm_gbs": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm, 4)}
+    res["moment_map"] = {"view": "orthographic down z, 512x512, step 0.5, trilinear; algorithmic bytes = "
+                                 "one read of the float32 cube per render", "modes": mm}
+
+    # BF16 / FP16 bricks of the same smoothed cubes, same perspective renders
+    br = {}
+    for storage in ("bf16", "f16"):
+        b1, b2 = shw.pack_bricks(step.s1, storage), shw.pack_bricks(step.s2, storage)
+        per = {}
+        for m in WL.MODES:
+            kw = dict(WL.MODE_PARAMS[m])
+            lut = step.rlut if m == "ratio" else step.lut
+            t = _timeit(torch, lambda: shw.render(b1, step.cam, m, lut=lut, vol2=b2 if m == "ratio" else None,
+                                                  step=W["step"], scalar=False, index=False, nsamples=False,
+                                                  out=step.outs[m], **kw), reps=3)
+            f32 = per_kernel[f"render_{m}"]
+            per[m] = {"ms": round(t, 4), "fp32_ms": round(f32, 4), "speedup_vs_fp32": round(f32 / t, 3),
+                      "gsamples_per_s": round(samples_per[m] / (t * 1e-3) / 1e9, 2)}
+        br[storage] = per
+        del b1, b2
+    res["bricks"] = br
+
+    # batch: sub-cubes with axes log-uniform in [32, 256], alternately float32 and BF16 bricks,
+    # alternately MIP and compositing, 256x256 from random views
+    import concurrent.futures as cf
+    B = WL.BATCH
+    dims = scene.batch_dims(n=B["n"], lo=B["lo"], hi=B["hi"])
+    rng = np.random.default_rng(11)
+    views = [(rng.uniform(0, 360), rng.uniform(-60, 60)) for _ in range(len(dims))]
+    t0 = time.time()
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        cubes = list(ex.map(lambda i: scene.batch_subcube(i, tuple(int(x) for x in dims[i])), range(len(dims))))
+    log(f"batch sub-cubes generated in {time.time() - t0:.1f}s")
+    items = []
+    for i, cube in enumerate(cubes):
+        d = tuple(int(x) for x in dims[i])
+        ct = torch.from_numpy(cube).to(dev)
+        vol = ct if i % 2 == 0 else shw.pack_bricks(ct, "bf16")
+        cam = scene.orbit_camera(d, views[i][0], views[i][1], B["width"], B["height"])
+        items.append((vol, cam, B["modes"][(i // 2) % 2]))
+    del cubes
+    plan = shw.BatchPlan(items, lut=step.lut, step=B["step"], opacity_scale=B["opacity_scale"])
+    t_plan = _timeit(torch, plan.render, reps=3)
+    outs = plan.outputs
+
+    def one_by_one():
+        for (vol, cam, mode), o in zip(items, outs):
+            shw.render(vol, cam, mode, lut=step.lut, step=B["step"], opacity_scale=B["opacity_scale"],
+                       scalar=False, index=False, nsamples=False, out={"rgba": o})
+    t_loop = _timeit(torch, one_by_one, reps=3, warm=1)
+    info = plan.info
+    res["batch"] = {"n": len(items), "persistent_graph_ms": round(t_plan, 3), "one_launch_per_cube_ms": round(t_loop, 3),
+                    "subcubes_per_s": round(len(items) / (t_plan * 1e-3), 1),
+                    "subcubes_per_s_one_launch_per_cube": round(len(items) / (t_loop * 1e-3), 1),
+                    "speedup": round(t_loop / t_plan, 3), "tile": info["tile"], "ctas_per_sm": info["ctas_per_sm"]}
+    plan.close()
+    del items, outs
+
+    # adjoint of the compositing render (256^3 cube, 512x512 image, checkpoints every 64 steps)
+    D = WL.DIFF
+    cube = torch.from_numpy(scene.diff_cube(dims=D["dims"])).to(dev)
+    cam = scene.orbit_camera(D["dims"], D["yaw"], D["pitch"], D["width"], D["height"])
+    kw = dict(lut=step.lut, step=D["step"], opacity_scale=D["opacity_scale"], ckpt_interval=D["ckpt_interval"])
+    fw = shw.render(cube, cam, "composite", scalar=False, index=False, nsamples=False, ckpt=True, **kw)
+    g_rgba = torch.ones_like(fw["rgba"])
+    g_vol, g_lut, g_s = torch.zeros_like(cube), torch.zeros_like(step.lut), torch.zeros(1, device=dev)
+    t_fw = _timeit(torch, lambda: shw.render(cube, cam, "composite", scalar=False, index=False, nsamples=False,
+                                             ckpt=True, out=fw, **kw))
+    t_bw = _timeit(torch, lambda: shw.render_backward(cube, cam, g_rgba, fw["ckpt"], grad_vol=g_vol, grad_lut=g_lut,
+                                                      grad_scale=g_s, **kw))
+    res["adjoint"] = {"workload": D["name"], "forward_ms": round(t_fw, 4), "backward_ms": round(t_bw, 4)}
+    shw.sync_status()
+    return res
 
 
 # --------------------------------------------------------------------------- oracle (CPU) arm
@@ -420,6 +538,29 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_case(args):
+    """One small case of one kernel family, for profiler captures (prints its time, no JSON line)."""
+    import torch
+    import paper_1707_00442_gb300 as shw
+    from scene.camera import ortho_axis_camera
+    nx, ny, nz = (int(v) for v in args.dims.split(","))
+    cube = torch.from_numpy(scene.survey_cube(dims=(nx, ny, nz), n_sources=50)).cuda()
+    lut = torch.from_numpy(scene.linear_lut()).cuda()
+    if args.case == "smooth":
+        out = torch.empty_like(cube)
+        fn = lambda: shw.smooth(cube, WL.SURVEY["sigma"], WL.SURVEY["radius"], out=out)  # noqa: E731
+    else:
+        cam = ortho_axis_camera((nx, ny, nz), nx, ny) if args.case == "moment-map" else \
+            scene.orbit_camera((nx, ny, nz), 30.0, 20.0, 960, 540)
+        o = {"rgba": torch.empty((cam.height, cam.width, 4), device="cuda")}
+        kw = dict(WL.MODE_PARAMS[args.mode])
+        fn = lambda: shw.render(cube, cam, args.mode, lut=lut, scalar=False, index=False,  # noqa: E731
+                                nsamples=False, out=o, **kw)
+    t = _timeit(torch, fn, reps=args.steps, warm=args.warmup)
+    shw.sync_status()
+    print(f"{args.case} {args.mode} {args.dims}: {t:.4f} ms", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -427,10 +568,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variants", action="store_true",
+                    help="also time the moment-map view, BF16/FP16 bricks, the batched launch and the adjoint")
     ap.add_argument("--workload", default="survey", choices=sorted(WORKLOADS),
                     help="survey: the headline workload; survey-small: the same step on a smaller cube "
                          "(profiler captures)")
+    ap.add_argument("--case", choices=["moment-map", "render", "smooth"],
+                    help="run one small case of one kernel family for a profiler capture, then exit")
+    ap.add_argument("--dims", default="384,384,768", help="--case: cube dims nx,ny,nz")
+    ap.add_argument("--mode", default="mip", help="--case: transfer function")
     args = ap.parse_args()
+    if args.case:
+        run_case(args)
+        return
     if args.warmup < 3 and args.impl == "ours":
         log("warning: fewer than 3 warm-up steps")
     if args.impl == "reference":

@@ -42,6 +42,52 @@ unsigned *device_error_word()
     return g_err_ptr[dev];
 }
 
+// Work counters of persistent launches: a ring of slots per device, each zeroed on the
+// launch's stream just before the launch that takes it.  A slot is reused only after
+// kWorkSlots later launches, far more than can be in flight at once.
+constexpr int kWorkSlots = 1024;
+static __device__ unsigned g_work_ctr[kWorkSlots];
+static unsigned *g_work_ptr[64] = {};
+static std::atomic<unsigned> g_work_next{0};
+
+unsigned *work_counter(cudaStream_t st)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    unsigned *base;
+    {
+        std::lock_guard<std::mutex> lk(g_err_mu);
+        if (!g_work_ptr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_work_ctr) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+            g_work_ptr[dev] = static_cast<unsigned *>(p);
+        }
+        base = g_work_ptr[dev];
+    }
+    unsigned *slot = base + (g_work_next.fetch_add(1, std::memory_order_relaxed) % kWorkSlots);
+    if (cudaMemsetAsync(slot, 0, sizeof(unsigned), st) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return slot;
+}
+
+int sm_count()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
 bool encode_tmap_3d_f32(CUtensorMap *map, const float *base, int nx, int ny, int nz, int bx, int by)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;

@@ -14,6 +14,8 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "ray.cuh"
 #include "sampler.cuh"
@@ -282,6 +284,70 @@ __device__ __forceinline__ bool march(const S &s, const S &s2, const RenderArgs 
     return false;
 }
 
+#ifndef SHW_PREFETCH
+#define SHW_PREFETCH 1  // 1: the interior loop loads the next cell's corners a sample ahead
+#endif
+
+// The interior samples [k0, k1) (every cell in [0, n-2] on every axis, no clamping),
+// trilinear, software-pipelined: while sample k is interpolated and fed to the
+// transfer function, the corners of sample k+1's cell are already being loaded when
+// that cell differs.  Same arithmetic as march<false>, so the same results.
+template <int MODE, class S, class St>
+__device__ __forceinline__ bool march_interior(const S &s, const S &s2, const RenderArgs &a, St &st, long long &X,
+                                               long long &Y, long long &Z, long long DX, long long DY, long long DZ,
+                                               int k0, int k1, int &kdone)
+{
+    constexpr bool TWO = MODE == SHW_RATIO;
+    if (k0 >= k1) {
+        kdone = k1;
+        return false;
+    }
+    int cx = fx_cell(X), cy = fx_cell(Y), cz = fx_cell(Z);
+    float cur[8], cur2[8];
+    s.template corners<false>(cx, cy, cz, cur);
+    if constexpr (TWO) s2.template corners<false>(cx, cy, cz, cur2);
+    for (int k = k0; k < k1; ++k) {
+        const long long Xn = X + DX, Yn = Y + DY, Zn = Z + DZ;
+        const int nx = fx_cell(Xn), ny = fx_cell(Yn), nz = fx_cell(Zn);
+        const bool change = (nx != cx) | (ny != cy) | (nz != cz);
+        const bool pf = change && k + 1 < k1;  // the next sample is interior and in a new cell
+        float nxt[8], nxt2[8];
+        if (pf) {
+            s.template corners<false>(nx, ny, nz, nxt);
+            if constexpr (TWO) s2.template corners<false>(nx, ny, nz, nxt2);
+        }
+        const float fx = fx_frac(X), fy = fx_frac(Y), fz = fx_frac(Z);
+        float v;
+        if constexpr (TWO) {
+            // Algorithm 14: ratio where cube1 exceeds the floor, else DATAMIN
+            const float c1 = trilerp(cur, fx, fy, fz), c2 = trilerp(cur2, fx, fy, fz);
+            v = (c1 > a.ratio_floor) ? __fdiv_rn(c2, c1) : a.lo;
+        } else {
+            v = trilerp(cur, fx, fy, fz);
+        }
+        v = isnan(v) ? a.lo : v;  // a NaN sample counts as DATAMIN
+        if (st.update(v, k)) {
+            kdone = k + 1;
+            return true;
+        }
+        if (pf) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                cur[i] = nxt[i];
+                if constexpr (TWO) cur2[i] = nxt2[i];
+            }
+            cx = nx;
+            cy = ny;
+            cz = nz;
+        }
+        X = Xn;
+        Y = Yn;
+        Z = Zn;
+    }
+    kdone = k1;
+    return false;
+}
+
 // One ray of Algorithm 1 with the transfer function MODE.  lut_c: the colour map in
 // shared memory (read per sample by COMPOSITE); a.lut: the same map in global memory.
 template <int MODE, int INTERP, class S>
@@ -318,7 +384,16 @@ __device__ __forceinline__ void render_pixel(const S &s, const S &s2, const shw_
         }
         CellCache cc, cc2;
         bool stop = march<true, MODE, INTERP>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, 0, ka, done);
-        if (!stop) stop = march<false, MODE, INTERP>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, ka, kb, done);
+        if (!stop) {
+            // (float32 only: for 16-bit bricks the extra registers cost more than the
+            // latency they hide)
+            if constexpr (INTERP == SHW_TRILINEAR && SHW_PREFETCH && S::kLinearF32) {
+                stop = march_interior<MODE>(s, s2, a, st, X, Y, Z, DX, DY, DZ, ka, kb, done);
+                cc.ix = cc2.ix = -4;  // the tail starts with a fresh cell
+            } else {
+                stop = march<false, MODE, INTERP>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, ka, kb, done);
+            }
+        }
         if (!stop) march<true, MODE, INTERP>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, kb, N, done);
 
         if constexpr (MODE == SHW_MIP || MODE == SHW_SPECTRAL || MODE == SHW_RATIO) {
@@ -368,6 +443,43 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(S s, S s2, shw_c
     render_pixel<MODE, INTERP, S>(s, s2, cam, a, lut_c, px, py);
 }
 
+#ifndef SHW_RENDER_PERSISTENT
+#define SHW_RENDER_PERSISTENT 1  // 1: resident CTAs whose warps take warp tiles from a counter
+#endif
+
+// host: a zeroed work counter for one persistent launch on stream st (null on failure),
+// and the device's SM count
+unsigned *work_counter(cudaStream_t st);
+int sm_count();
+
+// Persistent form: every warp takes the next warp tile (centre-out order, as above)
+// from a global counter until none is left, so no SM idles while rays of very
+// different lengths finish and no CTA launch overhead is paid per tile.
+#ifndef SHW_RENDER_MINB
+#define SHW_RENDER_MINB 1  // minimum resident CTAs per SM the persistent kernel is compiled for
+#endif
+template <int MODE, int INTERP, class S>
+__global__ void __launch_bounds__(kRenderThreads, SHW_RENDER_MINB)
+    render_kernel_persistent(S s, S s2, shw_camera cam, RenderArgs a, unsigned *ctr, int nwarp_tiles)
+{
+    const int lane = threadIdx.x & 31;
+    const int ws = a.warp_shift, wtx = 1 << ws, wty = 32 >> ws;
+    int tw, th;
+    cta_tile(ws, tw, th);
+    for (;;) {
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(ctr, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= (unsigned)nwarp_tiles) break;
+        const int rank = (int)t / kCtaWarps, warp = (int)t - rank * kCtaWarps;
+        const int rr = rank / a.tiles_x, cr = rank - rr * a.tiles_x;
+        const int ty = centre_out(rr, a.cty, a.tiles_y), tx = centre_out(cr, a.ctx, a.tiles_x);
+        const int px = tx * tw + (wtx >= wty ? 0 : warp * wtx) + (lane & (wtx - 1));
+        const int py = ty * th + (wtx >= wty ? warp * wty : 0) + (lane >> ws);
+        if (px < a.width && py < a.height) render_pixel<MODE, INTERP, S>(s, s2, cam, a, a.lut, px, py);
+    }
+}
+
 // Pixel coordinates of the cube centre's projection (image centre if behind the eye).
 inline void project_centre(const shw_camera &c, int nx, int ny, int nz, float &px, float &py)
 {
@@ -405,7 +517,30 @@ shw_status launch_render_modes(int mode, int interp, const S &s, const S &s2, co
     a.cty = (int)fminf(fmaxf(cpy / th, 0.0f), (float)(a.tiles_y - 1));
     const dim3 grid((unsigned)tiles);
     const dim3 block(kRenderThreads);
-#define SHW_LAUNCH(M, I) render_kernel<M, I, S><<<grid, block, 0, st>>>(s, s2, cam, a)
+    unsigned *ctr = SHW_RENDER_PERSISTENT ? work_counter(st) : nullptr;
+    const int nsm = sm_count();
+    const int nwarp_tiles = (int)(tiles * kCtaWarps);
+    // persistent grid: as many CTAs as fit on the device at once (at most one per tile)
+    auto persistent = [&](auto kern) {
+        static int per_sm = -1;  // one value per kernel instantiation
+        if (per_sm < 0) {
+            int n = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kRenderThreads, 0) != cudaSuccess) {
+                cudaGetLastError();
+                n = 0;
+            }
+            per_sm = n;
+        }
+        const long long g = std::min<long long>((long long)per_sm * nsm, tiles);
+        kern<<<(unsigned)std::max<long long>(g, 1), block, 0, st>>>(s, s2, cam, a, ctr, nwarp_tiles);
+    };
+#define SHW_LAUNCH(M, I)                                                       \
+    do {                                                                       \
+        if (ctr != nullptr && nsm > 0)                                         \
+            persistent(render_kernel_persistent<M, I, S>);                     \
+        else                                                                   \
+            render_kernel<M, I, S><<<grid, block, 0, st>>>(s, s2, cam, a);     \
+    } while (0)
 #define SHW_CASE(M)                                            \
     case M:                                                    \
         if (interp == SHW_NEAREST) SHW_LAUNCH(M, SHW_NEAREST); \

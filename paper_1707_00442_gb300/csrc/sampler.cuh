@@ -47,6 +47,7 @@ __device__ __forceinline__ int cell_of(long long p, int n)
 // Linear float32 cube [nz][ny][nx].  Idx: int for < 2^31 voxels, long long beyond.
 template <typename Idx>
 struct SamplerF32 {
+    static constexpr bool kLinearF32 = true;
     const float *__restrict__ v;
     int nx, ny, nz;
     Idx sy, sz;  // strides of y and z in elements
@@ -115,6 +116,7 @@ __device__ __forceinline__ float to_f32<__half>(unsigned short raw)
 // every cell live in one brick, at fixed offsets from the cell's base.
 template <typename T>
 struct SamplerBrick {
+    static constexpr bool kLinearF32 = false;
     const unsigned short *__restrict__ v;
     int nx, ny, nz;
     int nbx, nby;
