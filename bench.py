@@ -208,6 +208,24 @@ ALG_FLOPS_PER_SAMPLE = {"mip": _TRI + 1, "spectral": _TRI + 1, "avg": _TRI + 4,
                         "ratio": 2 * _TRI + 2, "composite": _TRI + 2 + 8 + 6 + 3 + 2}
 
 
+# --------------------------------------------------------------------------- multi-rank timing
+
+def max_over_ranks(ms_local: float, world: int, device=None) -> float:
+    """The job's time: the slowest rank's (all ranks hold the value afterwards)."""
+    if world <= 1:
+        return ms_local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank_step: float, steps: int, ms_job: float) -> float:
+    """Units processed by all ranks (weak scaling: each rank its own replica) per second, in G."""
+    return world * units_per_rank_step * steps / (ms_job * 1e-3) / 1e9
+
+
 # --------------------------------------------------------------------------- our arm
 
 def run_ours(args):
@@ -265,11 +283,7 @@ def run_ours(args):
     barrier()
     launches = shw.launch_count() - launches0
     clk = clocks.stop()
-    ms_total = t0.elapsed_time(t1)
-    if world > 1:
-        tt = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total = max_over_ranks(t0.elapsed_time(t1), world, dev)
     per_kernel = {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in events.items()}
 
     # end to end through the public API with host buffers
@@ -292,11 +306,7 @@ def run_ours(args):
             rgba_h[m].copy_(step.outs[m]["rgba"], non_blocking=True)
     e1.record()
     barrier()
-    ms_e2e = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_e2e = float(tt.item())
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1), world, dev)
     h2d = 2 * nvox * 4
     d2h = sum(int(np.prod(rgba_h[m].shape)) * 4 for m in WL.MODES)
 
@@ -306,8 +316,8 @@ def run_ours(args):
     total_by_kind = {k: per_kernel[k] for k in per_kernel}
     dom = max(total_by_kind, key=total_by_kind.get)
 
-    value = world * samples_step * args.steps / (ms_total * 1e-3) / 1e9
-    e2e_value = world * samples_step * args.steps / (ms_e2e * 1e-3) / 1e9
+    value = whole_job_rate(world, samples_step, args.steps, ms_total)
+    e2e_value = whole_job_rate(world, samples_step, args.steps, ms_e2e)
     res = None
     if rank == 0:
         dr = dict(roof[dom])
