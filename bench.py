@@ -351,8 +351,9 @@ def run_ours(args):
     return res, samples_per
 
 
-# ncu dram bytes per launch of the dominant kernels (null until captured for the current kernel)
-TRAFFIC_PER_LAUNCH: dict = {}
+# ncu dram bytes (read + write) per launch of the dominant kernel, from one capture of the
+# current build (profiles/survey_step_dram_traffic.md); reset to absent when the kernel changes
+TRAFFIC_PER_LAUNCH: dict = {"render_ratio": 4533665280 + 23236096}
 
 
 # --------------------------------------------------------------------------- variants
