@@ -348,6 +348,50 @@ __device__ __forceinline__ bool march_interior(const S &s, const S &s2, const Re
     return false;
 }
 
+// setFragment (Algorithm 1): the outputs of one ray from its final transfer-function
+// state.  N: samples of the ray (0: it missed); PZ, DZ: its first sample's z and z step
+// (fixed point); done: samples processed.
+template <int MODE, int INTERP, class St>
+__device__ __forceinline__ void emit_ray(const RenderArgs &a, long long pix, int N, long long PZ, long long DZ,
+                                         const St &st, int done)
+{
+    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+    float scalar = 0.0f;
+    int index = -1;
+    if (N > 0) {
+        if constexpr (MODE == SHW_MIP || MODE == SHW_SPECTRAL || MODE == SHW_RATIO) {
+            const long long Zm = PZ + (long long)st.kmax * DZ;
+            index = clampi(fx_round(Zm), 0, a.nz - 1);
+            scalar = st.m;
+            const float vh = normalise(st.m, a.lo, a.inv_range);
+            if constexpr (MODE == SHW_SPECTRAL) {
+                // Algorithm 4: colour from the spectral position, alpha from the value
+                const float zmax =
+                    (INTERP == SHW_NEAREST) ? (float)index : __ll2float_rn(Zm) * 2.3283064365386963e-10f;
+                const float tz = fminf(fmaxf((zmax + 0.5f) / (float)a.nz, 0.0f), 1.0f);
+                const float4 c = lut_eval(a.lut, tz);
+                out = make_float4(c.x, c.y, c.z, vh);
+            } else {
+                out = lut_eval(a.lut, vh);
+            }
+        } else if constexpr (MODE == SHW_AVG) {
+            scalar = __fdiv_rn(st.sum, (float)N);
+            out = lut_eval(a.lut, normalise(scalar, a.lo, a.inv_range));
+        } else {
+            out = make_float4(st.cr, st.cg, st.cb, 1.0f - st.T);
+            scalar = 1.0f - st.T;
+        }
+    } else {
+        done = 0;
+    }
+    if constexpr (MODE == SHW_COMPOSITE)
+        if (a.ckpt_K != nullptr) a.ckpt_K[pix] = done;
+    a.rgba[pix] = out;
+    if (a.scalar) a.scalar[pix] = scalar;
+    if (a.index) a.index[pix] = index;
+    if (a.nsamples) a.nsamples[pix] = done;
+}
+
 // One ray of Algorithm 1 with the transfer function MODE.  lut_c: the colour map in
 // shared memory (read per sample by COMPOSITE); a.lut: the same map in global memory.
 template <int MODE, int INTERP, class S>
@@ -361,16 +405,13 @@ __device__ __forceinline__ void render_pixel(const S &s, const S &s2, const shw_
     const bool hit = !quick_miss(cam, px, py, s.nx, s.ny, s.nz) && setup_ray(cam, px, py, s.nx, s.ny, s.nz, a.step, r);
     const int N = hit ? min(r.N, a.nmax) : 0;
 
-    float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
-    float scalar = 0.0f;
-    int index = -1;
     int done = 0;
+    typename StateOf<MODE>::type st;
     if (N > 0) {
         int ka, kb;
         interior_range(r, s.nx, s.ny, s.nz, N, ka, kb);
         long long X = r.P[0], Y = r.P[1], Z = r.P[2];
         const long long DX = r.D[0], DY = r.D[1], DZ = r.D[2];
-        typename StateOf<MODE>::type st;
         if constexpr (MODE == SHW_COMPOSITE) {
             st.lut = lut_c;
             st.lo = a.lo;
@@ -396,35 +437,8 @@ __device__ __forceinline__ void render_pixel(const S &s, const S &s2, const shw_
         }
         if (!stop) march<true, MODE, INTERP>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, kb, N, done);
 
-        if constexpr (MODE == SHW_MIP || MODE == SHW_SPECTRAL || MODE == SHW_RATIO) {
-            const long long Zm = r.P[2] + (long long)st.kmax * DZ;
-            index = clampi(fx_round(Zm), 0, a.nz - 1);
-            scalar = st.m;
-            const float vh = normalise(st.m, a.lo, a.inv_range);
-            if constexpr (MODE == SHW_SPECTRAL) {
-                // Algorithm 4: colour from the spectral position, alpha from the value
-                const float zmax =
-                    (INTERP == SHW_NEAREST) ? (float)index : __ll2float_rn(Zm) * 2.3283064365386963e-10f;
-                const float tz = fminf(fmaxf((zmax + 0.5f) / (float)a.nz, 0.0f), 1.0f);
-                const float4 c = lut_eval(a.lut, tz);
-                out = make_float4(c.x, c.y, c.z, vh);
-            } else {
-                out = lut_eval(a.lut, vh);
-            }
-        } else if constexpr (MODE == SHW_AVG) {
-            scalar = __fdiv_rn(st.sum, (float)N);
-            out = lut_eval(a.lut, normalise(scalar, a.lo, a.inv_range));
-        } else {
-            out = make_float4(st.cr, st.cg, st.cb, 1.0f - st.T);
-            scalar = 1.0f - st.T;
-        }
     }
-    if constexpr (MODE == SHW_COMPOSITE)
-        if (a.ckpt_K != nullptr) a.ckpt_K[pix] = done;
-    a.rgba[pix] = out;
-    if (a.scalar) a.scalar[pix] = scalar;
-    if (a.index) a.index[pix] = index;
-    if (a.nsamples) a.nsamples[pix] = done;
+    emit_ray<MODE, INTERP>(a, pix, N, N > 0 ? r.P[2] : 0, N > 0 ? r.D[2] : 0, st, done);
 }
 
 template <int MODE, int INTERP, class S>
