@@ -40,6 +40,7 @@
 #define OR_COMPOSITE 2
 #define OR_SPECTRAL 3
 #define OR_RATIO 4
+#define OR_MOMENT1 5
 
 #define OR_NEAREST 0
 #define OR_TRILINEAR 1
@@ -278,6 +279,8 @@ static void render_ray(const ovol *V, const ovol *V2, const ocam *c, const opara
 
     double m = -INFINITY, zmax = 0.0;        /* MIP / MIP_1 state */
     double sum = 0.0;                        /* average state */
+    double sw = 0.0, szw = 0.0;              /* first-moment state: sum of weights, of z * weight */
+    double top = -INFINITY;                  /* largest v - lo over the samples */
     double T = 1.0, C[3] = {0.0, 0.0, 0.0};  /* compositing state */
     double *vals = NULL, *zs = NULL;         /* kept for the near-tie check */
     int track = (P->mode == OR_MIP || P->mode == OR_SPECTRAL || P->mode == OR_RATIO) && P->eps_val > 0.0;
@@ -325,6 +328,19 @@ static void render_ray(const ovol *V, const ovol *V2, const ocam *c, const opara
         case OR_AVG:
             sum += v;
             break;
+        case OR_MOMENT1: {
+            /* Eq. 4 along the ray: weights are the intensity above DATAMIN (NaN and
+             * values at or below DATAMIN weigh nothing), positions the sample's z */
+            double w = v - P->lo;
+            if (w > top)
+                top = w;
+            if (w < 0.0)
+                w = 0.0;
+            sw += w;
+            szw += sample_z(V, P->interp, p) * w;
+            sum += v;
+            break;
+        }
         case OR_COMPOSITE: {
             /* Algorithm 3 in premultiplied form: a = clamp(s * A_lut(v_hat), 0, 1) */
             double col[4];
@@ -375,6 +391,29 @@ static void render_ray(const ovol *V, const ovol *V2, const ocam *c, const opara
         rgba[3] = 1.0 - T;
         *scalar = 1.0 - T;
         break;
+    case OR_MOMENT1:
+        /* the intensity-weighted mean position (the velocity field of a moment-1 map),
+         * coloured like spectral colouring, alpha from the mean intensity; nothing above
+         * DATAMIN: transparent, no channel */
+        if (sw > 0.0) {
+            double m1 = szw / sw;
+            double tz = (m1 + 0.5) / (double)V->n[2];
+            lut_eval(P->lut, tz < 0.0 ? 0.0 : (tz > 1.0 ? 1.0 : tz), col);
+            rgba[0] = col[0];
+            rgba[1] = col[1];
+            rgba[2] = col[2];
+            rgba[3] = normalise(sum / (double)N, P->lo, P->hi);
+            *scalar = m1;
+            *index = channel_of(m1, V->n[2]);
+            /* the channel is a rounding of m1: fragile within 1e-3 of a half channel;
+             * and a total weight at rounding level makes the moment itself a rounding
+             * decision (interpolated values within rounding of DATAMIN) */
+            if (frag && P->eps_val > 0.0 && (fabs(m1 - floor(m1) - 0.5) < 1e-3 || sw < P->eps_val))
+                *frag |= FRAG_ROUND;
+        } else if (frag && P->eps_val > 0.0 && top > -P->eps_val) {
+            *frag |= FRAG_ROUND; /* no weight, but a sample within rounding of DATAMIN */
+        }
+        break;
     }
     if (frag && P->mode == OR_RATIO && near_ratio >= m - P->eps_val)
         *frag |= FRAG_RATIO;
@@ -409,6 +448,8 @@ int oracle_render(const double *cube, const double *cube2, int nx, int ny, int n
 {
     if (!cube || nx <= 0 || ny <= 0 || nz <= 0 || W <= 0 || H <= 0 || !(step > 0.0) || !lut)
         return 1;
+    if (mode < OR_MIP || mode > OR_MOMENT1)
+        return -1;
     if (mode == OR_RATIO && !cube2)
         return 1;
     ovol V = {cube, {nx, ny, nz}}, V2 = {cube2, {nx, ny, nz}};
