@@ -388,8 +388,8 @@ def run_variants(shw, torch, step, W, per_kernel, samples_per, peaks):
     # moment-map view: orthographic down the spectral axis, one pixel per voxel column
     ocam = WL.survey_ortho_camera()
     mm = {}
-    for m in ("mip", "avg", "spectral", "composite"):
-        kw = dict(WL.MODE_PARAMS[m])
+    for m in ("mip", "avg", "spectral", "composite", "moment1"):
+        kw = dict(WL.MODE_PARAMS.get(m, {}))
         o = {"rgba": torch.empty((ocam.height, ocam.width, 4), dtype=torch.float32, device=dev)}
         ns = int(shw.render(step.s1, ocam, m, lut=step.lut, step=W["step"], scalar=False, index=False, **kw)
                  ["nsamples"].sum(dtype=torch.int64).item())

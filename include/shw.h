@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define SHW_ABI_VERSION 1
+#define SHW_ABI_VERSION 2
 #define SHW_LUT_SIZE 256
 #define SHW_MAX_SMOOTH_RADIUS 16
 #define SHW_BRICK 32        /* brick edge of the reduced-precision storage, voxels */
@@ -66,7 +66,11 @@ typedef enum {
     SHW_AVG = 1,        /* Eq. 3: mean of the samples (zeroth moment / N on a spectral-axis view) */
     SHW_COMPOSITE = 2,  /* Eq. 2 / Algorithm 3: front-to-back compositing through the colour map */
     SHW_SPECTRAL = 3,   /* Algorithm 4: colour from the spectral position of the maximum */
-    SHW_RATIO = 4       /* Algorithm 14: per-sample cube2/cube1, then maximum */
+    SHW_RATIO = 4,      /* Algorithm 14: per-sample cube2/cube1, then maximum */
+    SHW_MOMENT1 = 5     /* Eq. 4 along the ray: sum(z w) / sum(w), w = max(v - lo, 0), z the sample's
+                           height (its channel when nearest); colour from (M1 + 1/2) / nz, alpha
+                           from the mean intensity; a ray with no weight is transparent, channel -1
+                           (not in batch plans: SHW_EUNSUPPORTED) */
 } shw_mode;
 
 typedef enum { SHW_NEAREST = 0, SHW_TRILINEAR = 1 } shw_interp;

@@ -145,7 +145,7 @@ long long max_samples(const shw_volume *v, float step)
 bool valid_params(const shw_render_params *p, const shw_volume *v)
 {
     if (!p || !p->lut || !aligned(p->lut, 16)) return false;
-    if (p->mode < SHW_MIP || p->mode > SHW_RATIO) return false;
+    if (p->mode < SHW_MIP || p->mode > SHW_MOMENT1) return false;
     if (p->interp != SHW_NEAREST && p->interp != SHW_TRILINEAR) return false;
     if (!std::isfinite(p->step) || !(p->step > 0.0f)) return false;
     if (!std::isfinite(p->lo) || !std::isfinite(p->hi) || !(p->hi > p->lo)) return false;

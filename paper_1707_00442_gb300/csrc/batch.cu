@@ -298,7 +298,7 @@ shw_status shw_batch_plan_create(shw_batch_plan **out, const shw_batch_item *ite
         if (!valid_volume(&b.vol) || !valid_camera(&b.cam) || !b.out_rgba || !aligned(b.out_rgba, 16))
             return SHW_EINVAL;
         if (b.mode != SHW_MIP && b.mode != SHW_AVG && b.mode != SHW_COMPOSITE && b.mode != SHW_SPECTRAL)
-            return b.mode == SHW_RATIO ? SHW_EUNSUPPORTED : SHW_EINVAL;
+            return (b.mode == SHW_RATIO || b.mode == SHW_MOMENT1) ? SHW_EUNSUPPORTED : SHW_EINVAL;
         if ((long long)b.vol.nx * b.vol.ny * b.vol.nz >= (1LL << 31)) return SHW_EUNSUPPORTED;
         if (max_samples(&b.vol, p->step) > (1LL << 30)) return SHW_EINVAL;
     }
@@ -466,7 +466,7 @@ extern "C" shw_status shw_render_batch_noalloc(const shw_batch_item *items, int3
         if (!valid_volume(&b.vol) || !valid_camera(&b.cam) || !b.out_rgba || !aligned(b.out_rgba, 16))
             return SHW_EINVAL;
         if (b.mode != SHW_MIP && b.mode != SHW_AVG && b.mode != SHW_COMPOSITE && b.mode != SHW_SPECTRAL)
-            return b.mode == SHW_RATIO ? SHW_EUNSUPPORTED : SHW_EINVAL;
+            return (b.mode == SHW_RATIO || b.mode == SHW_MOMENT1) ? SHW_EUNSUPPORTED : SHW_EINVAL;
         if ((long long)b.vol.nx * b.vol.ny * b.vol.nz >= (1LL << 31)) return SHW_EUNSUPPORTED;
         if (max_samples(&b.vol, p->step) > (1LL << 30)) return SHW_EINVAL;
         nwork += (long long)ceil_div(b.cam.width, tile) * ceil_div(b.cam.height, tile);

@@ -129,6 +129,15 @@ __device__ __forceinline__ void axis_emit(const RenderArgs &a, long long pix, bo
         } else if constexpr (MODE == SHW_AVG) {
             scalar = __fdiv_rn(st.sum, (float)N);
             out = lut_eval(a.lut, normalise(scalar, a.lo, a.inv_range));
+        } else if constexpr (MODE == SHW_MOMENT1) {
+            if (st.sw > 0.0f) {
+                const float m1 = __fdiv_rn(st.szw, st.sw);
+                scalar = m1;
+                index = clampi(__float2int_rd(m1 + 0.5f), 0, a.nz - 1);
+                const float tz = fminf(fmaxf((m1 + 0.5f) / (float)a.nz, 0.0f), 1.0f);
+                const float4 c = lut_eval(a.lut, tz);
+                out = make_float4(c.x, c.y, c.z, normalise(__fdiv_rn(st.sv, (float)N), a.lo, a.inv_range));
+            }
         } else {
             out = make_float4(st.cr, st.cg, st.cb, 1.0f - st.T);
             scalar = 1.0f - st.T;
@@ -382,6 +391,13 @@ __global__ void __launch_bounds__(kAxThreads, MODE == SHW_COMPOSITE ? 1 : 2)
             st[i].ckpt_stride = (long long)a.width * a.height;
             st[i].I = a.ckpt_interval;
             st[i].nckpt = a.nckpt;
+        }
+        if constexpr (MODE == SHW_MOMENT1) {
+            st[i].Z = PZ;
+            st[i].DZ = DZ;
+            st[i].lo = a.lo;
+            st[i].nz = a.nz;
+            st[i].nearest = INTERP == SHW_NEAREST;
         }
     }
     // COMPOSITE: rays still taking samples (a ray that misses counts as stopped)
@@ -641,6 +657,7 @@ shw_status launch_axis(int mode, int interp, bool up, const CUtensorMap &map, co
         SHW_AXC(SHW_AVG)
         SHW_AXC(SHW_COMPOSITE)
         SHW_AXC(SHW_SPECTRAL)
+        SHW_AXC(SHW_MOMENT1)
     default:
         return SHW_EUNSUPPORTED;
     }

@@ -242,9 +242,42 @@ struct CompositeState {
     }
 };
 
+// Eq. 4 along the ray: intensity-weighted mean height.  Weights are the intensity above
+// DATAMIN (NaN samples are DATAMIN already); the height is the sample's z (its channel
+// for nearest sampling).  Compensated sums of w, z w and v (for the mean that sets alpha).
+// Z advances with the samples, which arrive in order.
+struct MomentState {
+    float sw = 0.0f, cw = 0.0f, szw = 0.0f, cz = 0.0f, sv = 0.0f, cv = 0.0f;
+    long long Z = 0, DZ = 0;
+    float lo = 0.0f;
+    int nz = 1;
+    bool nearest = false;
+    __device__ __forceinline__ static void kahan(float &s, float &c, float x)
+    {
+        const float y = __fsub_rn(x, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ bool update(float v, int)
+    {
+        const float z = nearest ? (float)clampi(fx_round(Z), 0, nz - 1) : __fadd_rn((float)fx_cell(Z), fx_frac(Z));
+        const float w = fmaxf(__fsub_rn(v, lo), 0.0f);
+        kahan(sw, cw, w);
+        kahan(szw, cz, __fmul_rn(z, w));
+        kahan(sv, cv, v);
+        Z += DZ;
+        return false;
+    }
+};
+
 template <int MODE>
 struct StateOf {
     using type = MaxState;
+};
+template <>
+struct StateOf<SHW_MOMENT1> {
+    using type = MomentState;
 };
 template <>
 struct StateOf<SHW_AVG> {
@@ -377,6 +410,15 @@ __device__ __forceinline__ void emit_ray(const RenderArgs &a, long long pix, int
         } else if constexpr (MODE == SHW_AVG) {
             scalar = __fdiv_rn(st.sum, (float)N);
             out = lut_eval(a.lut, normalise(scalar, a.lo, a.inv_range));
+        } else if constexpr (MODE == SHW_MOMENT1) {
+            if (st.sw > 0.0f) {
+                const float m1 = __fdiv_rn(st.szw, st.sw);
+                scalar = m1;
+                index = clampi(__float2int_rd(m1 + 0.5f), 0, a.nz - 1);
+                const float tz = fminf(fmaxf((m1 + 0.5f) / (float)a.nz, 0.0f), 1.0f);
+                const float4 c = lut_eval(a.lut, tz);
+                out = make_float4(c.x, c.y, c.z, normalise(__fdiv_rn(st.sv, (float)N), a.lo, a.inv_range));
+            }
         } else {
             out = make_float4(st.cr, st.cg, st.cb, 1.0f - st.T);
             scalar = 1.0f - st.T;
@@ -422,6 +464,13 @@ __device__ __forceinline__ void render_pixel(const S &s, const S &s2, const shw_
             st.ckpt_stride = npix;
             st.I = a.ckpt_interval;
             st.nckpt = a.nckpt;
+        }
+        if constexpr (MODE == SHW_MOMENT1) {
+            st.Z = r.P[2];
+            st.DZ = r.D[2];
+            st.lo = a.lo;
+            st.nz = a.nz;
+            st.nearest = INTERP == SHW_NEAREST;
         }
         CellCache cc, cc2;
         bool stop = march<true, MODE, INTERP>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, 0, ka, done);
@@ -566,6 +615,7 @@ shw_status launch_render_modes(int mode, int interp, const S &s, const S &s2, co
         SHW_CASE(SHW_COMPOSITE)
         SHW_CASE(SHW_SPECTRAL)
         SHW_CASE(SHW_RATIO)
+        SHW_CASE(SHW_MOMENT1)
     default:
         return SHW_EINVAL;
     }

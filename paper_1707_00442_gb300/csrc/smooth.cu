@@ -184,6 +184,7 @@ __global__ void __launch_bounds__(kSmThreads, SHW_SMOOTH_MINB)
         for (int k = 0; k < K; ++k) ring[j][k] = make_float2(0.0f, 0.0f);
 
     bool failed = false;
+    int fail_i = 0;  // the plane whose wait gave up
     for (int base = 0; base < nplanes && !failed; base += K) {
 #pragma unroll
         for (int slot = 0; slot < K; ++slot) {
@@ -193,6 +194,7 @@ __global__ void __launch_bounds__(kSmThreads, SHW_SMOOTH_MINB)
             const bool ok = mbar_wait(&bars[stage], (uint32_t)((i / kSmStages) & 1), err);
             if (__syncthreads_or(!ok)) {
                 failed = true;
+                fail_i = i;
                 break;
             }
             float *tile = s_in + stage * STAGE_FLOATS;
@@ -254,8 +256,10 @@ __global__ void __launch_bounds__(kSmThreads, SHW_SMOOTH_MINB)
         }
     }
     if (failed && tid == 0) {
-        // drain: wait (bounded) for this CTA's copies still in flight before leaving
-        for (int s = 0; s < kSmStages; ++s) mbar_wait(&bars[s], 0u, nullptr), mbar_wait(&bars[s], 1u, nullptr);
+        // drain: wait (bounded) for this CTA's copies still in flight before leaving --
+        // planes fail_i .. fail_i + stages - 1 were issued and not consumed
+        for (int j = fail_i; j < min(nplanes, fail_i + kSmStages); ++j)
+            mbar_wait(&bars[j % kSmStages], (uint32_t)((j / kSmStages) & 1), nullptr);
     }
 }
 
@@ -284,6 +288,7 @@ static bool launch_smooth_tma(const float *in, float *out, int nx, int ny, int n
     const size_t smem = smooth_tma_smem<R>();
     const int zc = smooth_zchunk(nx, ny, nz, R);
     const dim3 grid((unsigned)ceil_div(nx, kSmTX), (unsigned)ceil_div(ny, kSmTY), (unsigned)ceil_div(nz, zc));
+    if (smem > 48 * 1024) cudaFuncSetAttribute(smooth_tma_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     smooth_tma_kernel<R><<<grid, kSmThreads, smem, st>>>(map, out, nx, ny, nz, zc, w, err);
     return true;
 }

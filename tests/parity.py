@@ -85,7 +85,7 @@ def compare(g, o, mode, *, scale, tol=TOL_F32, pixels=None, exact=False, max_fra
     assert stats["rgba_max_err"] <= tol, f"{what}: rgba err {stats['rgba_max_err']} > {tol}"
 
     # channel of the maximum: exact unless near-tied (then any near-maximal channel is valid)
-    if mode in ("mip", "spectral", "ratio"):
+    if mode in ("mip", "spectral", "ratio", "moment1"):
         iok = vok & ((fr & F_TIE) == 0)
         bad = np.flatnonzero(iok & (gi != oi))
         stats["index_mismatch"] = int(len(bad))

@@ -56,7 +56,7 @@ def _both(m, monkeypatch, cube_t, cam, mode, lut_t, **kw):
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
-@pytest.mark.parametrize("mode", ["mip", "avg", "composite", "spectral"])
+@pytest.mark.parametrize("mode", ["mip", "avg", "composite", "spectral", "moment1"])
 @pytest.mark.parametrize("interp", ["trilinear", "nearest"])
 def test_sweep_equals_general_marcher(m, monkeypatch, case, mode, interp):
     c = CASES[case]
@@ -91,7 +91,7 @@ def test_sweep_equals_general_marcher(m, monkeypatch, case, mode, interp):
         o = oracle.render(cube, cam, mode, interp=interp, lut=scene.linear_lut(), opacity_scale=0.05,
                           step=float(np.float32(c.get("step", 0.5))), eps_pos=1e-6, eps_val=1e-4)
         g = {k: v.cpu().numpy() for k, v in a.items()}
-        compare(g, o, mode, scale=float(np.nanmax(cube) - np.nanmin(cube)),
+        compare(g, o, mode, scale=float(dims[2]) if mode == "moment1" else float(np.nanmax(cube) - np.nanmin(cube)),
                 max_fragile=0.15 if interp == "trilinear" else 1.0,
                 what=f"sweep/{mode}/{interp}/{case}")
 

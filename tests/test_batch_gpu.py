@@ -108,10 +108,11 @@ def test_batch_fault_injection(m, monkeypatch):
     p.close()
 
 
-def test_batch_rejects_ratio(m):
+@pytest.mark.parametrize("mode", ["ratio", "moment1"])
+def test_batch_rejects_ratio_and_moment(m, mode):
     items = _batch(n=2, storage_cycle=("f32",))
     dev = _dev_items(m, items)
-    dev[1] = (dev[1][0], dev[1][1], "ratio")
+    dev[1] = (dev[1][0], dev[1][1], mode)
     with pytest.raises(m.ShwError) as e:
         m.BatchPlan(dev, lut=to_dev(scene.linear_lut()), tune=False)
     assert e.value.status == 2

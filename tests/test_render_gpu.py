@@ -9,7 +9,7 @@ from parity import TOL_F32, compare, gpu_render, shw, to_dev
 
 pytestmark = pytest.mark.gpu
 
-MODES = ["mip", "avg", "composite", "spectral", "ratio"]
+MODES = ["mip", "avg", "composite", "spectral", "ratio", "moment1"]
 
 
 @pytest.fixture(scope="module")
@@ -37,6 +37,8 @@ def _scale(cube, mode, o):
         return float(s.max() - s.min()) or 1.0
     if mode == "composite":
         return 1.0
+    if mode == "moment1":
+        return float(cube.shape[0])  # the moment is a height: its range is the channels
     return float(np.nanmax(cube) - np.nanmin(cube))
 
 
