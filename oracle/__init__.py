@@ -51,6 +51,7 @@ def lib():
                                         C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, dp,
                                         C.c_double, C.c_double, C.c_double, lp, C.c_long, C.c_double,
                                         C.c_double, C.c_double, dp, dp, ip, ip, ucp]
+            L.oracle_render2.argtypes = L.oracle_render.argtypes + [C.c_int, C.c_double, C.c_double, C.c_int]
             L.oracle_count_samples.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_int, C.c_int, C.c_int,
                                                C.c_double, ip]
             L.oracle_count_samples.restype = C.c_longlong
@@ -83,10 +84,18 @@ def _cam_args(cam):
     return _d(cam.vec14()), int(bool(cam.ortho)), int(cam.width), int(cam.height)
 
 
+FILTERS = {None: 0, "none": 0, "clip": 1, "scale": 2}
+
+
 def render(cube, cam, mode, *, interp="trilinear", step=0.5, lo=-3.0, hi=8.0, lut=None,
            opacity_scale=1.0, term_alpha=0.99, ratio_floor=0.0, cube2=None, pixels=None,
-           eps_pos=0.0, eps_val=0.0, eps_exit=None):
+           eps_pos=0.0, eps_val=0.0, eps_exit=None, filter=None, min_threshold=0.0, max_threshold=0.0,
+           alpha_threshold=False):
     """Render with the FP64 oracle.  Returns dict(rgba, scalar, index, nsamples, fragile).
+
+    ``filter``: None, "clip" (Algorithm 10) or "scale" (Algorithm 11) with ``min_threshold`` /
+    ``max_threshold``; ``alpha_threshold``: spectral / first-moment alpha 0 up to
+    min_threshold, 1 above.
 
     ``pixels``: optional array of row-major pixel ids; outputs then follow that list.
     ``eps_pos`` / ``eps_val`` / ``eps_exit``: margins (voxels / values / opacity) within which a
@@ -105,13 +114,14 @@ def render(cube, cam, mode, *, interp="trilinear", step=0.5, lo=-3.0, hi=8.0, lu
     n = W * H if pix is None else len(pix)
     rgba = np.zeros((n, 4)); scal = np.zeros(n)
     idx = np.zeros(n, np.int32); ns = np.zeros(n, np.int32); fr = np.zeros(n, np.uint8)
-    rc = L.oracle_render(_ptr(cubed, C.c_double), _ptr(cube2d, C.c_double), nx, ny, nz,
+    rc = L.oracle_render2(_ptr(cubed, C.c_double), _ptr(cube2d, C.c_double), nx, ny, nz,
                          _ptr(c14, C.c_double), ortho, W, H, MODES[mode], INTERP[interp],
                          float(step), float(lo), float(hi), _ptr(lutd, C.c_double),
                          float(opacity_scale), float(term_alpha), float(ratio_floor),
                          _ptr(pix, C.c_long), n, float(eps_pos), float(eps_val), float(eps_exit),
                          _ptr(rgba, C.c_double), _ptr(scal, C.c_double), _ptr(idx, C.c_int),
-                         _ptr(ns, C.c_int), _ptr(fr, C.c_ubyte))
+                         _ptr(ns, C.c_int), _ptr(fr, C.c_ubyte), FILTERS[filter], float(min_threshold),
+                         float(max_threshold), int(bool(alpha_threshold)))
     if rc != 0:
         raise ValueError("oracle_render rejected its arguments")
     if pix is None:

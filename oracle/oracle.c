@@ -212,7 +212,51 @@ typedef struct {
     int mode, interp;
     double h, lo, hi, s, term_alpha, ratio_floor, eps_pos, eps_val, eps_exit;
     const double *lut;
+    int filter;        /* 0 none, 1 intensity clipping (Algorithm 10), 2 domain scaling (Algorithm 11) */
+    double tmin, tmax; /* the filters' minimum and maximum thresholds */
+    int alpha_thr;     /* spectral / first-moment colouring: alpha 0 up to tmin, 1 above */
 } oparams;
+
+#define OR_FILTER_NONE 0
+#define OR_FILTER_CLIP 1
+#define OR_FILTER_SCALE 2
+
+/* The per-sample filter of Algorithm 1 ("val <- filter(val)"): Algorithm 10 replaces a
+ * value below the minimum or above the maximum threshold by DATAMIN; Algorithm 11 does
+ * the same and maps the kept range onto [0, 1].  A value within eps of a threshold is a
+ * rounding decision. */
+static double filter_value(const oparams *P, double v, int *frag)
+{
+    if (P->filter == OR_FILTER_NONE)
+        return v;
+    if (frag && P->eps_val > 0.0 && (fabs(v - P->tmin) < P->eps_val || fabs(v - P->tmax) < P->eps_val))
+        *frag |= FRAG_ROUND;
+    if (P->filter == OR_FILTER_CLIP) {
+        if (v < P->tmin)
+            v = P->lo;
+        if (v > P->tmax)
+            v = P->lo;
+        return v;
+    }
+    const double ratio = 1.0 / (P->tmax - P->tmin);
+    if (v > P->tmax)
+        return P->lo;
+    if (v < P->tmin)
+        return P->lo;
+    return (v - P->tmin) * ratio;
+}
+
+/* Alpha of the first-moment-inspired colourings (spectral, first moment): the value's
+ * position in the colour-map domain, or -- with the threshold option (the remedy for
+ * faint images the paper's discussion gives) -- transparent up to tmin, opaque above. */
+static double colour_alpha(const oparams *P, double v, int *frag)
+{
+    if (!P->alpha_thr)
+        return normalise(v, P->lo, P->hi);
+    if (frag && P->eps_val > 0.0 && fabs(v - P->tmin) < P->eps_val)
+        *frag |= FRAG_ROUND;
+    return v > P->tmin ? 1.0 : 0.0;
+}
 
 /* A trilinear sample is NaN when any corner of its cell is; at a cell face next to a
  * NaN voxel, which cell the position falls in -- and so whether the sample is NaN --
@@ -296,8 +340,8 @@ static void render_ray(const ovol *V, const ovol *V2, const ocam *c, const opara
         double v;
         if (P->mode == OR_RATIO) {
             /* Algorithm 14: val = cube2/cube1 where cube1 > 0 (threshold f), else DATAMIN */
-            double c1 = fetch(V, P->interp, p, P->eps_pos, frag);
-            double c2 = fetch(V2, P->interp, p, P->eps_pos, frag);
+            double c1 = filter_value(P, fetch(V, P->interp, p, P->eps_pos, frag), frag);
+            double c2 = filter_value(P, fetch(V2, P->interp, p, P->eps_pos, frag), frag);
             v = (c1 > P->ratio_floor) ? c2 / c1 : P->lo;
             if (frag && P->eps_val > 0.0 && fabs(c1 - P->ratio_floor) < P->eps_val) {
                 double alt = (c1 > P->ratio_floor) ? P->lo : c2 / c1; /* the other branch */
@@ -307,9 +351,12 @@ static void render_ray(const ovol *V, const ovol *V2, const ocam *c, const opara
             }
         } else {
             v = fetch(V, P->interp, p, P->eps_pos, frag);
+            if (isnan(v))
+                v = P->lo; /* NaN sample -> DATAMIN */
+            v = filter_value(P, v, frag);
         }
         if (isnan(v))
-            v = P->lo; /* NaN sample -> DATAMIN */
+            v = P->lo; /* NaN sample (or ratio) -> DATAMIN */
         ++done;
         switch (P->mode) {
         case OR_MIP:
@@ -375,7 +422,7 @@ static void render_ray(const ovol *V, const ovol *V2, const ocam *c, const opara
         rgba[0] = col[0];
         rgba[1] = col[1];
         rgba[2] = col[2];
-        rgba[3] = normalise(m, P->lo, P->hi);
+        rgba[3] = colour_alpha(P, m, frag);
         *scalar = m;
         *index = channel_of(zmax, V->n[2]);
         break;
@@ -402,7 +449,7 @@ static void render_ray(const ovol *V, const ovol *V2, const ocam *c, const opara
             rgba[0] = col[0];
             rgba[1] = col[1];
             rgba[2] = col[2];
-            rgba[3] = normalise(sum / (double)N, P->lo, P->hi);
+            rgba[3] = colour_alpha(P, sum / (double)N, frag);
             *scalar = m1;
             *index = channel_of(m1, V->n[2]);
             /* the channel is a rounding of m1: fragile within 1e-3 of a half channel;
@@ -438,13 +485,13 @@ static void render_ray(const ovol *V, const ovol *V2, const ocam *c, const opara
 
 /* Render the pixels listed in pix (row-major pixel ids), or every pixel when pix is NULL.
  * Outputs are indexed by list position.  Any output pointer may be NULL. */
-int oracle_render(const double *cube, const double *cube2, int nx, int ny, int nz,
+int oracle_render2(const double *cube, const double *cube2, int nx, int ny, int nz,
                   const double *cam14, int ortho, int W, int H,
                   int mode, int interp, double step, double lo, double hi,
                   const double *lut, double opacity_scale, double term_alpha, double ratio_floor,
                   const long *pix, long npix, double eps_pos, double eps_val, double eps_exit,
                   double *out_rgba, double *out_scalar, int *out_index, int *out_nsamples,
-                  unsigned char *out_fragile)
+                   unsigned char *out_fragile, int filter, double tmin, double tmax, int alpha_thr)
 {
     if (!cube || nx <= 0 || ny <= 0 || nz <= 0 || W <= 0 || H <= 0 || !(step > 0.0) || !lut)
         return 1;
@@ -454,7 +501,11 @@ int oracle_render(const double *cube, const double *cube2, int nx, int ny, int n
         return 1;
     ovol V = {cube, {nx, ny, nz}}, V2 = {cube2, {nx, ny, nz}};
     ocam c = make_cam(cam14, ortho, W, H);
-    oparams P = {mode, interp, step, lo, hi, opacity_scale, term_alpha, ratio_floor, eps_pos, eps_val, eps_exit, lut};
+    if (filter < OR_FILTER_NONE || filter > OR_FILTER_SCALE || (filter != OR_FILTER_NONE && !(tmin <= tmax)) ||
+        (filter == OR_FILTER_SCALE && !(tmin < tmax)) || (alpha_thr != 0 && alpha_thr != 1))
+        return -1;
+    oparams P = {mode, interp, step, lo, hi, opacity_scale, term_alpha, ratio_floor, eps_pos, eps_val, eps_exit, lut,
+                 filter, tmin, tmax, alpha_thr};
     long n = pix ? npix : (long)W * H;
 #pragma omp parallel for schedule(dynamic, 64)
     for (long q = 0; q < n; ++q) {
@@ -472,6 +523,20 @@ int oracle_render(const double *cube, const double *cube2, int nx, int ny, int n
         if (out_fragile) out_fragile[q] = (unsigned char)fr;
     }
     return 0;
+}
+
+/* The same without a filter (Algorithm 1 with filter(val) = val). */
+int oracle_render(const double *cube, const double *cube2, int nx, int ny, int nz,
+                  const double *cam14, int ortho, int W, int H,
+                  int mode, int interp, double step, double lo, double hi,
+                  const double *lut, double opacity_scale, double term_alpha, double ratio_floor,
+                  const long *pix, long npix, double eps_pos, double eps_val, double eps_exit,
+                  double *out_rgba, double *out_scalar, int *out_index, int *out_nsamples,
+                  unsigned char *out_fragile)
+{
+    return oracle_render2(cube, cube2, nx, ny, nz, cam14, ortho, W, H, mode, interp, step, lo, hi, lut,
+                          opacity_scale, term_alpha, ratio_floor, pix, npix, eps_pos, eps_val, eps_exit, out_rgba,
+                          out_scalar, out_index, out_nsamples, out_fragile, OR_FILTER_NONE, 0.0, 0.0, 0);
 }
 
 /* Sample count of every ray (the loop bound N of Algorithm 1), without sampling. */
