@@ -109,7 +109,20 @@ typedef struct {
     float term_alpha;      /* COMPOSITE: stop after the sample that makes alpha > term_alpha (0.99) */
     float ratio_floor;     /* RATIO: a sample's ratio is cube2/cube1 where cube1 > ratio_floor, else DATAMIN */
     int32_t ckpt_interval; /* COMPOSITE checkpoints for the adjoint: samples between checkpoints (64) */
+    int32_t filter;        /* shw_filter: per-sample filter applied before the transfer function (after a
+                              NaN sample became DATAMIN; for SHW_RATIO, to each cube's sample) */
+    float min_threshold;   /* the filter's minimum threshold; also the alpha threshold (below) */
+    float max_threshold;   /* the filter's maximum threshold (>= min_threshold; > for SHW_FILTER_SCALE) */
+    int32_t alpha_threshold; /* SHW_SPECTRAL / SHW_MOMENT1: 0 = alpha from the value; 1 = alpha 0 when the
+                                value that sets it is <= min_threshold, else 1 (the paper's remedy for
+                                faint first-moment-style images) */
 } shw_render_params;
+
+typedef enum {
+    SHW_FILTER_NONE = 0,
+    SHW_FILTER_CLIP = 1,  /* Algorithm 10: a value below min_threshold or above max_threshold -> DATAMIN */
+    SHW_FILTER_SCALE = 2  /* Algorithm 11: outside [min, max] -> DATAMIN, else (v - min) / (max - min) */
+} shw_filter;
 
 /* ---- library information (host only, no GPU needed) ---------------------- */
 

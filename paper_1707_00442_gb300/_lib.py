@@ -38,7 +38,11 @@ class Camera(C.Structure):
 class RenderParams(C.Structure):
     _fields_ = [("mode", C.c_int32), ("interp", C.c_int32), ("step", C.c_float), ("lo", C.c_float),
                 ("hi", C.c_float), ("lut", C.c_void_p), ("opacity_scale", C.c_float),
-                ("term_alpha", C.c_float), ("ratio_floor", C.c_float), ("ckpt_interval", C.c_int32)]
+                ("term_alpha", C.c_float), ("ratio_floor", C.c_float), ("ckpt_interval", C.c_int32),
+                ("filter", C.c_int32), ("min_threshold", C.c_float), ("max_threshold", C.c_float),
+                ("alpha_threshold", C.c_int32)]
+
+FILTERS = {None: 0, "none": 0, "clip": 1, "scale": 2}
 
 
 class BatchItem(C.Structure):

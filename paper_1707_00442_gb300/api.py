@@ -72,12 +72,15 @@ def camera_struct(cam) -> _lib.Camera:
 
 
 def params_struct(mode, lut, *, interp="trilinear", step=0.5, lo=-3.0, hi=8.0, opacity_scale=1.0,
-                  term_alpha=0.99, ratio_floor=0.0, ckpt_interval=64) -> _lib.RenderParams:
+                  term_alpha=0.99, ratio_floor=0.0, ckpt_interval=64, filter=None, min_threshold=0.0,
+                  max_threshold=0.0, alpha_threshold=False) -> _lib.RenderParams:
     _need_cuda(lut, "lut", torch.float32)
     if lut.numel() != 4 * _lib.LUT_SIZE:
         raise ValueError("lut must hold 256 RGBA entries")
     return _lib.RenderParams(MODES[mode], INTERP[interp], float(step), float(lo), float(hi), lut.data_ptr(),
-                             float(opacity_scale), float(term_alpha), float(ratio_floor), int(ckpt_interval))
+                             float(opacity_scale), float(term_alpha), float(ratio_floor), int(ckpt_interval),
+                             _lib.FILTERS[filter], float(min_threshold), float(max_threshold),
+                             int(bool(alpha_threshold)))
 
 
 def smooth(cube: torch.Tensor, sigma: float, radius: int, out: torch.Tensor | None = None) -> torch.Tensor:
@@ -130,7 +133,8 @@ def ckpt_bytes(vol, cam, *, step=0.5, ckpt_interval=64) -> int:
 
 def render(vol, cam, mode: str, *, lut: torch.Tensor, interp="trilinear", step=0.5, lo=-3.0, hi=8.0,
            opacity_scale=1.0, term_alpha=0.99, ratio_floor=0.0, vol2=None, scalar=True, index=True,
-           nsamples=True, ckpt=False, ckpt_interval=64, out=None) -> dict:
+           nsamples=True, ckpt=False, ckpt_interval=64, out=None, filter=None, min_threshold=0.0,
+           max_threshold=0.0, alpha_threshold=False) -> dict:
     """Render one image (shw_render).  Returns a dict of CUDA tensors:
     rgba [H, W, 4] and optionally scalar [H, W], index [H, W], nsamples [H, W], ckpt (bytes).
     ``out``: optional dict of preallocated tensors with the same keys."""
@@ -138,7 +142,8 @@ def render(vol, cam, mode: str, *, lut: torch.Tensor, interp="trilinear", step=0
     v2 = volume_struct(vol2) if vol2 is not None else None
     c = camera_struct(cam)
     p = params_struct(mode, lut, interp=interp, step=step, lo=lo, hi=hi, opacity_scale=opacity_scale,
-                      term_alpha=term_alpha, ratio_floor=ratio_floor, ckpt_interval=ckpt_interval)
+                      term_alpha=term_alpha, ratio_floor=ratio_floor, ckpt_interval=ckpt_interval, filter=filter,
+                      min_threshold=min_threshold, max_threshold=max_threshold, alpha_threshold=alpha_threshold)
     dev = lut.device
     H, W = c.height, c.width
     out = dict(out or {})

@@ -153,6 +153,15 @@ bool valid_params(const shw_render_params *p, const shw_volume *v)
     if (!std::isfinite(p->opacity_scale) || !std::isfinite(p->term_alpha) || !std::isfinite(p->ratio_floor))
         return false;
     if (max_samples(v, p->step) > (1LL << 30)) return false;
+    if (p->filter < SHW_FILTER_NONE || p->filter > SHW_FILTER_SCALE) return false;
+    if (p->alpha_threshold != 0 && p->alpha_threshold != 1) return false;
+    if (p->filter != SHW_FILTER_NONE || p->alpha_threshold) {
+        if (!std::isfinite(p->min_threshold) || !std::isfinite(p->max_threshold)) return false;
+    }
+    if (p->filter == SHW_FILTER_CLIP && !(p->min_threshold <= p->max_threshold)) return false;
+    if (p->filter == SHW_FILTER_SCALE &&
+        (!(p->min_threshold < p->max_threshold) || !std::isfinite(1.0f / (p->max_threshold - p->min_threshold))))
+        return false;
     return true;
 }
 
@@ -257,6 +266,11 @@ shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_c
     a.opacity_scale = p->opacity_scale;
     a.term_alpha = p->term_alpha;
     a.ratio_floor = p->ratio_floor;
+    a.filter = p->filter;
+    a.alpha_thr = p->alpha_threshold;
+    a.tmin = p->min_threshold;
+    a.tmax = p->max_threshold;
+    a.tinv = p->filter == SHW_FILTER_SCALE ? (float)(1.0 / ((double)p->max_threshold - (double)p->min_threshold)) : 0.0f;
     a.nz = vol->nz;
     a.nmax = (int)max_samples(vol, p->step);
     a.warp_shift = warp_shift_for(*cam);

@@ -122,7 +122,7 @@ __device__ __forceinline__ void axis_emit(const RenderArgs &a, long long pix, bo
                 const float zmax = nearest ? (float)index : __ll2float_rn(Zm) * 2.3283064365386963e-10f;
                 const float tz = fminf(fmaxf((zmax + 0.5f) / (float)a.nz, 0.0f), 1.0f);
                 const float4 c = lut_eval(a.lut, tz);
-                out = make_float4(c.x, c.y, c.z, vh);
+                out = make_float4(c.x, c.y, c.z, colour_alpha(st.m, a));
             } else {
                 out = lut_eval(a.lut, vh);
             }
@@ -136,7 +136,7 @@ __device__ __forceinline__ void axis_emit(const RenderArgs &a, long long pix, bo
                 index = clampi(__float2int_rd(m1 + 0.5f), 0, a.nz - 1);
                 const float tz = fminf(fmaxf((m1 + 0.5f) / (float)a.nz, 0.0f), 1.0f);
                 const float4 c = lut_eval(a.lut, tz);
-                out = make_float4(c.x, c.y, c.z, normalise(__fdiv_rn(st.sv, (float)N), a.lo, a.inv_range));
+                out = make_float4(c.x, c.y, c.z, colour_alpha(__fdiv_rn(st.sv, (float)N), a));
             }
         } else {
             out = make_float4(st.cr, st.cg, st.cb, 1.0f - st.T);

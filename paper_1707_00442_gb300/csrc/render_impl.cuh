@@ -38,7 +38,10 @@ struct RenderArgs {
     int ctx, cty;          // the tile holding the projected cube centre (dispatched first)
     float step, lo, inv_range, opacity_scale, term_alpha, ratio_floor;
     int nz;
+    int filter, alpha_thr;  // shw_filter; the alpha-threshold option of spectral / first-moment colouring
+    float tmin, tmax, tinv; // the filter's thresholds; 1 / (tmax - tmin) for domain scaling
 };
+
 
 #ifndef SHW_CTA_WARPS
 #define SHW_CTA_WARPS 2
@@ -65,6 +68,24 @@ __device__ __forceinline__ float normalise(float v, float lo, float inv_range)
 {
     // fmaxf first: a NaN argument yields 0 (never reached: NaN samples become lo)
     return fminf(fmaxf((v - lo) * inv_range, 0.0f), 1.0f);
+}
+
+// The per-sample filter of Algorithm 1: Algorithm 10 (intensity clipping) replaces a value
+// below tmin or above tmax by DATAMIN; Algorithm 11 (domain scaling) does the same and
+// maps [tmin, tmax] onto [0, 1].  A NaN passes through (and becomes DATAMIN later).
+__device__ __forceinline__ float filter_value(float v, const RenderArgs &a)
+{
+    if (a.filter == SHW_FILTER_NONE) return v;
+    const bool out = v < a.tmin || v > a.tmax;
+    if (a.filter == SHW_FILTER_CLIP) return out ? a.lo : v;
+    return out ? a.lo : __fmul_rn(__fsub_rn(v, a.tmin), a.tinv);
+}
+
+// Alpha of the first-moment-inspired colourings: the value's place in the colour-map
+// domain, or with the threshold option transparent up to tmin and opaque above.
+__device__ __forceinline__ float colour_alpha(float v, const RenderArgs &a)
+{
+    return a.alpha_thr ? (v > a.tmin ? 1.0f : 0.0f) : normalise(v, a.lo, a.inv_range);
 }
 
 // CTA tile: the CTA's warps stacked across the warp tile's short side.
@@ -299,10 +320,12 @@ __device__ __forceinline__ bool march(const S &s, const S &s2, const RenderArgs 
         float v;
         if constexpr (MODE == SHW_RATIO) {
             // Algorithm 14: ratio where cube1 exceeds the floor, else DATAMIN
-            const float c1 = sample<CLAMP, INTERP>(s, X, Y, Z, cc), c2 = sample<CLAMP, INTERP>(s2, X, Y, Z, cc2);
+            const float c1 = filter_value(sample<CLAMP, INTERP>(s, X, Y, Z, cc), a);
+            const float c2 = filter_value(sample<CLAMP, INTERP>(s2, X, Y, Z, cc2), a);
             v = (c1 > a.ratio_floor) ? __fdiv_rn(c2, c1) : a.lo;
         } else {
             v = sample<CLAMP, INTERP>(s, X, Y, Z, cc);
+            v = filter_value(isnan(v) ? a.lo : v, a);
         }
         v = isnan(v) ? a.lo : v;  // a NaN sample counts as DATAMIN
         if (st.update(v, k)) {
@@ -353,10 +376,11 @@ __device__ __forceinline__ bool march_interior(const S &s, const S &s2, const Re
         float v;
         if constexpr (TWO) {
             // Algorithm 14: ratio where cube1 exceeds the floor, else DATAMIN
-            const float c1 = trilerp(cur, fx, fy, fz), c2 = trilerp(cur2, fx, fy, fz);
+            const float c1 = filter_value(trilerp(cur, fx, fy, fz), a), c2 = filter_value(trilerp(cur2, fx, fy, fz), a);
             v = (c1 > a.ratio_floor) ? __fdiv_rn(c2, c1) : a.lo;
         } else {
             v = trilerp(cur, fx, fy, fz);
+            v = filter_value(isnan(v) ? a.lo : v, a);
         }
         v = isnan(v) ? a.lo : v;  // a NaN sample counts as DATAMIN
         if (st.update(v, k)) {
@@ -403,7 +427,7 @@ __device__ __forceinline__ void emit_ray(const RenderArgs &a, long long pix, int
                     (INTERP == SHW_NEAREST) ? (float)index : __ll2float_rn(Zm) * 2.3283064365386963e-10f;
                 const float tz = fminf(fmaxf((zmax + 0.5f) / (float)a.nz, 0.0f), 1.0f);
                 const float4 c = lut_eval(a.lut, tz);
-                out = make_float4(c.x, c.y, c.z, vh);
+                out = make_float4(c.x, c.y, c.z, colour_alpha(st.m, a));
             } else {
                 out = lut_eval(a.lut, vh);
             }
@@ -417,7 +441,7 @@ __device__ __forceinline__ void emit_ray(const RenderArgs &a, long long pix, int
                 index = clampi(__float2int_rd(m1 + 0.5f), 0, a.nz - 1);
                 const float tz = fminf(fmaxf((m1 + 0.5f) / (float)a.nz, 0.0f), 1.0f);
                 const float4 c = lut_eval(a.lut, tz);
-                out = make_float4(c.x, c.y, c.z, normalise(__fdiv_rn(st.sv, (float)N), a.lo, a.inv_range));
+                out = make_float4(c.x, c.y, c.z, colour_alpha(__fdiv_rn(st.sv, (float)N), a));
             }
         } else {
             out = make_float4(st.cr, st.cg, st.cb, 1.0f - st.T);

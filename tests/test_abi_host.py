@@ -46,7 +46,7 @@ def test_struct_layout(L):
     from paper_1707_00442_gb300 import _lib
     assert L.shw_struct_size(0) == C.sizeof(_lib.Volume) == 24
     assert L.shw_struct_size(1) == C.sizeof(_lib.Camera) == 68
-    assert L.shw_struct_size(2) == C.sizeof(_lib.RenderParams) == 48
+    assert L.shw_struct_size(2) == C.sizeof(_lib.RenderParams) == 64
     assert L.shw_struct_size(3) == C.sizeof(_lib.BatchItem) == 112
     assert L.shw_struct_size(4) == C.sizeof(_lib.BatchInfo)
     assert L.shw_struct_size(9) == 0

@@ -124,3 +124,4 @@ def test_sweep_mip_without_index(m, monkeypatch, case, interp):
     assert set(a) == set(b) and "index" not in a
     for k in a:
         assert torch.equal(a[k], b[k]), (k, interp, case)
+

@@ -190,3 +190,43 @@ def test_launch_counter_moves(m, tiny):
     gpu_render(m, to_dev(tiny[0]), scene.ortho_axis_camera((64, 64, 64), 128, 128), "mip",
                to_dev(scene.linear_lut()))
     assert m.launch_count() == before + 1
+
+
+FILTER_CASES = [("clip", -0.5, 3.0), ("scale", -1.0, 4.0)]
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("filt", range(len(FILTER_CASES)))
+@pytest.mark.parametrize("view", ["axis", "persp"])
+def test_filters_parity(m, ragged, tiny, mode, filt, view):
+    """Per-sample intensity clipping (Algorithm 10) and domain scaling (Algorithm 11)."""
+    kind, tmin, tmax = FILTER_CASES[filt]
+    if view == "axis":
+        cube, c2 = tiny
+        cam = scene.ortho_axis_camera((64, 64, 64), 128, 128)
+    else:
+        cube, c2 = ragged
+        cam = scene.orbit_camera(RAGGED_DIMS, 30, 20, 100, 75)
+    lut = scene.ratio_lut() if mode == "ratio" else scene.linear_lut()
+    kw = _kw(mode)
+    if kind == "scale" and mode != "ratio":
+        kw.update(lo=-0.5, hi=1.0)  # the scaled domain is [0, 1]; DATAMIN below it
+    if mode == "ratio":
+        tmin, tmax = 0.5, 6.0
+    f = dict(filter=kind, min_threshold=tmin, max_threshold=tmax)
+    g = gpu_render(m, to_dev(cube), cam, mode, to_dev(lut), vol2=to_dev(c2), **kw, **f)
+    o = oracle.render(cube, cam, mode, lut=lut, cube2=c2, eps_pos=1e-6, eps_val=1e-4, **kw, **f)
+    compare(g, o, mode, scale=_scale(cube, mode, o), max_fragile=0.05, what=f"{mode}/{kind}/{view}")
+
+
+@pytest.mark.parametrize("mode", ["spectral", "moment1"])
+def test_alpha_threshold_parity(m, ragged, mode):
+    cube, _ = ragged
+    cam = scene.orbit_camera(RAGGED_DIMS, -40, 25, 90, 70)
+    lut = scene.linear_lut()
+    f = dict(alpha_threshold=True, min_threshold=2.0 if mode == "spectral" else 0.0)
+    g = gpu_render(m, to_dev(cube), cam, mode, to_dev(lut), **f)
+    o = oracle.render(cube, cam, mode, lut=lut, eps_pos=1e-6, eps_val=1e-4, **f)
+    compare(g, o, mode, scale=_scale(cube, mode, o), max_fragile=0.05, what=f"{mode}/alpha-threshold")
+    a = g["rgba"][..., 3]
+    assert set(np.unique(a)) <= {0.0, 1.0} and (a == 1.0).any() and (a == 0.0).any()
