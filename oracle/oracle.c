@@ -41,6 +41,10 @@
 #define OR_SPECTRAL 3
 #define OR_RATIO 4
 #define OR_MOMENT1 5
+#define OR_COMPOSITE_SPECTRAL 6 /* Algorithm 5, AVIP_1: compositing, colour from the sample's spectral position */
+#define OR_MIP_RGB 7            /* Algorithm 6: maximum, colour from the maximum's position (r, g, b) = (z, y, x) */
+#define OR_COMPOSITE_RGB 8      /* Algorithm 7, AVIP_RGB: compositing, colour from the sample's position */
+#define OR_RATIO_MIP 9          /* Algorithms 12-13, line ratio Method 1: maximum of each cube, then their ratio */
 
 #define OR_NEAREST 0
 #define OR_TRILINEAR 1
@@ -299,6 +303,29 @@ static double sample_z(const ovol *V, int interp, const double p[3])
     return p[2];
 }
 
+/* A position's texture coordinate along an axis of n voxels, (p + 1/2) / n in [0, 1]. */
+static double tex_coord(double p, int n)
+{
+    double t = (p + 0.5) / (double)n;
+    return t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+}
+
+/* The sample's position as colouring uses it: the voxel for nearest sampling, the point
+ * itself for trilinear (sample_z's rule on every axis). */
+static void sample_pos(const ovol *V, int interp, const double p[3], double q[3])
+{
+    for (int a = 0; a < 3; ++a) {
+        if (interp == OR_NEAREST) {
+            long k = (long)floor(p[a] + 0.5);
+            if (k < 0) k = 0;
+            if (k > V->n[a] - 1) k = V->n[a] - 1;
+            q[a] = (double)k;
+        } else {
+            q[a] = p[a];
+        }
+    }
+}
+
 static int channel_of(double z, int nz)
 {
     long k = (long)floor(z + 0.5);
@@ -326,8 +353,11 @@ static void render_ray(const ovol *V, const ovol *V2, const ocam *c, const opara
     double sw = 0.0, szw = 0.0;              /* first-moment state: sum of weights, of z * weight */
     double top = -INFINITY;                  /* largest v - lo over the samples */
     double T = 1.0, C[3] = {0.0, 0.0, 0.0};  /* compositing state */
+    double mpos[3] = {0.0, 0.0, 0.0};        /* MIP_RGB: position of the maximum */
+    double m1 = -INFINITY, m2 = -INFINITY;   /* line ratio Method 1: maximum of each cube */
     double *vals = NULL, *zs = NULL;         /* kept for the near-tie check */
-    int track = (P->mode == OR_MIP || P->mode == OR_SPECTRAL || P->mode == OR_RATIO) && P->eps_val > 0.0;
+    int track = (P->mode == OR_MIP || P->mode == OR_SPECTRAL || P->mode == OR_RATIO || P->mode == OR_MIP_RGB) &&
+                P->eps_val > 0.0;
     if (track) {
         vals = (double *)malloc(sizeof(double) * (size_t)N);
         zs = (double *)malloc(sizeof(double) * (size_t)N);
@@ -338,6 +368,17 @@ static void render_ray(const ovol *V, const ovol *V2, const ocam *c, const opara
         double t = t0 + (k + 0.5) * P->h;
         double p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
         double v;
+        if (P->mode == OR_RATIO_MIP) {
+            /* Algorithm 13: each cube's running maximum (">"; a NaN sample is DATAMIN) */
+            double c1 = filter_value(P, fetch(V, P->interp, p, P->eps_pos, frag), frag);
+            double c2 = filter_value(P, fetch(V2, P->interp, p, P->eps_pos, frag), frag);
+            if (isnan(c1)) c1 = P->lo;
+            if (isnan(c2)) c2 = P->lo;
+            if (c1 > m1) m1 = c1;
+            if (c2 > m2) m2 = c2;
+            ++done;
+            continue;
+        }
         if (P->mode == OR_RATIO) {
             /* Algorithm 14: val = cube2/cube1 where cube1 > 0 (threshold f), else DATAMIN */
             double c1 = filter_value(P, fetch(V, P->interp, p, P->eps_pos, frag), frag);
@@ -362,10 +403,12 @@ static void render_ray(const ovol *V, const ovol *V2, const ocam *c, const opara
         case OR_MIP:
         case OR_RATIO:
         case OR_SPECTRAL:
-            /* Eq. 1 / Algorithms 2 and 4: c_i = v_i if v_i >= c_{i-1} */
+        case OR_MIP_RGB:
+            /* Eq. 1 / Algorithms 2, 4 and 6: c_i = v_i if v_i >= c_{i-1} */
             if (v >= m) {
                 m = v;
                 zmax = sample_z(V, P->interp, p);
+                sample_pos(V, P->interp, p, mpos);
             }
             if (track) {
                 vals[k] = v;
@@ -388,12 +431,31 @@ static void render_ray(const ovol *V, const ovol *V2, const ocam *c, const opara
             sum += v;
             break;
         }
-        case OR_COMPOSITE: {
-            /* Algorithm 3 in premultiplied form: a = clamp(s * A_lut(v_hat), 0, 1) */
+        case OR_COMPOSITE:
+        case OR_COMPOSITE_SPECTRAL:
+        case OR_COMPOSITE_RGB: {
+            /* Algorithm 3 in premultiplied form: a = clamp(s * A_lut(v_hat), 0, 1); the
+             * colour from the value (Algorithm 3), from the sample's spectral position
+             * through the colour map (Algorithm 5), or from its position (Algorithm 7) */
             double col[4];
             lut_eval(P->lut, normalise(v, P->lo, P->hi), col);
             double a = P->s * col[3];
             a = a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
+            if (P->mode != OR_COMPOSITE) {
+                double q[3];
+                sample_pos(V, P->interp, p, q);
+                if (P->mode == OR_COMPOSITE_SPECTRAL) {
+                    double cz[4];
+                    lut_eval(P->lut, tex_coord(q[2], V->n[2]), cz);
+                    col[0] = cz[0];
+                    col[1] = cz[1];
+                    col[2] = cz[2];
+                } else {
+                    col[0] = tex_coord(q[2], V->n[2]);
+                    col[1] = tex_coord(q[1], V->n[1]);
+                    col[2] = tex_coord(q[0], V->n[0]);
+                }
+            }
             for (int ch = 0; ch < 3; ++ch)
                 C[ch] += T * a * col[ch];
             T *= (1.0 - a);
@@ -432,11 +494,34 @@ static void render_ray(const ovol *V, const ovol *V2, const ocam *c, const opara
         lut_eval(P->lut, normalise(*scalar, P->lo, P->hi), rgba);
         break;
     case OR_COMPOSITE:
+    case OR_COMPOSITE_SPECTRAL:
+    case OR_COMPOSITE_RGB:
         rgba[0] = C[0];
         rgba[1] = C[1];
         rgba[2] = C[2];
         rgba[3] = 1.0 - T;
         *scalar = 1.0 - T;
+        break;
+    case OR_MIP_RGB:
+        /* Algorithm 6: (r, g, b) = the maximum's (z, y, x) as texture coordinates */
+        rgba[0] = tex_coord(mpos[2], V->n[2]);
+        rgba[1] = tex_coord(mpos[1], V->n[1]);
+        rgba[2] = tex_coord(mpos[0], V->n[0]);
+        rgba[3] = colour_alpha(P, m, frag);
+        *scalar = m;
+        *index = channel_of(zmax, V->n[2]);
+        break;
+    case OR_RATIO_MIP:
+        /* Algorithm 13: the colour of maxval2 / maxval1 where maxval1 > 0 (the floor),
+         * else transparent black */
+        if (m1 > P->ratio_floor) {
+            *scalar = m2 / m1;
+            lut_eval(P->lut, normalise(*scalar, P->lo, P->hi), rgba);
+        } else {
+            *scalar = P->lo;
+        }
+        if (frag && P->eps_val > 0.0 && fabs(m1 - P->ratio_floor) < P->eps_val)
+            *frag |= FRAG_RATIO;
         break;
     case OR_MOMENT1:
         /* the intensity-weighted mean position (the velocity field of a moment-1 map),
@@ -474,7 +559,8 @@ static void render_ray(const ovol *V, const ovol *V2, const ocam *c, const opara
              * identically by any implementation of ">="; only near ties are fragile */
             if (!(vals[k] >= m - P->eps_val) || vals[k] == m)
                 continue;
-            int differs = (P->mode == OR_SPECTRAL) ? (zs[k] != zmax) : (channel_of(zs[k], V->n[2]) != ch);
+            int differs = (P->mode == OR_MIP_RGB) ? 1
+                          : (P->mode == OR_SPECTRAL) ? (zs[k] != zmax) : (channel_of(zs[k], V->n[2]) != ch);
             if (differs)
                 *frag |= FRAG_TIE;
         }
@@ -495,9 +581,9 @@ int oracle_render2(const double *cube, const double *cube2, int nx, int ny, int 
 {
     if (!cube || nx <= 0 || ny <= 0 || nz <= 0 || W <= 0 || H <= 0 || !(step > 0.0) || !lut)
         return 1;
-    if (mode < OR_MIP || mode > OR_MOMENT1)
+    if (mode < OR_MIP || mode > OR_RATIO_MIP)
         return -1;
-    if (mode == OR_RATIO && !cube2)
+    if ((mode == OR_RATIO || mode == OR_RATIO_MIP) && !cube2)
         return 1;
     ovol V = {cube, {nx, ny, nz}}, V2 = {cube2, {nx, ny, nz}};
     ocam c = make_cam(cam14, ortho, W, H);
