@@ -67,10 +67,19 @@ typedef enum {
     SHW_COMPOSITE = 2,  /* Eq. 2 / Algorithm 3: front-to-back compositing through the colour map */
     SHW_SPECTRAL = 3,   /* Algorithm 4: colour from the spectral position of the maximum */
     SHW_RATIO = 4,      /* Algorithm 14: per-sample cube2/cube1, then maximum */
-    SHW_MOMENT1 = 5     /* Eq. 4 along the ray: sum(z w) / sum(w), w = max(v - lo, 0), z the sample's
+    SHW_MOMENT1 = 5,    /* Eq. 4 along the ray: sum(z w) / sum(w), w = max(v - lo, 0), z the sample's
                            height (its channel when nearest); colour from (M1 + 1/2) / nz, alpha
-                           from the mean intensity; a ray with no weight is transparent, channel -1
-                           (not in batch plans: SHW_EUNSUPPORTED) */
+                           from the mean intensity; a ray with no weight is transparent, channel -1 */
+    SHW_COMPOSITE_SPECTRAL = 6, /* Algorithm 5 (AVIP_1): compositing, each sample coloured by the map at
+                                   its spectral position (z + 1/2) / nz, opacity as SHW_COMPOSITE */
+    SHW_MIP_RGB = 7,        /* Algorithm 6: maximum; (r, g, b) = the maximum's (z, y, x) as texture
+                               coordinates (p + 1/2) / n, alpha from its value */
+    SHW_COMPOSITE_RGB = 8,  /* Algorithm 7 (AVIP_RGB): compositing, each sample coloured by its (z, y, x) */
+    SHW_RATIO_MIP = 9       /* Algorithms 12-13 (line ratio, Method 1): each cube's maximum; the colour of
+                               max2 / max1 where max1 > ratio_floor, else transparent black (scalar
+                               DATAMIN); needs vol2 like SHW_RATIO; channel output -1 */
+    /* Modes 5..9 are not in batch plans (SHW_EUNSUPPORTED); positions follow spectral
+       colouring's rule: the voxel for nearest sampling, the point for trilinear. */
 } shw_mode;
 
 typedef enum { SHW_NEAREST = 0, SHW_TRILINEAR = 1 } shw_interp;

@@ -14,7 +14,8 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libshw.so")
 
 SHW_OK, SHW_EINVAL, SHW_EUNSUPPORTED, SHW_ECUDA, SHW_ENOMEM, SHW_ETIMEOUT, SHW_EDEVICE = range(7)
-MODES = {"mip": 0, "avg": 1, "composite": 2, "spectral": 3, "ratio": 4, "moment1": 5}
+MODES = {"mip": 0, "avg": 1, "composite": 2, "spectral": 3, "ratio": 4, "moment1": 5,
+         "composite_spectral": 6, "mip_rgb": 7, "composite_rgb": 8, "ratio_mip": 9}
 INTERP = {"nearest": 0, "trilinear": 1}
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
 ABI_VERSION = 2

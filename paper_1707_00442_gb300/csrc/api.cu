@@ -145,7 +145,7 @@ long long max_samples(const shw_volume *v, float step)
 bool valid_params(const shw_render_params *p, const shw_volume *v)
 {
     if (!p || !p->lut || !aligned(p->lut, 16)) return false;
-    if (p->mode < SHW_MIP || p->mode > SHW_MOMENT1) return false;
+    if (p->mode < SHW_MIP || p->mode > SHW_RATIO_MIP) return false;
     if (p->interp != SHW_NEAREST && p->interp != SHW_TRILINEAR) return false;
     if (!std::isfinite(p->step) || !(p->step > 0.0f)) return false;
     if (!std::isfinite(p->lo) || !std::isfinite(p->hi) || !(p->hi > p->lo)) return false;
@@ -246,7 +246,7 @@ shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_c
     if ((out_scalar && !aligned(out_scalar, 4)) || (out_index && !aligned(out_index, 4)) ||
         (out_nsamples && !aligned(out_nsamples, 4)))
         return SHW_EINVAL;
-    if (p->mode == SHW_RATIO) {
+    if (p->mode == SHW_RATIO || p->mode == SHW_RATIO_MIP) {
         if (!valid_volume(vol2) || vol2->nx != vol->nx || vol2->ny != vol->ny || vol2->nz != vol->nz ||
             vol2->storage != vol->storage)
             return SHW_EINVAL;
@@ -271,6 +271,8 @@ shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_c
     a.tmin = p->min_threshold;
     a.tmax = p->max_threshold;
     a.tinv = p->filter == SHW_FILTER_SCALE ? (float)(1.0 / ((double)p->max_threshold - (double)p->min_threshold)) : 0.0f;
+    a.nx = vol->nx;
+    a.ny = vol->ny;
     a.nz = vol->nz;
     a.nmax = (int)max_samples(vol, p->step);
     a.warp_shift = warp_shift_for(*cam);
@@ -282,7 +284,7 @@ shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_c
         a.ckpt_T = reinterpret_cast<float *>(static_cast<char *>(ckpt) + npix * 4);
         a.nckpt = (int)ckpt_count(vol, p);
     }
-    const shw_volume *v2 = (p->mode == SHW_RATIO) ? vol2 : nullptr;
+    const shw_volume *v2 = (p->mode == SHW_RATIO || p->mode == SHW_RATIO_MIP) ? vol2 : nullptr;
     cudaStream_t st = as_stream(stream);
     // orthographic views down the spectral axis: the plane sweep, when it applies
     const shw_status sa = render_axis(p->mode, p->interp, *vol, *cam, a, st);

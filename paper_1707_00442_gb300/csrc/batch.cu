@@ -87,6 +87,8 @@ __global__ void __launch_bounds__(TILE *TILE) batch_kernel(const BatchItemDev *_
         a.inv_range = sh.inv_range;
         a.opacity_scale = sh.opacity_scale;
         a.term_alpha = sh.term_alpha;
+        a.nx = it.nx;
+        a.ny = it.ny;
         a.nz = it.nz;
         if (it.storage == SHW_F32) {
             const SamplerF32<int> s{static_cast<const float *>(it.data), it.nx, it.ny, it.nz, it.nx, it.nx * it.ny};
@@ -299,7 +301,7 @@ shw_status shw_batch_plan_create(shw_batch_plan **out, const shw_batch_item *ite
         if (!valid_volume(&b.vol) || !valid_camera(&b.cam) || !b.out_rgba || !aligned(b.out_rgba, 16))
             return SHW_EINVAL;
         if (b.mode != SHW_MIP && b.mode != SHW_AVG && b.mode != SHW_COMPOSITE && b.mode != SHW_SPECTRAL)
-            return (b.mode == SHW_RATIO || b.mode == SHW_MOMENT1) ? SHW_EUNSUPPORTED : SHW_EINVAL;
+            return (b.mode >= SHW_RATIO && b.mode <= SHW_RATIO_MIP) ? SHW_EUNSUPPORTED : SHW_EINVAL;
         if ((long long)b.vol.nx * b.vol.ny * b.vol.nz >= (1LL << 31)) return SHW_EUNSUPPORTED;
         if (max_samples(&b.vol, p->step) > (1LL << 30)) return SHW_EINVAL;
     }
@@ -468,7 +470,7 @@ extern "C" shw_status shw_render_batch_noalloc(const shw_batch_item *items, int3
         if (!valid_volume(&b.vol) || !valid_camera(&b.cam) || !b.out_rgba || !aligned(b.out_rgba, 16))
             return SHW_EINVAL;
         if (b.mode != SHW_MIP && b.mode != SHW_AVG && b.mode != SHW_COMPOSITE && b.mode != SHW_SPECTRAL)
-            return (b.mode == SHW_RATIO || b.mode == SHW_MOMENT1) ? SHW_EUNSUPPORTED : SHW_EINVAL;
+            return (b.mode >= SHW_RATIO && b.mode <= SHW_RATIO_MIP) ? SHW_EUNSUPPORTED : SHW_EINVAL;
         if ((long long)b.vol.nx * b.vol.ny * b.vol.nz >= (1LL << 31)) return SHW_EUNSUPPORTED;
         if (max_samples(&b.vol, p->step) > (1LL << 30)) return SHW_EINVAL;
         nwork += (long long)ceil_div(b.cam.width, tile) * ceil_div(b.cam.height, tile);

@@ -37,7 +37,7 @@ struct RenderArgs {
     int tiles_x, tiles_y;  // CTA tiles per image row / column
     int ctx, cty;          // the tile holding the projected cube centre (dispatched first)
     float step, lo, inv_range, opacity_scale, term_alpha, ratio_floor;
-    int nz;
+    int nx, ny, nz;
     int filter, alpha_thr;  // shw_filter; the alpha-threshold option of spectral / first-moment colouring
     float tmin, tmax, tinv; // the filter's thresholds; 1 / (tmax - tmin) for domain scaling
 };
@@ -242,26 +242,78 @@ struct AvgState {
 };
 
 // Algorithm 3 in premultiplied form; stops after the sample that makes alpha > term
-struct CompositeState {
+// A sample's position along one axis as colouring uses it: the voxel for nearest
+// sampling, the point itself for trilinear (fixed point -> FP32); and its texture
+// coordinate (p + 1/2) / n in [0, 1].
+__device__ __forceinline__ float colour_pos(long long P, int n, bool nearest)
+{
+    return nearest ? (float)clampi(fx_round(P), 0, n - 1) : __fadd_rn((float)fx_cell(P), fx_frac(P));
+}
+__device__ __forceinline__ float tex_coord(float p, int n) { return fminf(fmaxf((p + 0.5f) / (float)n, 0.0f), 1.0f); }
+
+constexpr int kColourValue = 0, kColourSpectral = 1, kColourPosition = 2;
+
+// Algorithm 3 in premultiplied form; stops after the sample that makes alpha > term.
+// The colour comes from the value (Algorithm 3), from the map at the sample's spectral
+// position (Algorithm 5, AVIP_1) or from its position (Algorithm 7, AVIP_RGB); the
+// position then advances with the samples, which arrive in order.
+template <int COLOUR>
+struct CompositeStateT {
     float T = 1.0f, cr = 0.0f, cg = 0.0f, cb = 0.0f;
     const float4 *lut;
     float lo, inv_range, s, term;
     float *ckpt;  // this ray's first checkpoint slot, or null
     long long ckpt_stride;
     int I, nckpt;
+    long long X = 0, Y = 0, Z = 0, DX = 0, DY = 0, DZ = 0;  // COLOUR != value: the sample's position
+    int nx = 1, ny = 1, nz = 1;
+    bool nearest = false;
     __device__ __forceinline__ bool update(float v, int k)
     {
         if (ckpt != nullptr && (k % I) == 0 && k / I < nckpt) ckpt[(long long)(k / I) * ckpt_stride] = T;
         const float4 c = lut_eval(lut, normalise(v, lo, inv_range));
+        float r = c.x, g = c.y, b = c.z;
+        if constexpr (COLOUR == kColourSpectral) {
+            const float4 q = lut_eval(lut, tex_coord(colour_pos(Z, nz, nearest), nz));
+            r = q.x;
+            g = q.y;
+            b = q.z;
+        } else if constexpr (COLOUR == kColourPosition) {
+            r = tex_coord(colour_pos(Z, nz, nearest), nz);
+            g = tex_coord(colour_pos(Y, ny, nearest), ny);
+            b = tex_coord(colour_pos(X, nx, nearest), nx);
+        }
+        if constexpr (COLOUR != kColourValue) {
+            X += DX;
+            Y += DY;
+            Z += DZ;
+        }
         const float al = fminf(fmaxf(s * c.w, 0.0f), 1.0f);
         const float w = T * al;
-        cr = __fmaf_rn(w, c.x, cr);
-        cg = __fmaf_rn(w, c.y, cg);
-        cb = __fmaf_rn(w, c.z, cb);
+        cr = __fmaf_rn(w, r, cr);
+        cg = __fmaf_rn(w, g, cg);
+        cb = __fmaf_rn(w, b, cb);
         T = T * (1.0f - al);
         return 1.0f - T > term;
     }
 };
+using CompositeState = CompositeStateT<kColourValue>;
+
+// Algorithms 12-13 (line ratio, Method 1): each cube's running maximum (">")
+struct RatioMaxState {
+    float m1 = -INFINITY, m2 = -INFINITY;
+    int kmax = 0;
+    __device__ __forceinline__ void update2(float c1, float c2)
+    {
+        if (c1 > m1) m1 = c1;
+        if (c2 > m2) m2 = c2;
+    }
+};
+
+template <int MODE>
+constexpr bool is_composite = MODE == SHW_COMPOSITE || MODE == SHW_COMPOSITE_SPECTRAL || MODE == SHW_COMPOSITE_RGB;
+template <int MODE>
+constexpr bool two_cubes = MODE == SHW_RATIO || MODE == SHW_RATIO_MIP;
 
 // Eq. 4 along the ray: intensity-weighted mean height.  Weights are the intensity above
 // DATAMIN (NaN samples are DATAMIN already); the height is the sample's z (its channel
@@ -308,6 +360,18 @@ template <>
 struct StateOf<SHW_COMPOSITE> {
     using type = CompositeState;
 };
+template <>
+struct StateOf<SHW_COMPOSITE_SPECTRAL> {
+    using type = CompositeStateT<kColourSpectral>;
+};
+template <>
+struct StateOf<SHW_COMPOSITE_RGB> {
+    using type = CompositeStateT<kColourPosition>;
+};
+template <>
+struct StateOf<SHW_RATIO_MIP> {
+    using type = RatioMaxState;
+};
 
 // Samples [k0, k1) of one ray; true if the transfer function stopped the ray
 // (then kdone = samples processed).  X, Y, Z advance with the samples.
@@ -317,20 +381,27 @@ __device__ __forceinline__ bool march(const S &s, const S &s2, const RenderArgs 
                                       long long DY, long long DZ, int k0, int k1, int &kdone)
 {
     for (int k = k0; k < k1; ++k) {
-        float v;
-        if constexpr (MODE == SHW_RATIO) {
-            // Algorithm 14: ratio where cube1 exceeds the floor, else DATAMIN
+        if constexpr (MODE == SHW_RATIO_MIP) {
+            // Algorithm 13: each cube's maximum; a NaN sample counts as DATAMIN
             const float c1 = filter_value(sample<CLAMP, INTERP>(s, X, Y, Z, cc), a);
             const float c2 = filter_value(sample<CLAMP, INTERP>(s2, X, Y, Z, cc2), a);
-            v = (c1 > a.ratio_floor) ? __fdiv_rn(c2, c1) : a.lo;
+            st.update2(isnan(c1) ? a.lo : c1, isnan(c2) ? a.lo : c2);
         } else {
-            v = sample<CLAMP, INTERP>(s, X, Y, Z, cc);
-            v = filter_value(isnan(v) ? a.lo : v, a);
-        }
-        v = isnan(v) ? a.lo : v;  // a NaN sample counts as DATAMIN
-        if (st.update(v, k)) {
-            kdone = k + 1;
-            return true;
+            float v;
+            if constexpr (MODE == SHW_RATIO) {
+                // Algorithm 14: ratio where cube1 exceeds the floor, else DATAMIN
+                const float c1 = filter_value(sample<CLAMP, INTERP>(s, X, Y, Z, cc), a);
+                const float c2 = filter_value(sample<CLAMP, INTERP>(s2, X, Y, Z, cc2), a);
+                v = (c1 > a.ratio_floor) ? __fdiv_rn(c2, c1) : a.lo;
+            } else {
+                v = sample<CLAMP, INTERP>(s, X, Y, Z, cc);
+                v = filter_value(isnan(v) ? a.lo : v, a);
+            }
+            v = isnan(v) ? a.lo : v;  // a NaN sample counts as DATAMIN
+            if (st.update(v, k)) {
+                kdone = k + 1;
+                return true;
+            }
         }
         X += DX;
         Y += DY;
@@ -353,7 +424,7 @@ __device__ __forceinline__ bool march_interior(const S &s, const S &s2, const Re
                                                long long &Y, long long &Z, long long DX, long long DY, long long DZ,
                                                int k0, int k1, int &kdone)
 {
-    constexpr bool TWO = MODE == SHW_RATIO;
+    constexpr bool TWO = two_cubes<MODE>;
     if (k0 >= k1) {
         kdone = k1;
         return false;
@@ -373,8 +444,11 @@ __device__ __forceinline__ bool march_interior(const S &s, const S &s2, const Re
             if constexpr (TWO) s2.template corners<false>(nx, ny, nz, nxt2);
         }
         const float fx = fx_frac(X), fy = fx_frac(Y), fz = fx_frac(Z);
-        float v;
-        if constexpr (TWO) {
+        float v = 0.0f;
+        if constexpr (MODE == SHW_RATIO_MIP) {
+            const float c1 = filter_value(trilerp(cur, fx, fy, fz), a), c2 = filter_value(trilerp(cur2, fx, fy, fz), a);
+            st.update2(isnan(c1) ? a.lo : c1, isnan(c2) ? a.lo : c2);
+        } else if constexpr (TWO) {
             // Algorithm 14: ratio where cube1 exceeds the floor, else DATAMIN
             const float c1 = filter_value(trilerp(cur, fx, fy, fz), a), c2 = filter_value(trilerp(cur2, fx, fy, fz), a);
             v = (c1 > a.ratio_floor) ? __fdiv_rn(c2, c1) : a.lo;
@@ -382,10 +456,12 @@ __device__ __forceinline__ bool march_interior(const S &s, const S &s2, const Re
             v = trilerp(cur, fx, fy, fz);
             v = filter_value(isnan(v) ? a.lo : v, a);
         }
-        v = isnan(v) ? a.lo : v;  // a NaN sample counts as DATAMIN
-        if (st.update(v, k)) {
-            kdone = k + 1;
-            return true;
+        if constexpr (MODE != SHW_RATIO_MIP) {
+            v = isnan(v) ? a.lo : v;  // a NaN sample counts as DATAMIN
+            if (st.update(v, k)) {
+                kdone = k + 1;
+                return true;
+            }
         }
         if (pf) {
 #pragma unroll
@@ -406,12 +482,13 @@ __device__ __forceinline__ bool march_interior(const S &s, const S &s2, const Re
 }
 
 // setFragment (Algorithm 1): the outputs of one ray from its final transfer-function
-// state.  N: samples of the ray (0: it missed); PZ, DZ: its first sample's z and z step
-// (fixed point); done: samples processed.
+// state.  N: samples of the ray (0: it missed); P, D: its first sample and step (fixed
+// point, x y z); done: samples processed.
 template <int MODE, int INTERP, class St>
-__device__ __forceinline__ void emit_ray(const RenderArgs &a, long long pix, int N, long long PZ, long long DZ,
-                                         const St &st, int done)
+__device__ __forceinline__ void emit_ray(const RenderArgs &a, long long pix, int N, const long long P[3],
+                                         const long long D[3], const St &st, int done)
 {
+    const long long PZ = P[2], DZ = D[2];
     float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
     float scalar = 0.0f;
     int index = -1;
@@ -430,6 +507,23 @@ __device__ __forceinline__ void emit_ray(const RenderArgs &a, long long pix, int
                 out = make_float4(c.x, c.y, c.z, colour_alpha(st.m, a));
             } else {
                 out = lut_eval(a.lut, vh);
+            }
+        } else if constexpr (MODE == SHW_MIP_RGB) {
+            // Algorithm 6: (r, g, b) = the maximum's (z, y, x) as texture coordinates
+            const bool near = INTERP == SHW_NEAREST;
+            const long long km = (long long)st.kmax;
+            const float zm = colour_pos(PZ + km * DZ, a.nz, near);
+            index = clampi(fx_round(PZ + km * DZ), 0, a.nz - 1);
+            scalar = st.m;
+            out = make_float4(tex_coord(zm, a.nz), tex_coord(colour_pos(P[1] + km * D[1], a.ny, near), a.ny),
+                              tex_coord(colour_pos(P[0] + km * D[0], a.nx, near), a.nx), colour_alpha(st.m, a));
+        } else if constexpr (MODE == SHW_RATIO_MIP) {
+            // Algorithm 13: the colour of max2 / max1 where max1 passes the floor, else
+            // transparent black
+            scalar = a.lo;
+            if (st.m1 > a.ratio_floor) {
+                scalar = __fdiv_rn(st.m2, st.m1);
+                out = lut_eval(a.lut, normalise(scalar, a.lo, a.inv_range));
             }
         } else if constexpr (MODE == SHW_AVG) {
             scalar = __fdiv_rn(st.sum, (float)N);
@@ -478,7 +572,7 @@ __device__ __forceinline__ void render_pixel(const S &s, const S &s2, const shw_
         interior_range(r, s.nx, s.ny, s.nz, N, ka, kb);
         long long X = r.P[0], Y = r.P[1], Z = r.P[2];
         const long long DX = r.D[0], DY = r.D[1], DZ = r.D[2];
-        if constexpr (MODE == SHW_COMPOSITE) {
+        if constexpr (is_composite<MODE>) {
             st.lut = lut_c;
             st.lo = a.lo;
             st.inv_range = a.inv_range;
@@ -488,6 +582,18 @@ __device__ __forceinline__ void render_pixel(const S &s, const S &s2, const shw_
             st.ckpt_stride = npix;
             st.I = a.ckpt_interval;
             st.nckpt = a.nckpt;
+            if constexpr (MODE != SHW_COMPOSITE) {
+                st.X = r.P[0];
+                st.Y = r.P[1];
+                st.Z = r.P[2];
+                st.DX = r.D[0];
+                st.DY = r.D[1];
+                st.DZ = r.D[2];
+                st.nx = s.nx;
+                st.ny = s.ny;
+                st.nz = s.nz;
+                st.nearest = INTERP == SHW_NEAREST;
+            }
         }
         if constexpr (MODE == SHW_MOMENT1) {
             st.Z = r.P[2];
@@ -499,9 +605,9 @@ __device__ __forceinline__ void render_pixel(const S &s, const S &s2, const shw_
         CellCache cc, cc2;
         bool stop = march<true, MODE, INTERP>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, 0, ka, done);
         if (!stop) {
-            // (float32 only: for 16-bit bricks the extra registers cost more than the
-            // latency they hide)
-            if constexpr (INTERP == SHW_TRILINEAR && SHW_PREFETCH && S::kLinearF32) {
+            // (16-bit bricks: only for the line ratio, whose two gathers per sample leave
+            // the most latency to hide; otherwise the extra registers cost more)
+            if constexpr (INTERP == SHW_TRILINEAR && SHW_PREFETCH && (S::kLinearF32 || two_cubes<MODE>)) {
                 stop = march_interior<MODE>(s, s2, a, st, X, Y, Z, DX, DY, DZ, ka, kb, done);
                 cc.ix = cc2.ix = -4;  // the tail starts with a fresh cell
             } else {
@@ -511,7 +617,8 @@ __device__ __forceinline__ void render_pixel(const S &s, const S &s2, const shw_
         if (!stop) march<true, MODE, INTERP>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, kb, N, done);
 
     }
-    emit_ray<MODE, INTERP>(a, pix, N, N > 0 ? r.P[2] : 0, N > 0 ? r.D[2] : 0, st, done);
+    if (N <= 0) r.P[0] = r.P[1] = r.P[2] = r.D[0] = r.D[1] = r.D[2] = 0;
+    emit_ray<MODE, INTERP>(a, pix, N, r.P, r.D, st, done);
 }
 
 template <int MODE, int INTERP, class S>
@@ -519,7 +626,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_kernel(S s, S s2, shw_c
 {
     __shared__ float4 lut_s[kLut];
     const float4 *lut_c = a.lut;
-    if constexpr (MODE == SHW_COMPOSITE && SHW_LUT_SMEM) {
+    if constexpr (is_composite<MODE> && SHW_LUT_SMEM) {
         for (int i = threadIdx.x; i < kLut; i += blockDim.x) lut_s[i] = a.lut[i];
         __syncthreads();
         lut_c = lut_s;
@@ -640,6 +747,10 @@ shw_status launch_render_modes(int mode, int interp, const S &s, const S &s2, co
         SHW_CASE(SHW_SPECTRAL)
         SHW_CASE(SHW_RATIO)
         SHW_CASE(SHW_MOMENT1)
+        SHW_CASE(SHW_COMPOSITE_SPECTRAL)
+        SHW_CASE(SHW_MIP_RGB)
+        SHW_CASE(SHW_COMPOSITE_RGB)
+        SHW_CASE(SHW_RATIO_MIP)
     default:
         return SHW_EINVAL;
     }

@@ -269,10 +269,13 @@ static size_t smooth_tma_smem()
     return (size_t)(kSmStages * (kSmTY + 2 * R) * kSmBW + 2 * (kSmTY + 2 * R) * kSmTX) * 4;
 }
 
+#ifndef SHW_SMOOTH_ZC
+#define SHW_SMOOTH_ZC 128  // largest z chunk of one CTA (planes)
+#endif
 static int smooth_zchunk(int nx, int ny, int nz, int r)
 {
     const long long tiles = (long long)ceil_div(nx, 32) * ceil_div(ny, 32);
-    int zc = nz < 128 ? nz : 128;
+    int zc = nz < SHW_SMOOTH_ZC ? nz : SHW_SMOOTH_ZC;
     const int zmin = (4 * r > 16) ? 4 * r : 16;
     while (tiles * ceil_div(nz, zc) < 608 && zc / 2 >= zmin) zc /= 2;
     return zc;

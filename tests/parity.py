@@ -78,14 +78,14 @@ def compare(g, o, mode, *, scale, tol=TOL_F32, pixels=None, exact=False, max_fra
         assert stats["scalar_max_err"] <= tol * scale, f"{what}: scalar err {stats['scalar_max_err']} > {tol * scale}"
 
     # RGBA: spectral colour depends on which sample is the maximum -> skip near-ties
-    rok = vok & ((fr & F_TIE) == 0) if mode == "spectral" else vok
+    rok = vok & ((fr & F_TIE) == 0) if mode in ("spectral", "mip_rgb") else vok
     er = np.abs(gr[rok].astype(np.float64) - or_[rok])
     stats["rgba_max_err"] = float(er.max(initial=0.0))
     stats["rgba_rms_err"] = float(np.sqrt((er ** 2).mean())) if er.size else 0.0
     assert stats["rgba_max_err"] <= tol, f"{what}: rgba err {stats['rgba_max_err']} > {tol}"
 
     # channel of the maximum: exact unless near-tied (then any near-maximal channel is valid)
-    if mode in ("mip", "spectral", "ratio", "moment1"):
+    if mode in ("mip", "spectral", "ratio", "moment1", "mip_rgb"):
         iok = vok & ((fr & F_TIE) == 0)
         bad = np.flatnonzero(iok & (gi != oi))
         stats["index_mismatch"] = int(len(bad))

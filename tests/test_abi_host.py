@@ -94,7 +94,7 @@ def test_render_rejects_invalid_arguments_on_host(L):
         (_vol(data=0x1001), ok_c, ok_p, out),       # misaligned float32 cube
         (ok_v, _cam(W=0), ok_p, out),
         (ok_v, _cam(H=-3), ok_p, out),
-        (ok_v, ok_c, _params(mode=9), out),
+        (ok_v, ok_c, _params(mode=10), out),
         (ok_v, ok_c, _params(step=0.0), out),
         (ok_v, ok_c, _params(step=-1.0), out),
         (ok_v, ok_c, _params(step=float("nan")), out),
@@ -169,7 +169,9 @@ def test_batch_plan_rejects_invalid_arguments_on_host(L):
     items[1].mode = 4
     assert L.shw_batch_plan_create(b(h), items, 2, b(p), 0, None) == 2      # ratio: unsupported in a batch
     items[1].mode = 7
-    assert L.shw_batch_plan_create(b(h), items, 2, b(p), 0, None) == 1
+    assert L.shw_batch_plan_create(b(h), items, 2, b(p), 0, None) == 2      # MIP_RGB: unsupported in a batch
+    items[1].mode = 10
+    assert L.shw_batch_plan_create(b(h), items, 2, b(p), 0, None) == 1      # not a mode
     items[1].mode = 2
     items[1].out_rgba = 0x4004
     assert L.shw_batch_plan_create(b(h), items, 2, b(p), 0, None) == 1

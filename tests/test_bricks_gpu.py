@@ -89,3 +89,28 @@ def test_brick_render_parity(m, storage, mode, interp):
         return
     # against the unrounded cube: the reduced-precision bound
     compare(g, o, mode, scale=scale(o), tol=TOL_REDUCED, max_fragile=0.5, what=f"{storage}/{mode}/{interp} vs fp32")
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+@pytest.mark.parametrize("mode", ["moment1", "composite_spectral", "mip_rgb", "composite_rgb", "ratio_mip"])
+def test_brick_render_parity_other_modes(m, storage, mode):
+    """The first moment, the position-coloured modes and the ratio Method 1 on bricks: the
+    FP32 arithmetic on the rounded values (against the oracle on the rounded cube)."""
+    dims = (70, 45, 66)
+    cube = scene.tiny_cube(config_id=33, dims=dims, n_sources=3)
+    c2 = scene.ratio_cube(cube, config_id=33)
+    cam = scene.orbit_camera(dims, -25, 30, 80, 64)
+    lut = scene.ratio_lut() if mode == "ratio_mip" else scene.linear_lut()
+    kw = dict(lo=0.0, hi=1.0, ratio_floor=1.0) if mode == "ratio_mip" else (
+        dict(opacity_scale=0.05) if mode.startswith("composite") else {})
+    g = gpu_render(m, m.pack_bricks(to_dev(cube), storage), cam, mode, to_dev(lut),
+                   vol2=m.pack_bricks(to_dev(c2), storage), **kw)
+    rc, rc2 = ROUND[storage](cube), ROUND[storage](c2)
+    o = oracle.render(rc, cam, mode, lut=lut, cube2=rc2, eps_pos=1e-6, eps_val=1e-4, **kw)
+    if mode == "ratio_mip":
+        scale = float(o["scalar"].max() - o["scalar"].min()) or 1.0
+    elif mode == "moment1":
+        scale = float(dims[2])
+    else:
+        scale = 1.0 if mode.startswith("composite") else float(cube.max() - cube.min())
+    compare(g, o, mode, scale=scale, max_fragile=0.05, what=f"{storage}/{mode} vs rounded")

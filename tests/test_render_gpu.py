@@ -9,7 +9,8 @@ from parity import TOL_F32, compare, gpu_render, shw, to_dev
 
 pytestmark = pytest.mark.gpu
 
-MODES = ["mip", "avg", "composite", "spectral", "ratio", "moment1"]
+MODES = ["mip", "avg", "composite", "spectral", "ratio", "moment1", "composite_spectral", "mip_rgb",
+         "composite_rgb", "ratio_mip"]
 
 
 @pytest.fixture(scope="module")
@@ -24,18 +25,18 @@ def tiny():
 
 
 def _kw(mode):
-    if mode == "ratio":
+    if mode.startswith("ratio"):
         return dict(lo=0.0, hi=1.0, ratio_floor=1.0)
-    if mode == "composite":
+    if mode.startswith("composite"):
         return dict(opacity_scale=0.05)
     return {}
 
 
 def _scale(cube, mode, o):
-    if mode == "ratio":
+    if mode.startswith("ratio"):
         s = o["scalar"]
         return float(s.max() - s.min()) or 1.0
-    if mode == "composite":
+    if mode.startswith("composite"):
         return 1.0
     if mode == "moment1":
         return float(cube.shape[0])  # the moment is a height: its range is the channels
@@ -65,7 +66,7 @@ def test_ortho_nearest_mip_and_index_bit_exact(m, tiny):
 def test_ortho_axis_parity(m, tiny, mode, interp):
     cube, c2 = tiny
     cam = scene.ortho_axis_camera((64, 64, 64), 128, 128)
-    lut = scene.ratio_lut() if mode == "ratio" else scene.linear_lut()
+    lut = scene.ratio_lut() if mode.startswith("ratio") else scene.linear_lut()
     kw = _kw(mode)
     g = gpu_render(m, to_dev(cube), cam, mode, to_dev(lut), interp=interp, vol2=to_dev(c2), **kw)
     o = oracle.render(cube, cam, mode, interp=interp, lut=lut, cube2=c2, eps_pos=1e-6, eps_val=1e-4, **kw)
@@ -94,7 +95,7 @@ def test_general_view_parity(m, ragged, mode, interp, view):
         cam = scene.orbit_camera(RAGGED_DIMS, 137, -71, 83, 97, fov_deg=60)
     else:
         cam = scene.orbit_camera(RAGGED_DIMS, -52, 33, 90, 70, ortho=True)
-    lut = scene.ratio_lut() if mode == "ratio" else scene.linear_lut()
+    lut = scene.ratio_lut() if mode.startswith("ratio") else scene.linear_lut()
     kw = _kw(mode)
     g = gpu_render(m, to_dev(cube), cam, mode, to_dev(lut), interp=interp, vol2=to_dev(c2), **kw)
     o = oracle.render(cube, cam, mode, interp=interp, lut=lut, cube2=c2, eps_pos=1e-6, eps_val=1e-4, **kw)
@@ -207,11 +208,11 @@ def test_filters_parity(m, ragged, tiny, mode, filt, view):
     else:
         cube, c2 = ragged
         cam = scene.orbit_camera(RAGGED_DIMS, 30, 20, 100, 75)
-    lut = scene.ratio_lut() if mode == "ratio" else scene.linear_lut()
+    lut = scene.ratio_lut() if mode.startswith("ratio") else scene.linear_lut()
     kw = _kw(mode)
-    if kind == "scale" and mode != "ratio":
+    if kind == "scale" and not mode.startswith("ratio"):
         kw.update(lo=-0.5, hi=1.0)  # the scaled domain is [0, 1]; DATAMIN below it
-    if mode == "ratio":
+    if mode.startswith("ratio"):
         tmin, tmax = 0.5, 6.0
     f = dict(filter=kind, min_threshold=tmin, max_threshold=tmax)
     g = gpu_render(m, to_dev(cube), cam, mode, to_dev(lut), vol2=to_dev(c2), **kw, **f)
