@@ -53,6 +53,10 @@ def lib():
                                         C.c_double, C.c_double, C.c_double, lp, C.c_long, C.c_double,
                                         C.c_double, C.c_double, dp, dp, ip, ip, ucp]
             L.oracle_render2.argtypes = L.oracle_render.argtypes + [C.c_int, C.c_double, C.c_double, C.c_int]
+            L.oracle_fetch_counter.argtypes = [C.c_int]
+            L.oracle_fetches.restype = C.c_longlong
+            L.oracle_render3.argtypes = L.oracle_render2.argtypes + [C.c_int, C.c_int, C.c_int, C.c_double,
+                                                                     dp, dp]
             L.oracle_count_samples.argtypes = [C.c_int, C.c_int, C.c_int, dp, C.c_int, C.c_int, C.c_int,
                                                C.c_double, ip]
             L.oracle_count_samples.restype = C.c_longlong
@@ -86,17 +90,22 @@ def _cam_args(cam):
 
 
 FILTERS = {None: 0, "none": 0, "clip": 1, "scale": 2}
+SMOOTH = {None: 0, "none": 0, "box": 1, "taps": 2}
 
 
 def render(cube, cam, mode, *, interp="trilinear", step=0.5, lo=-3.0, hi=8.0, lut=None,
            opacity_scale=1.0, term_alpha=0.99, ratio_floor=0.0, cube2=None, pixels=None,
            eps_pos=0.0, eps_val=0.0, eps_exit=None, filter=None, min_threshold=0.0, max_threshold=0.0,
-           alpha_threshold=False):
+           alpha_threshold=False, smooth=None, smooth_arm=0, smooth_taps=None):
     """Render with the FP64 oracle.  Returns dict(rgba, scalar, index, nsamples, fragile).
 
     ``filter``: None, "clip" (Algorithm 10) or "scale" (Algorithm 11) with ``min_threshold`` /
     ``max_threshold``; ``alpha_threshold``: spectral / first-moment alpha 0 up to
     min_threshold, 1 above.
+
+    ``smooth``: None, "box" (Algorithm 8, ``smooth_arm`` neighbours each side along the ray)
+    or "taps" (Algorithm 9 per data axis, chained x, y, z) with ``smooth_taps`` =
+    (c0, offsets, weights).
 
     ``pixels``: optional array of row-major pixel ids; outputs then follow that list.
     ``eps_pos`` / ``eps_val`` / ``eps_exit``: margins (voxels / values / opacity) within which a
@@ -115,14 +124,24 @@ def render(cube, cam, mode, *, interp="trilinear", step=0.5, lo=-3.0, hi=8.0, lu
     n = W * H if pix is None else len(pix)
     rgba = np.zeros((n, 4)); scal = np.zeros(n)
     idx = np.zeros(n, np.int32); ns = np.zeros(n, np.int32); fr = np.zeros(n, np.uint8)
-    rc = L.oracle_render2(_ptr(cubed, C.c_double), _ptr(cube2d, C.c_double), nx, ny, nz,
+    kind = SMOOTH[smooth]
+    c0, toff, tw = 1.0, None, None
+    if kind == 2:
+        c0 = float(smooth_taps[0])
+        toff = _d(np.asarray(smooth_taps[1], dtype=np.float64).ravel())
+        tw = _d(np.asarray(smooth_taps[2], dtype=np.float64).ravel())
+        if len(toff) != len(tw):
+            raise ValueError("smooth_taps: offsets and weights differ in length")
+    ntap = 0 if toff is None else len(toff)
+    rc = L.oracle_render3(_ptr(cubed, C.c_double), _ptr(cube2d, C.c_double), nx, ny, nz,
                          _ptr(c14, C.c_double), ortho, W, H, MODES[mode], INTERP[interp],
                          float(step), float(lo), float(hi), _ptr(lutd, C.c_double),
                          float(opacity_scale), float(term_alpha), float(ratio_floor),
                          _ptr(pix, C.c_long), n, float(eps_pos), float(eps_val), float(eps_exit),
                          _ptr(rgba, C.c_double), _ptr(scal, C.c_double), _ptr(idx, C.c_int),
                          _ptr(ns, C.c_int), _ptr(fr, C.c_ubyte), FILTERS[filter], float(min_threshold),
-                         float(max_threshold), int(bool(alpha_threshold)))
+                         float(max_threshold), int(bool(alpha_threshold)), kind, int(smooth_arm), ntap, c0,
+                         _ptr(toff, C.c_double), _ptr(tw, C.c_double))
     if rc != 0:
         raise ValueError("oracle_render rejected its arguments")
     if pix is None:
@@ -185,6 +204,17 @@ def linear_sampling_merge(w):
     m = lib().oracle_linear_sampling_merge(_ptr(w, C.c_double), r, _ptr(off, C.c_double),
                                            _ptr(wt, C.c_double))
     return off[:m + 1], wt[:m + 1]
+
+
+def count_fetches(fn):
+    """Run fn() with the oracle's fetch counter on; returns (fn's result, cube fetches made)."""
+    L = lib()
+    L.oracle_fetch_counter(1)
+    try:
+        out = fn()
+        return out, int(L.oracle_fetches())
+    finally:
+        L.oracle_fetch_counter(0)
 
 
 def smooth(cube, w):

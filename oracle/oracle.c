@@ -17,6 +17,8 @@
  *   alpha compositing ......... Eq. 2, Algorithm 3 (AVIP_0, exit when alpha > 0.99)
  *   average ................... Eq. 3 (zeroth moment: orthographic ray sum)
  *   line ratio ................ Algorithm 14 (Method 2: per-sample ratio, then MIP_0)
+ *   in-ray smoothing .......... Algorithm 8 (box along the ray), Algorithm 9 (taps
+ *                               along each data axis, chained x, y, z)
  *   Gaussian smoothing ........ Eqs. 5-6 (sampled Gaussian, separable per axis),
  *                               binomial b_n = [1,1]^{*n} and Algorithm 9
  *   adjoint of compositing .... reverse mode over a stored per-sample tape
@@ -219,6 +221,11 @@ typedef struct {
     int filter;        /* 0 none, 1 intensity clipping (Algorithm 10), 2 domain scaling (Algorithm 11) */
     double tmin, tmax; /* the filters' minimum and maximum thresholds */
     int alpha_thr;     /* spectral / first-moment colouring: alpha 0 up to tmin, 1 above */
+    int smooth;        /* 0 none, 1 box along the ray (Algorithm 8), 2 per-axis taps (Algorithm 9) */
+    int arm;           /* box: neighbours visited on each side (filterArm) */
+    int ntap;          /* taps: fetches on each side of the sample per axis */
+    double c0;         /* taps: weight of the value entering each axis pass */
+    const double *toff, *tw; /* taps: offsets (voxels) and weights, ntap each */
 } oparams;
 
 #define OR_FILTER_NONE 0
@@ -280,14 +287,69 @@ static void nan_face_check(const ovol *V, const double p[3], double v, double ep
     }
 }
 
+/* Fetch counter (Section 6 counts texture fetches per ray step); counts only while enabled. */
+static int g_count_fetches = 0;
+static long long g_fetches = 0;
+
+void oracle_fetch_counter(int enable) { g_count_fetches = enable; g_fetches = 0; }
+long long oracle_fetches(void) { return g_fetches; }
+
 static double fetch(const ovol *V, int interp, const double p[3], double eps, int *frag)
 {
+    if (g_count_fetches) {
+#pragma omp atomic
+        ++g_fetches;
+    }
     if (interp == OR_NEAREST)
         return sample_nearest(V, p, eps, frag);
     double v = sample_trilinear(V, p);
     if (frag && eps > 0.0)
         nan_face_check(V, p, v, eps, frag);
     return v;
+}
+
+#define OR_SMOOTH_NONE 0
+#define OR_SMOOTH_BOX 1
+#define OR_SMOOTH_TAPS 2
+
+/* Algorithm 1's "val <- smooth(val)" (Section 4.1-4.2), applied to one cube's sample at
+ * p on a ray of unit direction d.
+ *
+ * Box (Algorithm 8): the sample plus arm neighbours on each side along the ray, one
+ * voxel apart (p +- i d, i = 1..arm), summed and scaled by 1/(2 arm + 1).
+ *
+ * Taps (Algorithm 9): one pass per data axis, x then y then z.  A pass starts from the
+ * value it is given (the raw sample for the x pass, the previous pass's result after
+ * that), weights it by c0 and adds w_j times the cube at p +- off_j along its axis.
+ * Every tap is a plain fetch of the cube, so a sample costs 1 + 6 ntap fetches. */
+static double smooth_fetch(const ovol *V, const oparams *P, const double p[3], const double d[3], int *frag)
+{
+    double val = fetch(V, P->interp, p, P->eps_pos, frag);
+    if (P->smooth == OR_SMOOTH_BOX) {
+        for (int i = 1; i <= P->arm; ++i) {
+            double fwd[3], back[3];
+            for (int a = 0; a < 3; ++a) {
+                fwd[a] = p[a] + i * d[a];
+                back[a] = p[a] - i * d[a];
+            }
+            val += fetch(V, P->interp, fwd, P->eps_pos, frag);
+            val += fetch(V, P->interp, back, P->eps_pos, frag);
+        }
+        val *= 1.0 / (2.0 * P->arm + 1.0);
+    } else if (P->smooth == OR_SMOOTH_TAPS) {
+        for (int axis = 0; axis < 3; ++axis) {
+            double out = val * P->c0;
+            for (int j = 0; j < P->ntap; ++j) {
+                double q[3] = {p[0], p[1], p[2]};
+                q[axis] = p[axis] + P->toff[j];
+                out += fetch(V, P->interp, q, P->eps_pos, frag) * P->tw[j];
+                q[axis] = p[axis] - P->toff[j];
+                out += fetch(V, P->interp, q, P->eps_pos, frag) * P->tw[j];
+            }
+            val = out;
+        }
+    }
+    return val;
 }
 
 /* The sample's z coordinate as used by spectral-position colouring: the channel of
@@ -370,8 +432,8 @@ static void render_ray(const ovol *V, const ovol *V2, const ocam *c, const opara
         double v;
         if (P->mode == OR_RATIO_MIP) {
             /* Algorithm 13: each cube's running maximum (">"; a NaN sample is DATAMIN) */
-            double c1 = filter_value(P, fetch(V, P->interp, p, P->eps_pos, frag), frag);
-            double c2 = filter_value(P, fetch(V2, P->interp, p, P->eps_pos, frag), frag);
+            double c1 = filter_value(P, smooth_fetch(V, P, p, d, frag), frag);
+            double c2 = filter_value(P, smooth_fetch(V2, P, p, d, frag), frag);
             if (isnan(c1)) c1 = P->lo;
             if (isnan(c2)) c2 = P->lo;
             if (c1 > m1) m1 = c1;
@@ -381,8 +443,8 @@ static void render_ray(const ovol *V, const ovol *V2, const ocam *c, const opara
         }
         if (P->mode == OR_RATIO) {
             /* Algorithm 14: val = cube2/cube1 where cube1 > 0 (threshold f), else DATAMIN */
-            double c1 = filter_value(P, fetch(V, P->interp, p, P->eps_pos, frag), frag);
-            double c2 = filter_value(P, fetch(V2, P->interp, p, P->eps_pos, frag), frag);
+            double c1 = filter_value(P, smooth_fetch(V, P, p, d, frag), frag);
+            double c2 = filter_value(P, smooth_fetch(V2, P, p, d, frag), frag);
             v = (c1 > P->ratio_floor) ? c2 / c1 : P->lo;
             if (frag && P->eps_val > 0.0 && fabs(c1 - P->ratio_floor) < P->eps_val) {
                 double alt = (c1 > P->ratio_floor) ? P->lo : c2 / c1; /* the other branch */
@@ -391,7 +453,7 @@ static void render_ray(const ovol *V, const ovol *V2, const ocam *c, const opara
                 if (hi2 > near_ratio) near_ratio = hi2;
             }
         } else {
-            v = fetch(V, P->interp, p, P->eps_pos, frag);
+            v = smooth_fetch(V, P, p, d, frag);
             if (isnan(v))
                 v = P->lo; /* NaN sample -> DATAMIN */
             v = filter_value(P, v, frag);
@@ -571,13 +633,14 @@ static void render_ray(const ovol *V, const ovol *V2, const ocam *c, const opara
 
 /* Render the pixels listed in pix (row-major pixel ids), or every pixel when pix is NULL.
  * Outputs are indexed by list position.  Any output pointer may be NULL. */
-int oracle_render2(const double *cube, const double *cube2, int nx, int ny, int nz,
-                  const double *cam14, int ortho, int W, int H,
-                  int mode, int interp, double step, double lo, double hi,
-                  const double *lut, double opacity_scale, double term_alpha, double ratio_floor,
-                  const long *pix, long npix, double eps_pos, double eps_val, double eps_exit,
-                  double *out_rgba, double *out_scalar, int *out_index, int *out_nsamples,
-                   unsigned char *out_fragile, int filter, double tmin, double tmax, int alpha_thr)
+int oracle_render3(const double *cube, const double *cube2, int nx, int ny, int nz,
+                   const double *cam14, int ortho, int W, int H,
+                   int mode, int interp, double step, double lo, double hi,
+                   const double *lut, double opacity_scale, double term_alpha, double ratio_floor,
+                   const long *pix, long npix, double eps_pos, double eps_val, double eps_exit,
+                   double *out_rgba, double *out_scalar, int *out_index, int *out_nsamples,
+                   unsigned char *out_fragile, int filter, double tmin, double tmax, int alpha_thr,
+                   int smooth, int arm, int ntap, double c0, const double *toff, const double *tw)
 {
     if (!cube || nx <= 0 || ny <= 0 || nz <= 0 || W <= 0 || H <= 0 || !(step > 0.0) || !lut)
         return 1;
@@ -590,8 +653,11 @@ int oracle_render2(const double *cube, const double *cube2, int nx, int ny, int 
     if (filter < OR_FILTER_NONE || filter > OR_FILTER_SCALE || (filter != OR_FILTER_NONE && !(tmin <= tmax)) ||
         (filter == OR_FILTER_SCALE && !(tmin < tmax)) || (alpha_thr != 0 && alpha_thr != 1))
         return -1;
+    if (smooth < OR_SMOOTH_NONE || smooth > OR_SMOOTH_TAPS || (smooth == OR_SMOOTH_BOX && arm < 0) ||
+        (smooth == OR_SMOOTH_TAPS && (ntap < 0 || (ntap > 0 && (!toff || !tw)))))
+        return -1;
     oparams P = {mode, interp, step, lo, hi, opacity_scale, term_alpha, ratio_floor, eps_pos, eps_val, eps_exit, lut,
-                 filter, tmin, tmax, alpha_thr};
+                 filter, tmin, tmax, alpha_thr, smooth, arm, ntap, c0, toff, tw};
     long n = pix ? npix : (long)W * H;
 #pragma omp parallel for schedule(dynamic, 64)
     for (long q = 0; q < n; ++q) {
@@ -609,6 +675,21 @@ int oracle_render2(const double *cube, const double *cube2, int nx, int ny, int 
         if (out_fragile) out_fragile[q] = (unsigned char)fr;
     }
     return 0;
+}
+
+/* The same without smoothing (Algorithm 1 with smooth(val) = val). */
+int oracle_render2(const double *cube, const double *cube2, int nx, int ny, int nz,
+                   const double *cam14, int ortho, int W, int H,
+                   int mode, int interp, double step, double lo, double hi,
+                   const double *lut, double opacity_scale, double term_alpha, double ratio_floor,
+                   const long *pix, long npix, double eps_pos, double eps_val, double eps_exit,
+                   double *out_rgba, double *out_scalar, int *out_index, int *out_nsamples,
+                   unsigned char *out_fragile, int filter, double tmin, double tmax, int alpha_thr)
+{
+    return oracle_render3(cube, cube2, nx, ny, nz, cam14, ortho, W, H, mode, interp, step, lo, hi, lut,
+                          opacity_scale, term_alpha, ratio_floor, pix, npix, eps_pos, eps_val, eps_exit, out_rgba,
+                          out_scalar, out_index, out_nsamples, out_fragile, filter, tmin, tmax, alpha_thr,
+                          OR_SMOOTH_NONE, 0, 0, 1.0, NULL, NULL);
 }
 
 /* The same without a filter (Algorithm 1 with filter(val) = val). */
