@@ -468,8 +468,51 @@ def run_variants(shw, torch, step, W, per_kernel, samples_per, peaks):
     t_bw = _timeit(torch, lambda: shw.render_backward(cube, cam, g_rgba, fw["ckpt"], grad_vol=g_vol, grad_lut=g_lut,
                                                       grad_scale=g_s, **kw))
     res["adjoint"] = {"workload": D["name"], "forward_ms": round(t_fw, 4), "backward_ms": round(t_bw, 4)}
+    del cube, fw, g_rgba, g_vol
+    res["in_ray_smoothing"] = run_in_ray_smoothing(shw, torch, dev)
     shw.sync_status()
     return res
+
+
+def run_in_ray_smoothing(shw, torch, dev):
+    """In-ray smoothing (Algorithms 8-9) on the paper's benchmark shape: frame time and
+    fetch rate of MIP and clipped compositing for raw sampling, the N-box filters and the
+    N-tap Gaussians (the 9-tap is Algorithm 9's printed kernel), median over the views."""
+    P = WL.PAPER_SMOOTH
+    n = P["n"]
+    cube = torch.from_numpy(scene.paper_uniform_cube(n)).to(dev)
+    lut = torch.from_numpy(scene.linear_lut()).to(dev)
+    kernels = [("raw", {}, 1)]
+    kernels += [(f"box{2 * a + 1}", dict(smooth="box", smooth_arm=a), 2 * a + 1) for a in P["box_arms"]]
+    for N in P["gauss_taps"]:
+        taps = shw.binomial_taps(9, drop=2) if N == 9 else shw.binomial_taps(N)
+        kernels.append((f"gauss{N}", dict(smooth="taps", smooth_taps=taps), 1 + 6 * len(taps[1])))
+    modes = {"mip": dict(lo=P["lo"], hi=P["hi"]),
+             "composite": dict(lo=P["lo"], hi=P["hi"], opacity_scale=P["opacity_scale"], filter="clip",
+                               min_threshold=P["clip"][0], max_threshold=P["clip"][1])}
+    out = {}
+    for m, mkw in modes.items():
+        rows = {}
+        for name, skw, fetches in kernels:
+            ts, ss = [], []
+            for yaw in P["yaws"]:
+                cam = scene.orbit_camera((n, n, n), yaw, P["pitch"], P["width"], P["height"])
+                o = shw.render(cube, cam, m, lut=lut, step=P["step"], scalar=False, index=False, **mkw, **skw)
+                ss.append(int(o["nsamples"].sum(dtype=torch.int64).item()))
+                o = {"rgba": o["rgba"]}
+                ts.append(_timeit(torch, lambda: shw.render(cube, cam, m, lut=lut, step=P["step"], scalar=False,
+                                                            index=False, nsamples=False, out=o, **mkw, **skw),
+                                  reps=3, warm=1))
+            k = int(np.argsort(ts)[len(ts) // 2])
+            t, ns = ts[k], ss[k]
+            rows[name] = {"fetches_per_step": fetches, "ms": round(t, 3), "fps": round(1e3 / t, 1),
+                          "gsamples_per_s": round(ns / (t * 1e-3) / 1e9, 2),
+                          "gfetches_per_s": round(fetches * ns / (t * 1e-3) / 1e9, 1)}
+        out[m] = rows
+    del cube
+    return {"workload": P["name"], "views": f"yaw {list(P['yaws'])}, pitch {P['pitch']}; median view",
+            "compositing": f"opacity scale {P['opacity_scale']}, clip [{P['clip'][0]}, {P['clip'][1]}]",
+            "modes": out}
 
 
 # --------------------------------------------------------------------------- oracle (CPU) arm
@@ -560,6 +603,10 @@ def run_case(args):
     if args.case == "smooth":
         out = torch.empty_like(cube)
         fn = lambda: shw.smooth(cube, WL.SURVEY["sigma"], WL.SURVEY["radius"], out=out)  # noqa: E731
+    elif args.case == "in-ray-smoothing":
+        print(json.dumps(run_in_ray_smoothing(shw, torch, "cuda")), flush=True)
+        shw.sync_status()
+        return
     else:
         cam = ortho_axis_camera((nx, ny, nz), nx, ny) if args.case == "moment-map" else \
             scene.orbit_camera((nx, ny, nz), 30.0, 20.0, 960, 540)
@@ -584,7 +631,7 @@ def main():
     ap.add_argument("--workload", default="survey", choices=sorted(WORKLOADS),
                     help="survey: the headline workload; survey-small: the same step on a smaller cube "
                          "(profiler captures)")
-    ap.add_argument("--case", choices=["moment-map", "render", "smooth"],
+    ap.add_argument("--case", choices=["moment-map", "render", "smooth", "in-ray-smoothing"],
                     help="run one small case of one kernel family for a profiler capture, then exit")
     ap.add_argument("--dims", default="384,384,768", help="--case: cube dims nx,ny,nz")
     ap.add_argument("--mode", default="mip", help="--case: transfer function")

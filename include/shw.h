@@ -45,9 +45,11 @@
 extern "C" {
 #endif
 
-#define SHW_ABI_VERSION 2
+#define SHW_ABI_VERSION 3
 #define SHW_LUT_SIZE 256
 #define SHW_MAX_SMOOTH_RADIUS 16
+#define SHW_MAX_SMOOTH_ARM 16   /* in-ray box smoothing: neighbours on each side */
+#define SHW_MAX_SMOOTH_TAPS 4   /* in-ray tap smoothing: fetches on each side per axis */
 #define SHW_BRICK 32        /* brick edge of the reduced-precision storage, voxels */
 #define SHW_BRICK_APRON 1   /* replicated border kept around every brick, voxels */
 
@@ -125,7 +127,33 @@ typedef struct {
     int32_t alpha_threshold; /* SHW_SPECTRAL / SHW_MOMENT1: 0 = alpha from the value; 1 = alpha 0 when the
                                 value that sets it is <= min_threshold, else 1 (the paper's remedy for
                                 faint first-moment-style images) */
+    int32_t smooth;          /* shw_smooth_kind: per-sample smoothing of each fetched value, before the
+                                filter (Algorithm 1's "smooth"; Sections 4.1-4.2) */
+    int32_t smooth_arm;      /* SHW_SMOOTH_BOX: neighbours on each side, 0..SHW_MAX_SMOOTH_ARM */
+    int32_t smooth_ntaps;    /* SHW_SMOOTH_TAPS: fetches on each side of the sample per axis,
+                                0..SHW_MAX_SMOOTH_TAPS */
+    float smooth_c0;         /* SHW_SMOOTH_TAPS: weight of the value entering each axis pass */
+    float smooth_offset[SHW_MAX_SMOOTH_TAPS]; /* SHW_SMOOTH_TAPS: fetch offsets along the axis, voxels,
+                                                 |offset| <= 64 (first smooth_ntaps used) */
+    float smooth_weight[SHW_MAX_SMOOTH_TAPS]; /* SHW_SMOOTH_TAPS: weight of each of the two fetches at
+                                                 +-offset (first smooth_ntaps used) */
 } shw_render_params;
+
+/* In-ray smoothing of every fetched sample (the cube lookups of Algorithm 1; both cubes
+ * for the line ratios).  Reads beyond the cube clamp to the edge voxel like every fetch.
+ * Only the general marcher applies it: batch plans and the adjoint reject it
+ * (SHW_EUNSUPPORTED). */
+typedef enum {
+    SHW_SMOOTH_NONE = 0,
+    SHW_SMOOTH_BOX = 1, /* Algorithm 8: (v(p) + sum_{i=1..arm} v(p + i u) + v(p - i u)) / (2 arm + 1),
+                           u the ray's unit direction (neighbours one voxel apart along the ray);
+                           2 arm + 1 fetches per sample */
+    SHW_SMOOTH_TAPS = 2 /* Algorithm 9 once per data axis e = x, then y, then z, each pass starting from
+                           the previous pass's value (the raw sample for x):
+                           val <- c0 val + sum_j w_j (v(p + off_j e) + v(p - off_j e));
+                           1 + 6 ntaps fetches per sample (Section 6's 3(N-1)/2 + 1 for an N-tap
+                           kernel merged by linear sampling, e.g. Algorithm 9's 9-tap: ntaps = 2) */
+} shw_smooth_kind;
 
 typedef enum {
     SHW_FILTER_NONE = 0,

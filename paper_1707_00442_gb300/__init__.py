@@ -6,9 +6,11 @@ from .api import (  # noqa: F401
     BatchPlan,
     BrickVolume,
     ShwError,
+    binomial_taps,
     bricked_bytes,
     ckpt_bytes,
     launch_count,
+    linear_sampling_taps,
     pack_bricks,
     render,
     render_backward,

@@ -18,7 +18,7 @@ MODES = {"mip": 0, "avg": 1, "composite": 2, "spectral": 3, "ratio": 4, "moment1
          "composite_spectral": 6, "mip_rgb": 7, "composite_rgb": 8, "ratio_mip": 9}
 INTERP = {"nearest": 0, "trilinear": 1}
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
-ABI_VERSION = 2
+ABI_VERSION = 3
 LUT_SIZE = 256
 MAX_SMOOTH_RADIUS = 16
 BRICK = 32
@@ -41,9 +41,13 @@ class RenderParams(C.Structure):
                 ("hi", C.c_float), ("lut", C.c_void_p), ("opacity_scale", C.c_float),
                 ("term_alpha", C.c_float), ("ratio_floor", C.c_float), ("ckpt_interval", C.c_int32),
                 ("filter", C.c_int32), ("min_threshold", C.c_float), ("max_threshold", C.c_float),
-                ("alpha_threshold", C.c_int32)]
+                ("alpha_threshold", C.c_int32), ("smooth", C.c_int32), ("smooth_arm", C.c_int32),
+                ("smooth_ntaps", C.c_int32), ("smooth_c0", C.c_float), ("smooth_offset", C.c_float * 4),
+                ("smooth_weight", C.c_float * 4)]
 
 FILTERS = {None: 0, "none": 0, "clip": 1, "scale": 2}
+SMOOTH = {None: 0, "none": 0, "box": 1, "taps": 2}
+MAX_SMOOTH_TAPS = 4
 
 
 class BatchItem(C.Structure):

@@ -73,14 +73,66 @@ def camera_struct(cam) -> _lib.Camera:
 
 def params_struct(mode, lut, *, interp="trilinear", step=0.5, lo=-3.0, hi=8.0, opacity_scale=1.0,
                   term_alpha=0.99, ratio_floor=0.0, ckpt_interval=64, filter=None, min_threshold=0.0,
-                  max_threshold=0.0, alpha_threshold=False) -> _lib.RenderParams:
+                  max_threshold=0.0, alpha_threshold=False, smooth=None, smooth_arm=0,
+                  smooth_taps=None) -> _lib.RenderParams:
+    """``smooth``: None, "box" (``smooth_arm`` neighbours each side along the ray) or "taps"
+    with ``smooth_taps`` = (c0, offsets, weights), e.g. from linear_sampling_taps()."""
     _need_cuda(lut, "lut", torch.float32)
     if lut.numel() != 4 * _lib.LUT_SIZE:
         raise ValueError("lut must hold 256 RGBA entries")
-    return _lib.RenderParams(MODES[mode], INTERP[interp], float(step), float(lo), float(hi), lut.data_ptr(),
-                             float(opacity_scale), float(term_alpha), float(ratio_floor), int(ckpt_interval),
-                             _lib.FILTERS[filter], float(min_threshold), float(max_threshold),
-                             int(bool(alpha_threshold)))
+    p = _lib.RenderParams(MODES[mode], INTERP[interp], float(step), float(lo), float(hi), lut.data_ptr(),
+                          float(opacity_scale), float(term_alpha), float(ratio_floor), int(ckpt_interval),
+                          _lib.FILTERS[filter], float(min_threshold), float(max_threshold),
+                          int(bool(alpha_threshold)))
+    p.smooth = _lib.SMOOTH[smooth]
+    if p.smooth == 1:
+        p.smooth_arm = int(smooth_arm)
+    elif p.smooth == 2:
+        c0, offs, wts = smooth_taps
+        offs, wts = [float(x) for x in offs], [float(x) for x in wts]
+        if len(offs) != len(wts) or len(offs) > _lib.MAX_SMOOTH_TAPS:
+            raise ValueError(f"smooth_taps: at most {_lib.MAX_SMOOTH_TAPS} offsets, one weight each")
+        p.smooth_ntaps = len(offs)
+        p.smooth_c0 = float(c0)
+        for j, (o, w) in enumerate(zip(offs, wts)):
+            p.smooth_offset[j] = o
+            p.smooth_weight[j] = w
+    return p
+
+
+def linear_sampling_taps(w):
+    """Fold a symmetric 1-D kernel w[-r..r] into the fetches of SHW_SMOOTH_TAPS (Section 4.2's
+    linear-sampling trick behind Algorithm 9): the centre keeps w_0; taps a and a+1 (a = 1, 3,
+    ...) become one fetch of weight w_a + w_{a+1} at the offset where linear interpolation
+    between them gives their weighted sum.  Returns (c0, offsets, weights)."""
+    w = [float(x) for x in w]
+    if len(w) % 2 != 1:
+        raise ValueError("the kernel must have odd length 2r+1")
+    r = (len(w) - 1) // 2
+    offs, wts = [], []
+    for a in range(1, r + 1, 2):
+        wa = w[r + a]
+        wb = w[r + a + 1] if a + 1 <= r else 0.0
+        tot = wa + wb
+        offs.append((a * wa + (a + 1) * wb) / tot if tot != 0.0 else float(a))
+        wts.append(tot)
+    return w[r], offs, wts
+
+
+def binomial_taps(ntaps: int, drop: int = 0):
+    """The N-tap binomial filter of Section 4.2 folded for SHW_SMOOTH_TAPS: b_{N-1+2 drop}
+    = [1, 1]^{*(N-1+2 drop)} without its `drop` outer taps on each side, renormalised.
+    ntaps = 5, 9, 13 with drop = 0 are b_4, b_8, b_12; ntaps = 9, drop = 2 is the kernel
+    whose folded constants Algorithm 9 prints."""
+    if ntaps < 1 or ntaps % 2 != 1 or drop < 0:
+        raise ValueError("ntaps must be odd and positive, drop >= 0")
+    n = ntaps - 1 + 2 * drop
+    row = [1]
+    for _ in range(n):
+        row = [a + b for a, b in zip([0] + row, row + [0])]
+    core = row[drop:len(row) - drop]
+    tot = float(sum(core))
+    return linear_sampling_taps([c / tot for c in core])
 
 
 def smooth(cube: torch.Tensor, sigma: float, radius: int, out: torch.Tensor | None = None) -> torch.Tensor:
@@ -134,7 +186,7 @@ def ckpt_bytes(vol, cam, *, step=0.5, ckpt_interval=64) -> int:
 def render(vol, cam, mode: str, *, lut: torch.Tensor, interp="trilinear", step=0.5, lo=-3.0, hi=8.0,
            opacity_scale=1.0, term_alpha=0.99, ratio_floor=0.0, vol2=None, scalar=True, index=True,
            nsamples=True, ckpt=False, ckpt_interval=64, out=None, filter=None, min_threshold=0.0,
-           max_threshold=0.0, alpha_threshold=False) -> dict:
+           max_threshold=0.0, alpha_threshold=False, smooth=None, smooth_arm=0, smooth_taps=None) -> dict:
     """Render one image (shw_render).  Returns a dict of CUDA tensors:
     rgba [H, W, 4] and optionally scalar [H, W], index [H, W], nsamples [H, W], ckpt (bytes).
     ``out``: optional dict of preallocated tensors with the same keys."""
@@ -143,7 +195,8 @@ def render(vol, cam, mode: str, *, lut: torch.Tensor, interp="trilinear", step=0
     c = camera_struct(cam)
     p = params_struct(mode, lut, interp=interp, step=step, lo=lo, hi=hi, opacity_scale=opacity_scale,
                       term_alpha=term_alpha, ratio_floor=ratio_floor, ckpt_interval=ckpt_interval, filter=filter,
-                      min_threshold=min_threshold, max_threshold=max_threshold, alpha_threshold=alpha_threshold)
+                      min_threshold=min_threshold, max_threshold=max_threshold, alpha_threshold=alpha_threshold,
+                      smooth=smooth, smooth_arm=smooth_arm, smooth_taps=smooth_taps)
     dev = lut.device
     H, W = c.height, c.width
     out = dict(out or {})

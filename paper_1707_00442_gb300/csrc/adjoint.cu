@@ -191,7 +191,8 @@ extern "C" shw_status shw_render_backward(const shw_volume *vol, const shw_camer
     if (p->ckpt_interval <= 0) return SHW_EINVAL;
     if (p->ckpt_interval > kMaxCkptInterval) return SHW_EUNSUPPORTED;
     if (vol->storage != SHW_F32) return SHW_EUNSUPPORTED;
-    if (p->filter != SHW_FILTER_NONE) return SHW_EUNSUPPORTED;  // the adjoint has no filter
+    if (p->filter != SHW_FILTER_NONE || p->smooth != SHW_SMOOTH_NONE)
+        return SHW_EUNSUPPORTED;  // the adjoint has no filter and no smoothing
     if ((grad_vol && !aligned(grad_vol, 4)) || (grad_lut && !aligned(grad_lut, 4)) ||
         (grad_scale && !aligned(grad_scale, 4)))
         return SHW_EINVAL;

@@ -162,6 +162,16 @@ bool valid_params(const shw_render_params *p, const shw_volume *v)
     if (p->filter == SHW_FILTER_SCALE &&
         (!(p->min_threshold < p->max_threshold) || !std::isfinite(1.0f / (p->max_threshold - p->min_threshold))))
         return false;
+    if (p->smooth < SHW_SMOOTH_NONE || p->smooth > SHW_SMOOTH_TAPS) return false;
+    if (p->smooth == SHW_SMOOTH_BOX && (p->smooth_arm < 0 || p->smooth_arm > SHW_MAX_SMOOTH_ARM)) return false;
+    if (p->smooth == SHW_SMOOTH_TAPS) {
+        if (p->smooth_ntaps < 0 || p->smooth_ntaps > SHW_MAX_SMOOTH_TAPS || !std::isfinite(p->smooth_c0))
+            return false;
+        for (int j = 0; j < p->smooth_ntaps; ++j)
+            if (!std::isfinite(p->smooth_weight[j]) || !std::isfinite(p->smooth_offset[j]) ||
+                std::fabs(p->smooth_offset[j]) > 64.0f)
+                return false;
+    }
     return true;
 }
 
@@ -274,6 +284,19 @@ shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_c
     a.nx = vol->nx;
     a.ny = vol->ny;
     a.nz = vol->nz;
+    a.smooth = p->smooth;
+    if (p->smooth == SHW_SMOOTH_BOX) {
+        a.smooth_n = p->smooth_arm;
+        a.smooth_c0 = (float)(1.0 / (2.0 * p->smooth_arm + 1.0));
+    } else if (p->smooth == SHW_SMOOTH_TAPS) {
+        a.smooth_n = p->smooth_ntaps;
+        a.smooth_c0 = p->smooth_c0;
+        for (int j = 0; j < p->smooth_ntaps; ++j) {
+            // the offset in 32.32 fixed point (exact for any float of magnitude <= 64 and >= 2^-9)
+            a.smooth_off[j] = std::llrint((double)p->smooth_offset[j] * 4294967296.0);
+            a.smooth_w[j] = p->smooth_weight[j];
+        }
+    }
     a.nmax = (int)max_samples(vol, p->step);
     a.warp_shift = warp_shift_for(*cam);
     a.ckpt_interval = p->ckpt_interval > 0 ? p->ckpt_interval : 64;
@@ -286,6 +309,9 @@ shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_c
     }
     const shw_volume *v2 = (p->mode == SHW_RATIO || p->mode == SHW_RATIO_MIP) ? vol2 : nullptr;
     cudaStream_t st = as_stream(stream);
+    if (p->smooth != SHW_SMOOTH_NONE)
+        return vol->storage == SHW_F32 ? render_smooth_f32(p->mode, p->interp, *vol, v2, *cam, a, st)
+                                       : render_smooth_b16(p->mode, p->interp, *vol, v2, *cam, a, st);
     // orthographic views down the spectral axis: the plane sweep, when it applies
     const shw_status sa = render_axis(p->mode, p->interp, *vol, *cam, a, st);
     if (sa != SHW_EUNSUPPORTED) return sa;

@@ -292,7 +292,8 @@ shw_status shw_batch_plan_create(shw_batch_plan **out, const shw_batch_item *ite
     *out = nullptr;
     if (!items || n <= 0 || !p || !p->lut || !aligned(p->lut, 16)) return SHW_EINVAL;
     if (p->interp != SHW_NEAREST && p->interp != SHW_TRILINEAR) return SHW_EINVAL;
-    if (p->filter != SHW_FILTER_NONE || p->alpha_threshold != 0) return SHW_EUNSUPPORTED;  // not in batch plans
+    if (p->filter != SHW_FILTER_NONE || p->alpha_threshold != 0 || p->smooth != SHW_SMOOTH_NONE)
+        return SHW_EUNSUPPORTED;  // not in batch plans
     if (!std::isfinite(p->step) || !(p->step > 0.0f) || !(p->hi > p->lo) || !std::isfinite(p->lo) ||
         !std::isfinite(p->hi) || !std::isfinite(p->opacity_scale) || !std::isfinite(p->term_alpha))
         return SHW_EINVAL;
@@ -458,7 +459,8 @@ extern "C" shw_status shw_render_batch_noalloc(const shw_batch_item *items, int3
 {
     if (!items || n <= 0 || !p || !p->lut || !aligned(p->lut, 16)) return SHW_EINVAL;
     if (p->interp != SHW_NEAREST && p->interp != SHW_TRILINEAR) return SHW_EINVAL;
-    if (p->filter != SHW_FILTER_NONE || p->alpha_threshold != 0) return SHW_EUNSUPPORTED;  // not in batch plans
+    if (p->filter != SHW_FILTER_NONE || p->alpha_threshold != 0 || p->smooth != SHW_SMOOTH_NONE)
+        return SHW_EUNSUPPORTED;  // not in batch plans
     if (!std::isfinite(p->step) || !(p->step > 0.0f) || !(p->hi > p->lo) || !std::isfinite(p->lo) ||
         !std::isfinite(p->hi) || !std::isfinite(p->opacity_scale) || !std::isfinite(p->term_alpha))
         return SHW_EINVAL;

@@ -115,10 +115,12 @@ __device__ __forceinline__ long long ff_to_fx(ff v)
     return __float2ll_rn(__fmul_rn(v.hi, 4294967296.0f)) + __float2ll_rn(__fmul_rn(v.lo, 4294967296.0f));
 }
 
-// A ray in 32.32 fixed point: sample k is at P + k*D; N samples.
+// A ray in 32.32 fixed point: sample k is at P + k*D; N samples; U: the unit
+// direction (one voxel along the ray).
 struct RayFx {
     long long P[3];
     long long D[3];
+    long long U[3];
     int N;
 };
 
@@ -198,6 +200,7 @@ __device__ __forceinline__ bool setup_ray(const shw_camera &c, int px, int py, i
     for (int a = 0; a < 3; ++a) {
         r.P[a] = ff_to_fx(ff_add(o[a], ff_mul(ts, d[a])));
         r.D[a] = ff_to_fx(ff_mul(hf, d[a]));
+        r.U[a] = ff_to_fx(d[a]);
     }
     return true;
 }

@@ -25,7 +25,7 @@ shw_status render_axis(int mode, int interp, const shw_volume &v, const shw_came
     if (!axis_eligible(v, c, mode)) return SHW_EUNSUPPORTED;
     // (a per-sample filter would sit in the sweep's innermost loop: filtered views take the
     // general marcher)
-    if (a.filter != SHW_FILTER_NONE) return SHW_EUNSUPPORTED;
+    if (a.filter != SHW_FILTER_NONE || a.smooth != SHW_SMOOTH_NONE) return SHW_EUNSUPPORTED;
     // pixel -> (x, y) is affine for a parallel projection
     const double W = c.width, H = c.height, aspect = W / H;
     const double hw = (double)c.ortho_half_h * aspect, hh = c.ortho_half_h;

@@ -40,6 +40,11 @@ struct RenderArgs {
     int nx, ny, nz;
     int filter, alpha_thr;  // shw_filter; the alpha-threshold option of spectral / first-moment colouring
     float tmin, tmax, tinv; // the filter's thresholds; 1 / (tmax - tmin) for domain scaling
+    int smooth;             // shw_smooth_kind of in-ray smoothing
+    int smooth_n;           // box: neighbours on each side; taps: fetches on each side per axis
+    float smooth_c0;        // box: 1 / (2 arm + 1); taps: weight of the value entering each axis pass
+    float smooth_w[SHW_MAX_SMOOTH_TAPS];          // taps: weights
+    long long smooth_off[SHW_MAX_SMOOTH_TAPS];    // taps: offsets, 32.32 fixed point
 };
 
 
@@ -212,6 +217,53 @@ __device__ __forceinline__ float sample(const S &s, long long X, long long Y, lo
         return trilinear_cached<CLAMP>(s, X, Y, Z, cc);
 }
 
+// Algorithm 1's "val <- smooth(val)" on one cube at (X, Y, Z) (Sections 4.1-4.2).
+// Box (Algorithm 8): the sample and a.smooth_n neighbours on each side one voxel apart
+// along the ray (U, the unit direction), times 1 / (2 arm + 1).  Taps (Algorithm 9 per
+// data axis): passes along x, y, z in turn, each val <- c0 val + sum_j w_j (v(+off_j) +
+// v(-off_j)).  The centre goes through the cell cache; taps fetch with clamping.
+template <int INTERP, class S>
+__device__ __forceinline__ float smoothed_sample(const S &s, long long X, long long Y, long long Z,
+                                                 const long long U[3], const RenderArgs &a, CellCache &cc)
+{
+    float v = sample<true, INTERP>(s, X, Y, Z, cc);
+    if (a.smooth == SHW_SMOOTH_BOX) {
+        long long ox = 0, oy = 0, oz = 0;
+        for (int i = 0; i < a.smooth_n; ++i) {
+            ox += U[0];
+            oy += U[1];
+            oz += U[2];
+            v += fetch<INTERP>(s, X + ox, Y + oy, Z + oz);
+            v += fetch<INTERP>(s, X - ox, Y - oy, Z - oz);
+        }
+        v *= a.smooth_c0;
+    } else if (a.smooth == SHW_SMOOTH_TAPS) {
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            float out = v * a.smooth_c0;
+            for (int j = 0; j < a.smooth_n; ++j) {
+                const long long o = a.smooth_off[j];
+                const long long dx = ax == 0 ? o : 0, dy = ax == 1 ? o : 0, dz = ax == 2 ? o : 0;
+                out = __fmaf_rn(fetch<INTERP>(s, X + dx, Y + dy, Z + dz), a.smooth_w[j], out);
+                out = __fmaf_rn(fetch<INTERP>(s, X - dx, Y - dy, Z - dz), a.smooth_w[j], out);
+            }
+            v = out;
+        }
+    }
+    return v;
+}
+
+// One cube's value at a ray sample: smoothed (SM) or the plain fetch.
+template <bool CLAMP, bool SM, int INTERP, class S>
+__device__ __forceinline__ float ray_sample(const S &s, long long X, long long Y, long long Z, CellCache &cc,
+                                            const RenderArgs &a, const long long *U)
+{
+    if constexpr (SM)
+        return smoothed_sample<INTERP>(s, X, Y, Z, U, a, cc);
+    else
+        return sample<CLAMP, INTERP>(s, X, Y, Z, cc);
+}
+
 // ---- transfer-function state per mode --------------------------------------
 
 // Eq. 1 / Algorithms 2, 4, 14: running maximum with ">=" (the last maximum wins)
@@ -375,26 +427,28 @@ struct StateOf<SHW_RATIO_MIP> {
 
 // Samples [k0, k1) of one ray; true if the transfer function stopped the ray
 // (then kdone = samples processed).  X, Y, Z advance with the samples.
-template <bool CLAMP, int MODE, int INTERP, class S, class St>
+// SM: every sample smoothed (U: the ray's unit direction).
+template <bool CLAMP, int MODE, int INTERP, bool SM = false, class S, class St>
 __device__ __forceinline__ bool march(const S &s, const S &s2, const RenderArgs &a, St &st, CellCache &cc,
                                       CellCache &cc2, long long &X, long long &Y, long long &Z, long long DX,
-                                      long long DY, long long DZ, int k0, int k1, int &kdone)
+                                      long long DY, long long DZ, int k0, int k1, int &kdone,
+                                      const long long *U = nullptr)
 {
     for (int k = k0; k < k1; ++k) {
         if constexpr (MODE == SHW_RATIO_MIP) {
             // Algorithm 13: each cube's maximum; a NaN sample counts as DATAMIN
-            const float c1 = filter_value(sample<CLAMP, INTERP>(s, X, Y, Z, cc), a);
-            const float c2 = filter_value(sample<CLAMP, INTERP>(s2, X, Y, Z, cc2), a);
+            const float c1 = filter_value(ray_sample<CLAMP, SM, INTERP>(s, X, Y, Z, cc, a, U), a);
+            const float c2 = filter_value(ray_sample<CLAMP, SM, INTERP>(s2, X, Y, Z, cc2, a, U), a);
             st.update2(isnan(c1) ? a.lo : c1, isnan(c2) ? a.lo : c2);
         } else {
             float v;
             if constexpr (MODE == SHW_RATIO) {
                 // Algorithm 14: ratio where cube1 exceeds the floor, else DATAMIN
-                const float c1 = filter_value(sample<CLAMP, INTERP>(s, X, Y, Z, cc), a);
-                const float c2 = filter_value(sample<CLAMP, INTERP>(s2, X, Y, Z, cc2), a);
+                const float c1 = filter_value(ray_sample<CLAMP, SM, INTERP>(s, X, Y, Z, cc, a, U), a);
+                const float c2 = filter_value(ray_sample<CLAMP, SM, INTERP>(s2, X, Y, Z, cc2, a, U), a);
                 v = (c1 > a.ratio_floor) ? __fdiv_rn(c2, c1) : a.lo;
             } else {
-                v = sample<CLAMP, INTERP>(s, X, Y, Z, cc);
+                v = ray_sample<CLAMP, SM, INTERP>(s, X, Y, Z, cc, a, U);
                 v = filter_value(isnan(v) ? a.lo : v, a);
             }
             v = isnan(v) ? a.lo : v;  // a NaN sample counts as DATAMIN
@@ -554,7 +608,7 @@ __device__ __forceinline__ void emit_ray(const RenderArgs &a, long long pix, int
 
 // One ray of Algorithm 1 with the transfer function MODE.  lut_c: the colour map in
 // shared memory (read per sample by COMPOSITE); a.lut: the same map in global memory.
-template <int MODE, int INTERP, class S>
+template <int MODE, int INTERP, class S, bool SM = false>
 __device__ __forceinline__ void render_pixel(const S &s, const S &s2, const shw_camera &cam, const RenderArgs &a,
                                              const float4 *lut_c, int px, int py)
 {
@@ -603,6 +657,10 @@ __device__ __forceinline__ void render_pixel(const S &s, const S &s2, const shw_
             st.nearest = INTERP == SHW_NEAREST;
         }
         CellCache cc, cc2;
+        if constexpr (SM) {
+            // smoothing: taps reach past the interior, so every sample fetches with clamping
+            march<true, MODE, INTERP, true>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, 0, N, done, r.U);
+        } else {
         bool stop = march<true, MODE, INTERP>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, 0, ka, done);
         if (!stop) {
             // (16-bit bricks: only for the line ratio, whose two gathers per sample leave
@@ -615,7 +673,7 @@ __device__ __forceinline__ void render_pixel(const S &s, const S &s2, const shw_
             }
         }
         if (!stop) march<true, MODE, INTERP>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, kb, N, done);
-
+        }
     }
     if (N <= 0) r.P[0] = r.P[1] = r.P[2] = r.D[0] = r.D[1] = r.D[2] = 0;
     emit_ray<MODE, INTERP>(a, pix, N, r.P, r.D, st, done);
@@ -652,7 +710,7 @@ int sm_count();
 #ifndef SHW_RENDER_MINB
 #define SHW_RENDER_MINB 1  // minimum resident CTAs per SM the persistent kernel is compiled for
 #endif
-template <int MODE, int INTERP, class S>
+template <int MODE, int INTERP, class S, bool SM = false>
 __global__ void __launch_bounds__(kRenderThreads, SHW_RENDER_MINB)
     render_kernel_persistent(S s, S s2, shw_camera cam, RenderArgs a, unsigned *ctr, int nwarp_tiles)
 {
@@ -670,8 +728,24 @@ __global__ void __launch_bounds__(kRenderThreads, SHW_RENDER_MINB)
         const int ty = centre_out(rr, a.cty, a.tiles_y), tx = centre_out(cr, a.ctx, a.tiles_x);
         const int px = tx * tw + (wtx >= wty ? 0 : warp * wtx) + (lane & (wtx - 1));
         const int py = ty * th + (wtx >= wty ? warp * wty : 0) + (lane >> ws);
-        if (px < a.width && py < a.height) render_pixel<MODE, INTERP, S>(s, s2, cam, a, a.lut, px, py);
+        if (px < a.width && py < a.height) render_pixel<MODE, INTERP, S, SM>(s, s2, cam, a, a.lut, px, py);
     }
+}
+
+// Resident CTAs per SM of one kernel, queried once per kernel (a static per instance).
+template <auto KERN>
+int resident_per_sm()
+{
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, KERN, kRenderThreads, 0) != cudaSuccess) {
+            cudaGetLastError();
+            n = 0;
+        }
+        per_sm = n;
+    }
+    return per_sm;
 }
 
 // Pixel coordinates of the cube centre's projection (image centre if behind the eye).
@@ -695,7 +769,8 @@ inline void project_centre(const shw_camera &c, int nx, int ny, int nz, float &p
 }
 
 // Host-side launch for one storage type (instantiated per storage in its own TU).
-template <class S>
+// SM: the in-ray smoothing instances (persistent form only).
+template <bool SM, class S>
 shw_status launch_render_modes(int mode, int interp, const S &s, const S &s2, const shw_camera &cam,
                                const RenderArgs &a0, cudaStream_t st)
 {
@@ -715,23 +790,19 @@ shw_status launch_render_modes(int mode, int interp, const S &s, const S &s2, co
     const int nsm = sm_count();
     const int nwarp_tiles = (int)(tiles * kCtaWarps);
     // persistent grid: as many CTAs as fit on the device at once (at most one per tile)
-    auto persistent = [&](auto kern) {
-        static int per_sm = -1;  // one value per kernel instantiation
-        if (per_sm < 0) {
-            int n = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kRenderThreads, 0) != cudaSuccess) {
-                cudaGetLastError();
-                n = 0;
-            }
-            per_sm = n;
-        }
+    auto persistent = [&](auto kern, int per_sm) {
         const long long g = std::min<long long>((long long)per_sm * nsm, tiles);
         kern<<<(unsigned)std::max<long long>(g, 1), block, 0, st>>>(s, s2, cam, a, ctr, nwarp_tiles);
     };
+    if (SM && (ctr == nullptr || nsm <= 0)) return SHW_ECUDA;
 #define SHW_LAUNCH(M, I)                                                       \
     do {                                                                       \
-        if (ctr != nullptr && nsm > 0)                                         \
-            persistent(render_kernel_persistent<M, I, S>);                     \
+        if constexpr (SM)                                                      \
+            persistent(render_kernel_persistent<M, I, S, true>,                \
+                       resident_per_sm<render_kernel_persistent<M, I, S, true>>()); \
+        else if (ctr != nullptr && nsm > 0)                                    \
+            persistent(render_kernel_persistent<M, I, S>,                      \
+                       resident_per_sm<render_kernel_persistent<M, I, S>>());  \
         else                                                                   \
             render_kernel<M, I, S><<<grid, block, 0, st>>>(s, s2, cam, a);     \
     } while (0)
@@ -772,6 +843,13 @@ inline int warp_shift_for(const shw_camera &c)
 // Entry points of the per-storage translation units.
 shw_status render_f32(int mode, int interp, const shw_volume &v, const shw_volume *v2, const shw_camera &cam,
                       const RenderArgs &a, cudaStream_t st);
+shw_status render_f32_big(int mode, int interp, const shw_volume &v, const shw_volume *v2, const shw_camera &cam,
+                          const RenderArgs &a, cudaStream_t st);
+// in-ray smoothing (a.smooth != SHW_SMOOTH_NONE), any storage
+shw_status render_smooth_f32(int mode, int interp, const shw_volume &v, const shw_volume *v2,
+                             const shw_camera &cam, const RenderArgs &a, cudaStream_t st);
+shw_status render_smooth_b16(int mode, int interp, const shw_volume &v, const shw_volume *v2,
+                             const shw_camera &cam, const RenderArgs &a, cudaStream_t st);
 shw_status render_bf16(int mode, int interp, const shw_volume &v, const shw_volume *v2, const shw_camera &cam,
                        const RenderArgs &a, cudaStream_t st);
 shw_status render_f16(int mode, int interp, const shw_volume &v, const shw_volume *v2, const shw_camera &cam,

@@ -26,6 +26,12 @@ SURVEY.setdefault("n_sources", 200)
 # the moment-map view of the survey cube: parallel rays down the spectral axis
 SURVEY_ORTHO_Z = dict(name="survey-512x512x1024-ortho-z-512^2", width=512, height=512, step=0.5)
 
+# the paper's smoothing benchmark (Section 6, Appendix B) in shape: a U[0,1] cube, a
+# 1000x1000 canvas, MIP and compositing, per-step fetch counts from raw to the 13-tap kernel
+PAPER_SMOOTH = dict(name="paper-smoothing-512^3-U01-persp-1000^2", n=512, width=1000, height=1000, step=0.5,
+                    yaws=(0.0, 120.0, 240.0), pitch=20.0, lo=0.0, hi=1.0, opacity_scale=0.22,
+                    clip=(0.9, 1.0), box_arms=(1, 2, 3, 4), gauss_taps=(5, 9, 13))
+
 DIFF = dict(name="diff-256^3-persp-512^2", dims=(256, 256, 256), yaw=30.0, pitch=20.0, width=512, height=512,
             step=0.5, opacity_scale=0.02, target_scale=1.2, lut_sigma=0.05, ckpt_interval=64)
 

@@ -46,11 +46,11 @@ def test_struct_layout(L):
     from paper_1707_00442_gb300 import _lib
     assert L.shw_struct_size(0) == C.sizeof(_lib.Volume) == 24
     assert L.shw_struct_size(1) == C.sizeof(_lib.Camera) == 68
-    assert L.shw_struct_size(2) == C.sizeof(_lib.RenderParams) == 64
+    assert L.shw_struct_size(2) == C.sizeof(_lib.RenderParams) == 112
     assert L.shw_struct_size(3) == C.sizeof(_lib.BatchItem) == 112
     assert L.shw_struct_size(4) == C.sizeof(_lib.BatchInfo)
     assert L.shw_struct_size(9) == 0
-    assert L.shw_abi_version() == 2
+    assert L.shw_abi_version() == 3
 
 
 def test_status_strings(L):
@@ -75,9 +75,13 @@ def _cam(W=16, H=16, ortho=1):
     return c
 
 
-def _params(mode=0, step=0.5, lut=0x2000, lo=-3.0, hi=8.0):
+def _params(mode=0, step=0.5, lut=0x2000, lo=-3.0, hi=8.0, smooth=0, arm=0, ntaps=0, c0=1.0, off=0.0, w=0.0):
     from paper_1707_00442_gb300 import _lib
-    return _lib.RenderParams(mode, 1, step, lo, hi, lut, 1.0, 0.99, 0.0, 64)
+    p = _lib.RenderParams(mode, 1, step, lo, hi, lut, 1.0, 0.99, 0.0, 64)
+    p.smooth, p.smooth_arm, p.smooth_ntaps, p.smooth_c0 = smooth, arm, ntaps, c0
+    for j in range(4):
+        p.smooth_offset[j], p.smooth_weight[j] = off, w
+    return p
 
 
 def test_render_rejects_invalid_arguments_on_host(L):
@@ -102,6 +106,13 @@ def test_render_rejects_invalid_arguments_on_host(L):
         (ok_v, ok_c, _params(lut=0x2004), out),      # colour map not 16-byte aligned
         (ok_v, ok_c, _params(lo=1.0, hi=1.0), out),
         (ok_v, ok_c, _params(mode=4), out),          # RATIO without a second cube
+        (ok_v, ok_c, _params(smooth=3), out),        # unknown smoothing kind
+        (ok_v, ok_c, _params(smooth=1, arm=-1), out),
+        (ok_v, ok_c, _params(smooth=1, arm=17), out),  # box arm beyond SHW_MAX_SMOOTH_ARM
+        (ok_v, ok_c, _params(smooth=2, ntaps=5, off=1.5, w=0.1), out),  # beyond SHW_MAX_SMOOTH_TAPS
+        (ok_v, ok_c, _params(smooth=2, ntaps=2, off=65.0, w=0.1), out),  # offset beyond 64 voxels
+        (ok_v, ok_c, _params(smooth=2, ntaps=2, off=1.5, w=float("inf")), out),
+        (ok_v, ok_c, _params(smooth=2, ntaps=1, c0=float("nan"), off=1.5, w=0.1), out),
         (ok_v, ok_c, ok_p, 0),                       # no rgba output
         (ok_v, ok_c, ok_p, 0x4008),                  # rgba not 16-byte aligned
     ]
@@ -166,6 +177,7 @@ def test_batch_plan_rejects_invalid_arguments_on_host(L):
     assert L.shw_batch_plan_create(b(h), items, 0, b(p), 0, None) == 1
     assert L.shw_batch_plan_create(b(h), items, 2, b(_params(lut=0)), 0, None) == 1
     assert L.shw_batch_plan_create(b(h), items, 2, b(_params(step=0.0)), 0, None) == 1
+    assert L.shw_batch_plan_create(b(h), items, 2, b(_params(smooth=1, arm=2)), 0, None) == 2  # no in-ray smoothing
     items[1].mode = 4
     assert L.shw_batch_plan_create(b(h), items, 2, b(p), 0, None) == 2      # ratio: unsupported in a batch
     items[1].mode = 7
