@@ -179,6 +179,62 @@ class Step:
         return per
 
 
+class E2EPipeline:
+    """The step fed from and drained to host memory, as a stream of frames would run it:
+    uploads on one stream, kernels on the current stream, downloads on a third.  A cube's
+    upload for the next step starts once this step's smoothing has consumed it, so it
+    overlaps the renders; each image's download overlaps the renders after it.  The renders
+    that need only the first cube run before the second cube's smoothing, so the second
+    upload overlaps them too.  Every step still moves both cubes in and all images out."""
+
+    def __init__(self, step, cube_h, cube2_h, rgba_h):
+        import torch
+        self.torch, self.step = torch, step
+        self.cube_h, self.cube2_h, self.rgba_h = cube_h, cube2_h, rgba_h
+        dev = step.cube.device
+        self.cin, self.cout = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+
+    def _ev(self, stream):
+        e = self.torch.cuda.Event()
+        e.record(stream)
+        return e
+
+    def run(self, steps):
+        torch, st, shw, w = self.torch, self.step, self.step.shw, self.step.w
+        main = torch.cuda.current_stream()
+        free1 = free2 = self._ev(main)
+        out_free = {m: free1 for m in WL.MODES}
+        first = [m for m in WL.MODES if m != "ratio"]
+        for _ in range(steps):
+            self.cin.wait_event(free1)
+            with torch.cuda.stream(self.cin):
+                st.cube.copy_(self.cube_h, non_blocking=True)
+            in1 = self._ev(self.cin)
+            self.cin.wait_event(free2)
+            with torch.cuda.stream(self.cin):
+                st.cube2.copy_(self.cube2_h, non_blocking=True)
+            in2 = self._ev(self.cin)
+            main.wait_event(in1)
+            shw.smooth(st.cube, w["sigma"], w["radius"], out=st.s1)
+            free1 = self._ev(main)
+            for m in first + ["ratio"]:
+                if m == "ratio":
+                    main.wait_event(in2)
+                    shw.smooth(st.cube2, w["sigma"], w["radius"], out=st.s2)
+                    free2 = self._ev(main)
+                main.wait_event(out_free[m])
+                kw = dict(WL.MODE_PARAMS[m])
+                shw.render(st.s1, st.cam, m, lut=st.rlut if m == "ratio" else st.lut,
+                           vol2=st.s2 if m == "ratio" else None, step=w["step"], scalar=False, index=False,
+                           nsamples=False, out=st.outs[m], **kw)
+                self.cout.wait_event(self._ev(main))
+                with torch.cuda.stream(self.cout):
+                    self.rgba_h[m].copy_(st.outs[m]["rgba"], non_blocking=True)
+                out_free[m] = self._ev(self.cout)
+        main.wait_stream(self.cin)
+        main.wait_stream(self.cout)
+
+
 # --------------------------------------------------------------------------- roofline
 
 def kernel_roofline(name, t_ms, nvox, samples_per, peaks, sm_mhz):
@@ -286,24 +342,16 @@ def run_ours(args):
     ms_total = max_over_ranks(t0.elapsed_time(t1), world, dev)
     per_kernel = {k: statistics.mean(a.elapsed_time(b) for a, b in v) for k, v in events.items()}
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: every step uploads both cubes
+    # and downloads the five images, pipelined over three streams
     rgba_h = {m: torch.empty(step.outs[m]["rgba"].shape, dtype=torch.float32).pin_memory() for m in WL.MODES}
-    for _ in range(1):
-        cube_t.copy_(cube_h, non_blocking=True)
-        cube2_t.copy_(cube2_h, non_blocking=True)
-        step.run()
-        for m in WL.MODES:
-            rgba_h[m].copy_(step.outs[m]["rgba"], non_blocking=True)
+    e2e = E2EPipeline(step, cube_h, cube2_h, rgba_h)
+    e2e.run(1)
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
-        cube_t.copy_(cube_h, non_blocking=True)
-        cube2_t.copy_(cube2_h, non_blocking=True)
-        step.run()
-        for m in WL.MODES:
-            rgba_h[m].copy_(step.outs[m]["rgba"], non_blocking=True)
+    e2e.run(args.steps)
     e1.record()
     barrier()
     ms_e2e = max_over_ranks(e0.elapsed_time(e1), world, dev)
@@ -612,6 +660,11 @@ def run_case(args):
             scene.orbit_camera((nx, ny, nz), 30.0, 20.0, 960, 540)
         o = {"rgba": torch.empty((cam.height, cam.width, 4), device="cuda")}
         kw = dict(WL.MODE_PARAMS[args.mode])
+        if args.smooth.startswith("box"):
+            kw.update(smooth="box", smooth_arm=(int(args.smooth[3:]) - 1) // 2)
+        elif args.smooth.startswith("gauss"):
+            n = int(args.smooth[5:])
+            kw.update(smooth="taps", smooth_taps=shw.binomial_taps(9, drop=2) if n == 9 else shw.binomial_taps(n))
         fn = lambda: shw.render(cube, cam, args.mode, lut=lut, scalar=False, index=False,  # noqa: E731
                                 nsamples=False, out=o, **kw)
     t = _timeit(torch, fn, reps=args.steps, warm=args.warmup)
@@ -635,6 +688,7 @@ def main():
                     help="run one small case of one kernel family for a profiler capture, then exit")
     ap.add_argument("--dims", default="384,384,768", help="--case: cube dims nx,ny,nz")
     ap.add_argument("--mode", default="mip", help="--case: transfer function")
+    ap.add_argument("--smooth", default="raw", help="--case render: in-ray smoothing raw, boxN or gaussN")
     args = ap.parse_args()
     if args.case:
         run_case(args)
