@@ -22,7 +22,15 @@ namespace shw {
 
 struct SmoothWeights {
     float w[2 * SHW_MAX_SMOOTH_RADIUS + 1];
+    float2 w2[2 * SHW_MAX_SMOOTH_RADIUS + 1];  // (w_k, w_k): the packed FMAs' weight operand
 };
+
+#ifndef SHW_SMOOTH_ONEBAR
+#define SHW_SMOOTH_ONEBAR 1  // 1: one CTA barrier per plane (after the x pass); 0: also one after the wait
+#endif
+#ifndef SHW_SMOOTH_WPAIR
+#define SHW_SMOOTH_WPAIR 1  // 1: packed FMAs take the weight pair from the parameters; 0: built per use
+#endif
 
 __device__ __forceinline__ int clampi_s(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
@@ -101,6 +109,10 @@ __global__ void __launch_bounds__(32 * (32 / YB)) smooth_kernel(const float *__r
 constexpr int kSmTX = 32, kSmTY = 32, kSmXP = 8, kSmBW = kSmTX + 2 * kSmXP, kSmStages = 3, kSmThreads = 256;
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 wpair(const SmoothWeights &W, int k)
+{
+    return SHW_SMOOTH_WPAIR ? W.w2[k] : f2(W.w[k]);
+}
 
 // Replace the zero-filled out-of-range border of a staged tile by the edge values
 // (clamp-to-edge): first the columns outside [c_lo, c_hi], then whole rows outside
@@ -129,7 +141,7 @@ __device__ __forceinline__ void clamp_tile_edges(float *tile, int c_lo, int c_hi
 }
 
 #ifndef SHW_SMOOTH_MINB
-#define SHW_SMOOTH_MINB 2
+#define SHW_SMOOTH_MINB 3  // 80 registers, no spills, with the weight pairs in the parameters
 #endif
 
 template <int R>
@@ -192,11 +204,13 @@ __global__ void __launch_bounds__(kSmThreads, SHW_SMOOTH_MINB)
             if (i >= nplanes) break;
             const int stage = i % kSmStages;
             const bool ok = mbar_wait(&bars[stage], (uint32_t)((i / kSmStages) & 1), err);
+#if !SHW_SMOOTH_ONEBAR
             if (__syncthreads_or(!ok)) {
                 failed = true;
                 fail_i = i;
                 break;
             }
+#endif
             float *tile = s_in + stage * STAGE_FLOATS;
             if (edge) clamp_tile_edges<IH>(tile, c_lo, c_hi, r_lo, r_hi, tid);
             float *xp = s_xp + (i & 1) * IH * kSmTX;
@@ -221,7 +235,18 @@ __global__ void __launch_bounds__(kSmThreads, SHW_SMOOTH_MINB)
                 *reinterpret_cast<float4 *>(xp + r * kSmTX + 4 * q) = make_float4(acc[0], acc[1], acc[2], acc[3]);
             }
             if (edge) fence_proxy_async();  // the edge clamp wrote the stage that a tensor copy refills next
+#if SHW_SMOOTH_ONEBAR
+            // one barrier per plane: it orders the x pass before the refill and the y pass, and
+            // reports a wait that gave up (the x pass then read a stage whose copy may not have
+            // landed; nothing of this plane reaches memory outside the CTA)
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                fail_i = i;
+                break;
+            }
+#else
             __syncthreads();
+#endif
             // the stage is consumed: refill it with plane i + stages
             if (tid == 0 && i + kSmStages < nplanes) {
                 mbar_arrive_expect_tx(&bars[stage], STAGE_BYTES);
@@ -237,7 +262,7 @@ __global__ void __launch_bounds__(kSmThreads, SHW_SMOOTH_MINB)
             for (int j = 0; j < 2; ++j) {
                 float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
-                for (int k = 0; k < K; ++k) acc = __ffma2_rn(f2(W.w[k]), col[j + k], acc);
+                for (int k = 0; k < K; ++k) acc = __ffma2_rn(wpair(W, k), col[j + k], acc);
                 ring[j][slot] = acc;
             }
             // z-pass: the ring holds planes i-2R .. i (oldest in slot (slot+1) mod K)
@@ -248,7 +273,7 @@ __global__ void __launch_bounds__(kSmThreads, SHW_SMOOTH_MINB)
                     const int gy = y0 + 2 * rg + j;
                     float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
-                    for (int k = 0; k < K; ++k) acc = __ffma2_rn(f2(W.w[k]), ring[j][(slot + 1 + k) % K], acc);
+                    for (int k = 0; k < K; ++k) acc = __ffma2_rn(wpair(W, k), ring[j][(slot + 1 + k) % K], acc);
                     if (gx < nx && gy < ny)
                         *reinterpret_cast<float2 *>(out + (size_t)zo * plane + (size_t)gy * nx + gx) = acc;
                 }
@@ -365,7 +390,10 @@ shw_status shw_smooth(const float *in, float *out, int32_t nx, int32_t ny, int32
         sum += w[k + radius];
     }
     SmoothWeights W{};
-    for (int k = 0; k <= 2 * radius; ++k) W.w[k] = (float)(w[k] / sum);
+    for (int k = 0; k <= 2 * radius; ++k) {
+        W.w[k] = (float)(w[k] / sum);
+        W.w2[k] = make_float2(W.w[k], W.w[k]);
+    }
     return smooth_dispatch(in, out, nx, ny, nz, W, radius, as_stream(stream));
 }
 
@@ -379,6 +407,7 @@ shw_status shw_smooth_weights(const float *in, float *out, int32_t nx, int32_t n
     for (int k = 0; k <= 2 * radius; ++k) {
         if (!std::isfinite(w_host[k])) return SHW_EINVAL;
         W.w[k] = w_host[k];
+        W.w2[k] = make_float2(w_host[k], w_host[k]);
     }
     return smooth_dispatch(in, out, nx, ny, nz, W, radius, as_stream(stream));
 }
