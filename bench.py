@@ -2,7 +2,8 @@
 
 One step = the whole hot path over the survey input (512 x 512 x 1024 float32 cube
 and its co-registered second line): separable Gaussian smoothing (sigma 2, radius 6)
-of both cubes, then one 1920 x 1080 perspective render (yaw 30, pitch 20, fov 45,
+of both cubes (the second straight into the line ratio's interleaved pair storage),
+then one 1920 x 1080 perspective render (yaw 30, pitch 20, fov 45,
 step 0.5, trilinear) per transfer function -- MIP, average, compositing,
 spectral-position colouring, line ratio -- on the smoothed cubes.
 
@@ -127,14 +128,19 @@ def make_inputs(w=None):
 
 
 class Step:
-    """The survey step on one GPU: 2 smooths + 5 renders, all launches on one stream."""
+    """The survey step on one GPU: 2 smooths + 5 renders, all launches on one stream.
+
+    The first cube is smoothed into s1 (read by the four single-cube renders); the second is
+    smoothed into the line ratio's interleaved pair storage next to s1 (shw_smooth_zip), so
+    the ratio render fetches both cubes' corners with one load."""
 
     def __init__(self, shw, torch, cube_t, cube2_t, w):
         self.shw, self.torch, self.w = shw, torch, w
         self.cam = WL.survey_camera(w=w)
         dev = cube_t.device
         self.cube, self.cube2 = cube_t, cube2_t
-        self.s1, self.s2 = torch.empty_like(cube_t), torch.empty_like(cube2_t)
+        self.s1 = torch.empty_like(cube_t)
+        self.pair = torch.empty(tuple(cube2_t.shape) + (2,), dtype=torch.float32, device=dev)
         self.lut = torch.from_numpy(scene.linear_lut()).to(dev)
         self.rlut = torch.from_numpy(scene.ratio_lut()).to(dev)
         H, W = self.cam.height, self.cam.width
@@ -144,13 +150,16 @@ class Step:
     def launches(self):
         shw, w = self.shw, self.w
         yield "smooth", lambda: shw.smooth(self.cube, w["sigma"], w["radius"], out=self.s1)
-        yield "smooth2", lambda: shw.smooth(self.cube2, w["sigma"], w["radius"], out=self.s2)
+        yield "smooth2", lambda: shw.smooth_zip(self.cube2, self.s1, w["sigma"], w["radius"], out=self.pair)
         for m in WL.MODES:
             kw = dict(WL.MODE_PARAMS[m])
             lut = self.rlut if m == "ratio" else self.lut
             yield f"render_{m}", (lambda m=m, kw=kw, lut=lut: shw.render(
-                self.s1, self.cam, m, lut=lut, vol2=self.s2 if m == "ratio" else None, step=w["step"],
-                scalar=False, index=False, nsamples=False, out=self.outs[m], **kw))
+                self.vol_of(m), self.cam, m, lut=lut, step=w["step"], scalar=False, index=False, nsamples=False,
+                out=self.outs[m], **kw))
+
+    def vol_of(self, m):
+        return self.pair if m == "ratio" else self.s1
 
     def run(self, events=None):
         for name, fn in self.launches():
@@ -169,12 +178,12 @@ class Step:
         shw, w = self.shw, self.w
         per = {}
         shw.smooth(self.cube, w["sigma"], w["radius"], out=self.s1)
-        shw.smooth(self.cube2, w["sigma"], w["radius"], out=self.s2)
+        shw.smooth_zip(self.cube2, self.s1, w["sigma"], w["radius"], out=self.pair)
         for m in WL.MODES:
             kw = dict(WL.MODE_PARAMS[m])
             lut = self.rlut if m == "ratio" else self.lut
-            o = shw.render(self.s1, self.cam, m, lut=lut, vol2=self.s2 if m == "ratio" else None, step=w["step"],
-                           scalar=False, index=False, nsamples=True, **kw)
+            o = shw.render(self.vol_of(m), self.cam, m, lut=lut, step=w["step"], scalar=False, index=False,
+                           nsamples=True, **kw)
             per[m] = int(o["nsamples"].sum(dtype=self.torch.int64).item())
         return per
 
@@ -220,13 +229,12 @@ class E2EPipeline:
             for m in first + ["ratio"]:
                 if m == "ratio":
                     main.wait_event(in2)
-                    shw.smooth(st.cube2, w["sigma"], w["radius"], out=st.s2)
+                    shw.smooth_zip(st.cube2, st.s1, w["sigma"], w["radius"], out=st.pair)
                     free2 = self._ev(main)
                 main.wait_event(out_free[m])
                 kw = dict(WL.MODE_PARAMS[m])
-                shw.render(st.s1, st.cam, m, lut=st.rlut if m == "ratio" else st.lut,
-                           vol2=st.s2 if m == "ratio" else None, step=w["step"], scalar=False, index=False,
-                           nsamples=False, out=st.outs[m], **kw)
+                shw.render(st.vol_of(m), st.cam, m, lut=st.rlut if m == "ratio" else st.lut, step=w["step"],
+                           scalar=False, index=False, nsamples=False, out=st.outs[m], **kw)
                 self.cout.wait_event(self._ev(main))
                 with torch.cuda.stream(self.cout):
                     self.rgba_h[m].copy_(st.outs[m]["rgba"], non_blocking=True)
@@ -241,7 +249,9 @@ def kernel_roofline(name, t_ms, nvox, samples_per, peaks, sm_mhz):
     """Algorithmic work per launch / measured duration, against the bound of that kernel."""
     hbm = float(peaks["hbm_gbs"])
     if name.startswith("smooth"):
-        bytes_ = 2 * 4 * nvox  # read the cube once, write the result once
+        # read the cube once, write the result once; the second smoothing also reads the
+        # first smoothed cube and writes both into the line ratio's pair storage
+        bytes_ = (16 if name == "smooth2" else 8) * nvox
         ach = bytes_ / (t_ms * 1e-3) / 1e9
         return {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(ach / hbm, 4), "algorithmic_bytes": bytes_}
@@ -401,7 +411,11 @@ def run_ours(args):
 
 # ncu dram bytes (read + write) per launch of the dominant kernel, from one capture of the
 # current build (profiles/survey_step_dram_traffic.md); reset to absent when the kernel changes
-TRAFFIC_PER_LAUNCH: dict = {"render_ratio": 4533665280 + 23236096}
+TRAFFIC_PER_LAUNCH: dict = {
+    "smooth": 1280741120 + 1035349248, "smooth2": 2325389056 + 2100782848,
+    "render_mip": 1518867456 + 22110976, "render_avg": 1582366208 + 22686464,
+    "render_composite": 1395104256 + 24589312, "render_spectral": 1561487872 + 22204416,
+    "render_ratio": 2634651904 + 24575744}
 
 
 # --------------------------------------------------------------------------- variants
@@ -452,7 +466,7 @@ def run_variants(shw, torch, step, W, per_kernel, samples_per, peaks):
     # BF16 / FP16 bricks of the same smoothed cubes, same perspective renders
     br = {}
     for storage in ("bf16", "f16"):
-        b1, b2 = shw.pack_bricks(step.s1, storage), shw.pack_bricks(step.s2, storage)
+        b1, b2 = shw.pack_bricks(step.s1, storage), shw.pack_bricks(step.pair[..., 1].contiguous(), storage)
         per = {}
         for m in WL.MODES:
             kw = dict(WL.MODE_PARAMS[m])

@@ -89,7 +89,13 @@ typedef enum { SHW_NEAREST = 0, SHW_TRILINEAR = 1 } shw_interp;
 typedef enum {
     SHW_F32 = 0,        /* linear float32 [nz][ny][nx] */
     SHW_BF16_BRICK = 1, /* bricks written by shw_pack_bricks, bfloat16 */
-    SHW_F16_BRICK = 2   /* bricks written by shw_pack_bricks, IEEE binary16 */
+    SHW_F16_BRICK = 2,  /* bricks written by shw_pack_bricks, IEEE binary16 */
+    SHW_F32_PAIR = 3    /* the two co-registered cubes of a line ratio interleaved: float32
+                           [nz][ny][nx][2], element 0 the first cube (the ratio's denominator),
+                           element 1 the second; 8-byte aligned.  Only SHW_RATIO and SHW_RATIO_MIP
+                           render it (vol2 = NULL; other modes SHW_EUNSUPPORTED), without in-ray
+                           smoothing; results equal the two-cube render bit for bit.  Written by
+                           shw_smooth_zip */
 } shw_storage;
 
 /* A cube.  data: device.  For SHW_F32 it is the linear float32 array; for the
@@ -190,6 +196,15 @@ shw_status shw_smooth(const float *in, float *out, int32_t nx, int32_t ny, int32
 shw_status shw_smooth_weights(const float *in, float *out, int32_t nx, int32_t ny, int32_t nz,
                               const float *w_host, int32_t radius, void *stream);
 
+/* Smoothing into the interleaved storage of the line ratios: out_pair[v] = (first[v],
+ * smooth(in)[v]) for every voxel v, smooth(in) exactly as shw_smooth(in, sigma, radius)
+ * computes it.  in, first: device float32 [nz][ny][nx] (first is typically the other cube,
+ * already smoothed; in == first is allowed); out_pair: device float32 [nz][ny][nx][2],
+ * 8-byte aligned, overlapping neither input.  One kernel: in and first are read once,
+ * out_pair is written once. */
+shw_status shw_smooth_zip(const float *in, const float *first, float *out_pair, int32_t nx, int32_t ny,
+                          int32_t nz, float sigma, int32_t radius, void *stream);
+
 /* ---- reduced-precision brick storage -------------------------------------- */
 
 /* Bytes of the brick buffer for a cube of these dims: ceil(n/32) bricks per axis,
@@ -206,8 +221,8 @@ shw_status shw_pack_bricks(const float *in, int32_t nx, int32_t ny, int32_t nz, 
 
 /* ---- rendering (Sections 2-4) -------------------------------------------- */
 
-/* Render one image.  vol2: the second cube for SHW_RATIO (same dims and storage),
- * else NULL.  Outputs (device, any may be NULL except out_rgba):
+/* Render one image.  vol2: the second cube for SHW_RATIO / SHW_RATIO_MIP (same dims and
+ * storage), else NULL; NULL also when vol holds both cubes as SHW_F32_PAIR.  Outputs (device, any may be NULL except out_rgba):
  *   out_rgba   [H][W][4] float32: MIP/AVG/RATIO: colourMap(v_hat(result));
  *              SPECTRAL: (colourMap_rgb(t_z), v_hat(max)), t_z = (z_max + 1/2)/nz;
  *              COMPOSITE: premultiplied (C_r, C_g, C_b, 1 - T).

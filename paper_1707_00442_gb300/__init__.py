@@ -16,6 +16,7 @@ from .api import (  # noqa: F401
     render_backward,
     smooth,
     smooth_weights,
+    smooth_zip,
     sync_status,
 )
 from .autograd import composite_render  # noqa: F401

@@ -17,7 +17,7 @@ SHW_OK, SHW_EINVAL, SHW_EUNSUPPORTED, SHW_ECUDA, SHW_ENOMEM, SHW_ETIMEOUT, SHW_E
 MODES = {"mip": 0, "avg": 1, "composite": 2, "spectral": 3, "ratio": 4, "moment1": 5,
          "composite_spectral": 6, "mip_rgb": 7, "composite_rgb": 8, "ratio_mip": 9}
 INTERP = {"nearest": 0, "trilinear": 1}
-STORAGE = {"f32": 0, "bf16": 1, "f16": 2}
+STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "pair": 3}
 ABI_VERSION = 3
 LUT_SIZE = 256
 MAX_SMOOTH_RADIUS = 16
@@ -84,6 +84,7 @@ SIGNATURES = {
     "shw_sync_status": (_i32, [_vp]),
     "shw_smooth": (_i32, [_vp, _vp, _i32, _i32, _i32, _f, _i32, _vp]),
     "shw_smooth_weights": (_i32, [_vp, _vp, _i32, _i32, _i32, _P(C.c_float), _i32, _vp]),
+    "shw_smooth_zip": (_i32, [_vp, _vp, _vp, _i32, _i32, _i32, _f, _i32, _vp]),
     "shw_bricked_bytes": (_sz, [_i32, _i32, _i32, _i32]),
     "shw_pack_bricks": (_i32, [_vp, _i32, _i32, _i32, _i32, _vp, _sz, _vp]),
     "shw_render": (_i32, [_P(Volume), _P(Volume), _P(Camera), _P(RenderParams), _vp, _vp, _vp, _vp, _vp, _sz,

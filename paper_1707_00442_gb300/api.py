@@ -51,8 +51,11 @@ def volume_struct(vol) -> _lib.Volume:
         _need_cuda(vol.data, "bricks", torch.int16)
         return _lib.Volume(vol.data.data_ptr(), vol.nx, vol.ny, vol.nz, STORAGE[vol.storage])
     _need_cuda(vol, "cube", torch.float32)
+    if vol.dim() == 4 and vol.shape[3] == 2:  # the line ratios' interleaved pair storage
+        nz, ny, nx, _ = vol.shape
+        return _lib.Volume(vol.data_ptr(), nx, ny, nz, STORAGE["pair"])
     if vol.dim() != 3:
-        raise ValueError("cube must be [nz, ny, nx]")
+        raise ValueError("cube must be [nz, ny, nx] (or [nz, ny, nx, 2] for the pair storage)")
     nz, ny, nx = vol.shape
     return _lib.Volume(vol.data_ptr(), nx, ny, nz, STORAGE["f32"])
 
@@ -143,6 +146,24 @@ def smooth(cube: torch.Tensor, sigma: float, radius: int, out: torch.Tensor | No
     nz, ny, nx = cube.shape
     check(lib().shw_smooth(cube.data_ptr(), out.data_ptr(), nx, ny, nz, float(sigma), int(radius), _stream()),
           "shw_smooth")
+    return out
+
+
+def smooth_zip(cube: torch.Tensor, first: torch.Tensor, sigma: float, radius: int,
+               out: torch.Tensor | None = None) -> torch.Tensor:
+    """Smooth ``cube`` as smooth() does and interleave it after ``first``: the [nz, ny, nx, 2]
+    pair storage of the line ratios, (first, smoothed) per voxel (shw_smooth_zip)."""
+    _need_cuda(cube, "cube", torch.float32)
+    _need_cuda(first, "first", torch.float32)
+    if cube.dim() != 3 or tuple(first.shape) != tuple(cube.shape):
+        raise ValueError("cube and first must be [nz, ny, nx] of the same shape")
+    nz, ny, nx = cube.shape
+    out = torch.empty((nz, ny, nx, 2), dtype=torch.float32, device=cube.device) if out is None else out
+    _need_cuda(out, "out", torch.float32)
+    if tuple(out.shape) != (nz, ny, nx, 2):
+        raise ValueError("out must be [nz, ny, nx, 2]")
+    check(lib().shw_smooth_zip(cube.data_ptr(), first.data_ptr(), out.data_ptr(), nx, ny, nz, float(sigma),
+                               int(radius), _stream()), "shw_smooth_zip")
     return out
 
 

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "ray.cuh"
@@ -264,6 +265,35 @@ __device__ __forceinline__ float ray_sample(const S &s, long long X, long long Y
         return sample<CLAMP, INTERP>(s, X, Y, Z, cc);
 }
 
+// Both cubes of a line ratio at one sample from the interleaved pair storage.
+template <bool CLAMP, int INTERP, class S>
+__device__ __forceinline__ float2 pair_sample(const S &s, long long X, long long Y, long long Z, CellCachePair &cc)
+{
+    if constexpr (INTERP == SHW_NEAREST)
+        return s.template nearest2<CLAMP>(X, Y, Z);
+    else
+        return trilinear_pair_cached<CLAMP>(s, X, Y, Z, cc);
+}
+
+template <class S>
+using CacheOf = typename std::conditional<S::kPair, CellCachePair, CellCache>::type;
+
+// The two cubes' raw values at a sample of the line ratios: one interleaved fetch for the
+// pair storage, else one fetch (or smoothed value) per cube.
+template <bool CLAMP, bool SM, int INTERP, class S, class CC>
+__device__ __forceinline__ void two_samples(const S &s, const S &s2, long long X, long long Y, long long Z, CC &cc,
+                                            CC &cc2, const RenderArgs &a, const long long *U, float &c1, float &c2)
+{
+    if constexpr (S::kPair) {
+        const float2 c = pair_sample<CLAMP, INTERP>(s, X, Y, Z, cc);
+        c1 = c.x;
+        c2 = c.y;
+    } else {
+        c1 = ray_sample<CLAMP, SM, INTERP>(s, X, Y, Z, cc, a, U);
+        c2 = ray_sample<CLAMP, SM, INTERP>(s2, X, Y, Z, cc2, a, U);
+    }
+}
+
 // ---- transfer-function state per mode --------------------------------------
 
 // Eq. 1 / Algorithms 2, 4, 14: running maximum with ">=" (the last maximum wins)
@@ -428,24 +458,26 @@ struct StateOf<SHW_RATIO_MIP> {
 // Samples [k0, k1) of one ray; true if the transfer function stopped the ray
 // (then kdone = samples processed).  X, Y, Z advance with the samples.
 // SM: every sample smoothed (U: the ray's unit direction).
-template <bool CLAMP, int MODE, int INTERP, bool SM = false, class S, class St>
-__device__ __forceinline__ bool march(const S &s, const S &s2, const RenderArgs &a, St &st, CellCache &cc,
-                                      CellCache &cc2, long long &X, long long &Y, long long &Z, long long DX,
+template <bool CLAMP, int MODE, int INTERP, bool SM = false, class S, class St, class CC>
+__device__ __forceinline__ bool march(const S &s, const S &s2, const RenderArgs &a, St &st, CC &cc,
+                                      CC &cc2, long long &X, long long &Y, long long &Z, long long DX,
                                       long long DY, long long DZ, int k0, int k1, int &kdone,
                                       const long long *U = nullptr)
 {
     for (int k = k0; k < k1; ++k) {
         if constexpr (MODE == SHW_RATIO_MIP) {
             // Algorithm 13: each cube's maximum; a NaN sample counts as DATAMIN
-            const float c1 = filter_value(ray_sample<CLAMP, SM, INTERP>(s, X, Y, Z, cc, a, U), a);
-            const float c2 = filter_value(ray_sample<CLAMP, SM, INTERP>(s2, X, Y, Z, cc2, a, U), a);
+            float r1, r2;
+            two_samples<CLAMP, SM, INTERP>(s, s2, X, Y, Z, cc, cc2, a, U, r1, r2);
+            const float c1 = filter_value(r1, a), c2 = filter_value(r2, a);
             st.update2(isnan(c1) ? a.lo : c1, isnan(c2) ? a.lo : c2);
         } else {
             float v;
             if constexpr (MODE == SHW_RATIO) {
                 // Algorithm 14: ratio where cube1 exceeds the floor, else DATAMIN
-                const float c1 = filter_value(ray_sample<CLAMP, SM, INTERP>(s, X, Y, Z, cc, a, U), a);
-                const float c2 = filter_value(ray_sample<CLAMP, SM, INTERP>(s2, X, Y, Z, cc2, a, U), a);
+                float r1, r2;
+                two_samples<CLAMP, SM, INTERP>(s, s2, X, Y, Z, cc, cc2, a, U, r1, r2);
+                const float c1 = filter_value(r1, a), c2 = filter_value(r2, a);
                 v = (c1 > a.ratio_floor) ? __fdiv_rn(c2, c1) : a.lo;
             } else {
                 v = ray_sample<CLAMP, SM, INTERP>(s, X, Y, Z, cc, a, U);
@@ -473,10 +505,59 @@ __device__ __forceinline__ bool march(const S &s, const S &s2, const RenderArgs 
 // trilinear, software-pipelined: while sample k is interpolated and fed to the
 // transfer function, the corners of sample k+1's cell are already being loaded when
 // that cell differs.  Same arithmetic as march<false>, so the same results.
+// march_interior_pair: the line ratios on the interleaved pair storage, one 8-byte load per
+// corner for both cubes, packed interpolation (each cube bit-identical to the single form).
 template <int MODE, class S, class St>
-__device__ __forceinline__ bool march_interior(const S &s, const S &s2, const RenderArgs &a, St &st, long long &X,
-                                               long long &Y, long long &Z, long long DX, long long DY, long long DZ,
-                                               int k0, int k1, int &kdone)
+__device__ __forceinline__ bool march_interior_pair(const S &s, const RenderArgs &a, St &st, long long &X,
+                                                    long long &Y, long long &Z, long long DX, long long DY,
+                                                    long long DZ, int k0, int k1, int &kdone)
+{
+    if (k0 >= k1) {
+        kdone = k1;
+        return false;
+    }
+    int cx = fx_cell(X), cy = fx_cell(Y), cz = fx_cell(Z);
+    float2 cur[8];
+    s.template corners2<false>(cx, cy, cz, cur);
+    for (int k = k0; k < k1; ++k) {
+        const long long Xn = X + DX, Yn = Y + DY, Zn = Z + DZ;
+        const int nx = fx_cell(Xn), ny = fx_cell(Yn), nz = fx_cell(Zn);
+        const bool pf = ((nx != cx) | (ny != cy) | (nz != cz)) && k + 1 < k1;
+        float2 nxt[8];
+        if (pf) s.template corners2<false>(nx, ny, nz, nxt);
+        const float2 c = trilerp_pair(cur, fx_frac(X), fx_frac(Y), fx_frac(Z));
+        const float c1 = filter_value(c.x, a), c2 = filter_value(c.y, a);
+        if constexpr (MODE == SHW_RATIO_MIP) {
+            st.update2(isnan(c1) ? a.lo : c1, isnan(c2) ? a.lo : c2);
+        } else {
+            // Algorithm 14: ratio where cube1 exceeds the floor, else DATAMIN
+            float v = (c1 > a.ratio_floor) ? __fdiv_rn(c2, c1) : a.lo;
+            v = isnan(v) ? a.lo : v;
+            if (st.update(v, k)) {
+                kdone = k + 1;
+                return true;
+            }
+        }
+        if (pf) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) cur[i] = nxt[i];
+            cx = nx;
+            cy = ny;
+            cz = nz;
+        }
+        X = Xn;
+        Y = Yn;
+        Z = Zn;
+    }
+    kdone = k1;
+    return false;
+}
+
+// march_interior_single: one or two separate cubes.
+template <int MODE, class S, class St>
+__device__ __forceinline__ bool march_interior_single(const S &s, const S &s2, const RenderArgs &a, St &st,
+                                                      long long &X, long long &Y, long long &Z, long long DX,
+                                                      long long DY, long long DZ, int k0, int k1, int &kdone)
 {
     constexpr bool TWO = two_cubes<MODE>;
     if (k0 >= k1) {
@@ -533,6 +614,18 @@ __device__ __forceinline__ bool march_interior(const S &s, const S &s2, const Re
     }
     kdone = k1;
     return false;
+}
+
+// The interior loop for the sampler at hand.
+template <int MODE, class S, class St>
+__device__ __forceinline__ bool march_interior(const S &s, const S &s2, const RenderArgs &a, St &st, long long &X,
+                                               long long &Y, long long &Z, long long DX, long long DY, long long DZ,
+                                               int k0, int k1, int &kdone)
+{
+    if constexpr (S::kPair)
+        return march_interior_pair<MODE>(s, a, st, X, Y, Z, DX, DY, DZ, k0, k1, kdone);
+    else
+        return march_interior_single<MODE>(s, s2, a, st, X, Y, Z, DX, DY, DZ, k0, k1, kdone);
 }
 
 // setFragment (Algorithm 1): the outputs of one ray from its final transfer-function
@@ -656,7 +749,7 @@ __device__ __forceinline__ void render_pixel(const S &s, const S &s2, const shw_
             st.nz = a.nz;
             st.nearest = INTERP == SHW_NEAREST;
         }
-        CellCache cc, cc2;
+        CacheOf<S> cc, cc2;
         if constexpr (SM) {
             // smoothing: taps reach past the interior, so every sample fetches with clamping
             march<true, MODE, INTERP, true>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, 0, N, done, r.U);
@@ -811,6 +904,15 @@ shw_status launch_render_modes(int mode, int interp, const S &s, const S &s2, co
         if (interp == SHW_NEAREST) SHW_LAUNCH(M, SHW_NEAREST); \
         else SHW_LAUNCH(M, SHW_TRILINEAR);                     \
         break;
+    if constexpr (S::kPair) {
+        // the interleaved pair storage serves the line ratios only
+        switch (mode) {
+            SHW_CASE(SHW_RATIO)
+            SHW_CASE(SHW_RATIO_MIP)
+        default:
+            return SHW_EUNSUPPORTED;
+        }
+    } else {
     switch (mode) {
         SHW_CASE(SHW_MIP)
         SHW_CASE(SHW_AVG)
@@ -824,6 +926,7 @@ shw_status launch_render_modes(int mode, int interp, const S &s, const S &s2, co
         SHW_CASE(SHW_RATIO_MIP)
     default:
         return SHW_EINVAL;
+    }
     }
 #undef SHW_CASE
 #undef SHW_LAUNCH
@@ -845,6 +948,9 @@ shw_status render_f32(int mode, int interp, const shw_volume &v, const shw_volum
                       const RenderArgs &a, cudaStream_t st);
 shw_status render_f32_big(int mode, int interp, const shw_volume &v, const shw_volume *v2, const shw_camera &cam,
                           const RenderArgs &a, cudaStream_t st);
+// the line ratios on the interleaved pair storage
+shw_status render_f32_pair(int mode, int interp, const shw_volume &v, const shw_camera &cam, const RenderArgs &a,
+                           cudaStream_t st);
 // in-ray smoothing (a.smooth != SHW_SMOOTH_NONE), any storage
 shw_status render_smooth_f32(int mode, int interp, const shw_volume &v, const shw_volume *v2,
                              const shw_camera &cam, const RenderArgs &a, cudaStream_t st);

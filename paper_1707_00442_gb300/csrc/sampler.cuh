@@ -48,6 +48,7 @@ __device__ __forceinline__ int cell_of(long long p, int n)
 template <typename Idx>
 struct SamplerF32 {
     static constexpr bool kLinearF32 = true;
+    static constexpr bool kPair = false;
     const float *__restrict__ v;
     int nx, ny, nz;
     Idx sy, sz;  // strides of y and z in elements
@@ -117,6 +118,7 @@ __device__ __forceinline__ float to_f32<__half>(unsigned short raw)
 template <typename T>
 struct SamplerBrick {
     static constexpr bool kLinearF32 = false;
+    static constexpr bool kPair = false;
     const unsigned short *__restrict__ v;
     int nx, ny, nz;
     int nbx, nby;
@@ -169,6 +171,69 @@ struct SamplerBrick {
     }
 };
 
+// The two cubes of a line ratio interleaved, float2 [nz][ny][nx]: (first, second) per voxel.
+// One 8-byte load fetches a corner of both cubes; the interpolation runs on the pairs with
+// packed FP32x2 lerps in the single-cube order, so each cube's value is bit-identical to
+// trilerp() of that cube alone.
+__device__ __forceinline__ float2 trilerp_pair(const float2 c[8], float fx, float fy, float fz)
+{
+    const float2 a = lerp2(c[0], c[1], fx), b = lerp2(c[2], c[3], fx);  // z0: rows y0, y1
+    const float2 d = lerp2(c[4], c[5], fx), e = lerp2(c[6], c[7], fx);  // z1: rows y0, y1
+    return lerp2(lerp2(a, b, fy), lerp2(d, e, fy), fz);
+}
+
+template <typename Idx>
+struct SamplerF32Pair {
+    static constexpr bool kLinearF32 = false;
+    static constexpr bool kPair = true;
+    const float2 *__restrict__ v;
+    int nx, ny, nz;
+    Idx sy, sz;  // strides of y and z in pairs
+
+    template <bool CLAMP = true>
+    __device__ __forceinline__ float2 nearest2(long long X, long long Y, long long Z) const
+    {
+        int x = fx_round(X), y = fx_round(Y), z = fx_round(Z);
+        if (CLAMP) {
+            x = clampi(x, 0, nx - 1);
+            y = clampi(y, 0, ny - 1);
+            z = clampi(z, 0, nz - 1);
+        }
+        return __ldg(v + ((Idx)z * sz + (Idx)y * sy + x));
+    }
+
+    template <bool CLAMP = true>
+    __device__ __forceinline__ void corners2(int ix, int iy, int iz, float2 c[8]) const
+    {
+        int x0 = ix, y0 = iy, z0 = iz, dx = 1;
+        Idx dy = sy, dz = sz;
+        if (CLAMP) {
+            x0 = max(ix, 0);
+            y0 = max(iy, 0);
+            z0 = max(iz, 0);
+            dx = min(ix + 1, nx - 1) - x0;
+            dy = (Idx)(min(iy + 1, ny - 1) - y0) * sy;
+            dz = (Idx)(min(iz + 1, nz - 1) - z0) * sz;
+        }
+        const float2 *p00 = v + ((Idx)z0 * sz + (Idx)y0 * sy + x0);
+        const float2 *p01 = p00 + dy, *p10 = p00 + dz, *p11 = p10 + dy;
+        c[0] = __ldg(p00);
+        c[1] = __ldg(p00 + dx);
+        c[2] = __ldg(p01);
+        c[3] = __ldg(p01 + dx);
+        c[4] = __ldg(p10);
+        c[5] = __ldg(p10 + dx);
+        c[6] = __ldg(p11);
+        c[7] = __ldg(p11 + dx);
+    }
+};
+
+// The pair sampler's corner cache (see CellCache below).
+struct CellCachePair {
+    int ix = -4, iy = -4, iz = -4;
+    float2 c[8];
+};
+
 // 1: reuse the 8 corners of the cell a ray is in until it leaves that cell; 0: no reuse
 #ifndef SHW_CELL_CACHE
 #define SHW_CELL_CACHE 1
@@ -180,6 +245,20 @@ struct CellCache {
     int ix = -4, iy = -4, iz = -4;  // no cell yet: valid cells start at -1
     float c[8];
 };
+
+template <bool CLAMP, class S>
+__device__ __forceinline__ float2 trilinear_pair_cached(const S &s, long long X, long long Y, long long Z,
+                                                        CellCachePair &cc)
+{
+    const int ix = cell_of<CLAMP>(X, s.nx), iy = cell_of<CLAMP>(Y, s.ny), iz = cell_of<CLAMP>(Z, s.nz);
+    if (!SHW_CELL_CACHE || ix != cc.ix || iy != cc.iy || iz != cc.iz) {
+        s.template corners2<CLAMP>(ix, iy, iz, cc.c);
+        cc.ix = ix;
+        cc.iy = iy;
+        cc.iz = iz;
+    }
+    return trilerp_pair(cc.c, fx_frac(X), fx_frac(Y), fx_frac(Z));
+}
 
 template <bool CLAMP, class S>
 __device__ __forceinline__ float trilinear_cached(const S &s, long long X, long long Y, long long Z, CellCache &cc)

@@ -34,9 +34,11 @@ struct SmoothWeights {
 
 __device__ __forceinline__ int clampi_s(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
-template <int R, int YB>
+// ZIP: out is the interleaved pair buffer, (first[v], smoothed[v]) per voxel.
+template <int R, int YB, bool ZIP>
 __global__ void __launch_bounds__(32 * (32 / YB)) smooth_kernel(const float *__restrict__ in, float *__restrict__ out,
-                                                                int nx, int ny, int nz, int zchunk, SmoothWeights W)
+                                                                int nx, int ny, int nz, int zchunk, SmoothWeights W,
+                                                                const float *__restrict__ first)
 {
     constexpr int TX = 32, TY = 32, TR = TY / YB, K = 2 * R + 1;
     constexpr int IW = TX + 2 * R, IH = TY + 2 * R;
@@ -85,7 +87,15 @@ __global__ void __launch_bounds__(32 * (32 / YB)) smooth_kernel(const float *__r
                 float acc = 0.0f;
 #pragma unroll
                 for (int k = 0; k < K; ++k) acc = __fmaf_rn(W.w[k], ring[j][k], acc);
-                if (gx < nx && gy < ny) out[(size_t)zo * plane + (size_t)gy * nx + gx] = acc;
+                if (gx < nx && gy < ny) {
+                    const size_t o = (size_t)zo * plane + (size_t)gy * nx + gx;
+                    if constexpr (ZIP) {
+                        out[2 * o] = __ldg(first + o);
+                        out[2 * o + 1] = acc;
+                    } else {
+                        out[o] = acc;
+                    }
+                }
             }
         }
     }
@@ -144,10 +154,10 @@ __device__ __forceinline__ void clamp_tile_edges(float *tile, int c_lo, int c_hi
 #define SHW_SMOOTH_MINB 3  // 80 registers, no spills, with the weight pairs in the parameters
 #endif
 
-template <int R>
+template <int R, bool ZIP>
 __global__ void __launch_bounds__(kSmThreads, SHW_SMOOTH_MINB)
     smooth_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict__ out, int nx, int ny, int nz,
-                      int zchunk, SmoothWeights W, unsigned *err)
+                      int zchunk, SmoothWeights W, unsigned *err, const float *__restrict__ first)
 {
     constexpr int IH = kSmTY + 2 * R, K = 2 * R + 1;
     constexpr int STAGE_FLOATS = IH * kSmBW;
@@ -274,8 +284,16 @@ __global__ void __launch_bounds__(kSmThreads, SHW_SMOOTH_MINB)
                     float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
                     for (int k = 0; k < K; ++k) acc = __ffma2_rn(wpair(W, k), ring[j][(slot + 1 + k) % K], acc);
-                    if (gx < nx && gy < ny)
-                        *reinterpret_cast<float2 *>(out + (size_t)zo * plane + (size_t)gy * nx + gx) = acc;
+                    if (gx < nx && gy < ny) {
+                        const size_t o = (size_t)zo * plane + (size_t)gy * nx + gx;
+                        if constexpr (ZIP) {
+                            // (first, smoothed) for the voxels gx and gx + 1: one 16-byte store
+                            const float2 f = __ldg(reinterpret_cast<const float2 *>(first + o));
+                            *reinterpret_cast<float4 *>(out + 2 * o) = make_float4(f.x, acc.x, f.y, acc.y);
+                        } else {
+                            *reinterpret_cast<float2 *>(out + o) = acc;
+                        }
+                    }
                 }
             }
         }
@@ -306,9 +324,9 @@ static int smooth_zchunk(int nx, int ny, int nz, int r)
     return zc;
 }
 
-template <int R>
+template <int R, bool ZIP>
 static bool launch_smooth_tma(const float *in, float *out, int nx, int ny, int nz, const SmoothWeights &w,
-                              cudaStream_t st)
+                              const float *first, cudaStream_t st)
 {
     CUtensorMap map;
     if (!encode_tmap_3d_f32(&map, in, nx, ny, nz, kSmBW, kSmTY + 2 * R)) return false;
@@ -316,14 +334,15 @@ static bool launch_smooth_tma(const float *in, float *out, int nx, int ny, int n
     const size_t smem = smooth_tma_smem<R>();
     const int zc = smooth_zchunk(nx, ny, nz, R);
     const dim3 grid((unsigned)ceil_div(nx, kSmTX), (unsigned)ceil_div(ny, kSmTY), (unsigned)ceil_div(nz, zc));
-    if (smem > 48 * 1024) cudaFuncSetAttribute(smooth_tma_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    smooth_tma_kernel<R><<<grid, kSmThreads, smem, st>>>(map, out, nx, ny, nz, zc, w, err);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(smooth_tma_kernel<R, ZIP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    smooth_tma_kernel<R, ZIP><<<grid, kSmThreads, smem, st>>>(map, out, nx, ny, nz, zc, w, err, first);
     return true;
 }
 
-template <int R>
+template <int R, bool ZIP>
 static void launch_smooth_r(const float *in, float *out, int nx, int ny, int nz, const SmoothWeights &w,
-                            cudaStream_t st)
+                            const float *first, cudaStream_t st)
 {
     constexpr int YB = (R <= 8) ? 4 : 2;
     const int tiles = ceil_div(nx, 32) * ceil_div(ny, 32);
@@ -332,18 +351,20 @@ static void launch_smooth_r(const float *in, float *out, int nx, int ny, int nz,
     while ((long long)tiles * ceil_div(nz, zc) < 1216 && zc / 2 >= zmin) zc /= 2;
     const dim3 grid((unsigned)ceil_div(nx, 32), (unsigned)ceil_div(ny, 32), (unsigned)ceil_div(nz, zc));
     const dim3 block(32, 32 / YB);
-    smooth_kernel<R, YB><<<grid, block, 0, st>>>(in, out, nx, ny, nz, zc, w);
+    smooth_kernel<R, YB, ZIP><<<grid, block, 0, st>>>(in, out, nx, ny, nz, zc, w, first);
 }
 
+template <bool ZIP>
 static shw_status smooth_dispatch(const float *in, float *out, int nx, int ny, int nz, const SmoothWeights &w,
-                                  int r, cudaStream_t st)
+                                  int r, const float *first, cudaStream_t st)
 {
     // TMA pipeline where its alignment rules hold, the staged kernel otherwise
-    if (r >= 1 && r <= 8 && nx % 4 == 0 && aligned(in, 16) && !std::getenv("SHW_SMOOTH_NO_TMA")) {
+    const bool zip_ok = !ZIP || (aligned(first, 8) && aligned(out, 16));
+    if (r >= 1 && r <= 8 && nx % 4 == 0 && aligned(in, 16) && zip_ok && !std::getenv("SHW_SMOOTH_NO_TMA")) {
         bool ok = false;
         switch (r) {
 #define SHW_T(n) \
-    case n: ok = launch_smooth_tma<n>(in, out, nx, ny, nz, w, st); break;
+    case n: ok = launch_smooth_tma<n, ZIP>(in, out, nx, ny, nz, w, first, st); break;
             SHW_T(1) SHW_T(2) SHW_T(3) SHW_T(4) SHW_T(5) SHW_T(6) SHW_T(7) SHW_T(8)
 #undef SHW_T
         }
@@ -351,13 +372,35 @@ static shw_status smooth_dispatch(const float *in, float *out, int nx, int ny, i
     }
     switch (r) {
 #define SHW_R(n) \
-    case n: launch_smooth_r<n>(in, out, nx, ny, nz, w, st); break;
+    case n: launch_smooth_r<n, ZIP>(in, out, nx, ny, nz, w, first, st); break;
         SHW_R(0) SHW_R(1) SHW_R(2) SHW_R(3) SHW_R(4) SHW_R(5) SHW_R(6) SHW_R(7) SHW_R(8)
         SHW_R(9) SHW_R(10) SHW_R(11) SHW_R(12) SHW_R(13) SHW_R(14) SHW_R(15) SHW_R(16)
 #undef SHW_R
     default: return SHW_EUNSUPPORTED;
     }
     return after_launch();
+}
+
+static bool overlaps(const void *a, size_t na, const void *b, size_t nb)
+{
+    const char *p = static_cast<const char *>(a), *q = static_cast<const char *>(b);
+    return p < q + nb && q < p + na;
+}
+
+// Eq. 5 sampled at the integer taps k = -radius..radius, normalised to unit sum (host, double)
+static bool gauss_weights(float sigma, int radius, SmoothWeights &W)
+{
+    if (!std::isfinite(sigma) || !(sigma > 0.0f)) return false;
+    double w[2 * SHW_MAX_SMOOTH_RADIUS + 1], sum = 0.0;
+    for (int k = -radius; k <= radius; ++k) {
+        w[k + radius] = std::exp(-(double)k * k / (2.0 * (double)sigma * sigma));
+        sum += w[k + radius];
+    }
+    for (int k = 0; k <= 2 * radius; ++k) {
+        W.w[k] = (float)(w[k] / sum);
+        W.w2[k] = make_float2(W.w[k], W.w[k]);
+    }
+    return true;
 }
 
 static shw_status smooth_check(const float *in, float *out, int nx, int ny, int nz, int r)
@@ -382,19 +425,22 @@ shw_status shw_smooth(const float *in, float *out, int32_t nx, int32_t ny, int32
 {
     shw_status s = smooth_check(in, out, nx, ny, nz, radius);
     if (s != SHW_OK) return s;
-    if (!std::isfinite(sigma) || !(sigma > 0.0f)) return SHW_EINVAL;
-    // Eq. 5 sampled at the integer taps, normalised to unit sum (host, double)
-    double w[2 * SHW_MAX_SMOOTH_RADIUS + 1], sum = 0.0;
-    for (int k = -radius; k <= radius; ++k) {
-        w[k + radius] = std::exp(-(double)k * k / (2.0 * (double)sigma * sigma));
-        sum += w[k + radius];
-    }
     SmoothWeights W{};
-    for (int k = 0; k <= 2 * radius; ++k) {
-        W.w[k] = (float)(w[k] / sum);
-        W.w2[k] = make_float2(W.w[k], W.w[k]);
-    }
-    return smooth_dispatch(in, out, nx, ny, nz, W, radius, as_stream(stream));
+    if (!gauss_weights(sigma, radius, W)) return SHW_EINVAL;
+    return smooth_dispatch<false>(in, out, nx, ny, nz, W, radius, nullptr, as_stream(stream));
+}
+
+shw_status shw_smooth_zip(const float *in, const float *first, float *out_pair, int32_t nx, int32_t ny, int32_t nz,
+                          float sigma, int32_t radius, void *stream)
+{
+    if (!in || !first || !out_pair || nx <= 0 || ny <= 0 || nz <= 0 || radius < 0) return SHW_EINVAL;
+    if (!aligned(in, 4) || !aligned(first, 4) || !aligned(out_pair, 8)) return SHW_EINVAL;
+    if (radius > SHW_MAX_SMOOTH_RADIUS) return SHW_EUNSUPPORTED;
+    const size_t bytes = (size_t)nx * ny * nz * 4;
+    if (overlaps(in, bytes, out_pair, 2 * bytes) || overlaps(first, bytes, out_pair, 2 * bytes)) return SHW_EINVAL;
+    SmoothWeights W{};
+    if (!gauss_weights(sigma, radius, W)) return SHW_EINVAL;
+    return smooth_dispatch<true>(in, out_pair, nx, ny, nz, W, radius, first, as_stream(stream));
 }
 
 shw_status shw_smooth_weights(const float *in, float *out, int32_t nx, int32_t ny, int32_t nz, const float *w_host,
@@ -409,7 +455,7 @@ shw_status shw_smooth_weights(const float *in, float *out, int32_t nx, int32_t n
         W.w[k] = w_host[k];
         W.w2[k] = make_float2(w_host[k], w_host[k]);
     }
-    return smooth_dispatch(in, out, nx, ny, nz, W, radius, as_stream(stream));
+    return smooth_dispatch<false>(in, out, nx, ny, nz, W, radius, nullptr, as_stream(stream));
 }
 
 }  // extern "C"

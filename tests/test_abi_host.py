@@ -130,6 +130,32 @@ def test_render_rejects_invalid_arguments_on_host(L):
     assert L.shw_render(b(ok_v), None, b(ok_c), b(p2), out, None, None, None, 0x8000, need - 4, None) == 4  # ENOMEM
 
 
+def test_pair_storage_rules_on_host(L):
+    """The interleaved pair storage: line ratios only, no second volume, no in-ray smoothing,
+    8-byte alignment, not in batch plans; shw_smooth_zip's argument checks."""
+    EINVAL, EUNSUP = 1, 2
+    b = C.byref
+    pv, ok_c, out = _vol(storage=3), _cam(), 0x4000
+    for mode, want in ((4, None), (9, None), (0, EUNSUP), (2, EUNSUP), (7, EUNSUP)):
+        if want is not None:
+            assert L.shw_render(b(pv), None, b(ok_c), b(_params(mode=mode)), out, None, None, None, None, 0,
+                                None) == want, mode
+    assert L.shw_render(b(pv), b(_vol()), b(ok_c), b(_params(mode=4)), out, None, None, None, None, 0,
+                        None) == EINVAL  # a second volume with the pair storage
+    assert L.shw_render(b(pv), None, b(ok_c), b(_params(mode=4, smooth=1, arm=2)), out, None, None, None, None,
+                        0, None) == EUNSUP
+    assert L.shw_render(b(_vol(storage=3, data=0x1004)), None, b(ok_c), b(_params(mode=4)), out, None, None, None,
+                        None, 0, None) == EINVAL  # not 8-byte aligned
+    n = 8 * 8 * 8 * 4
+    assert L.shw_smooth_zip(0, 0x100000, 0x200000, 8, 8, 8, 1.0, 3, None) == EINVAL
+    assert L.shw_smooth_zip(0x100000, 0, 0x200000, 8, 8, 8, 1.0, 3, None) == EINVAL
+    assert L.shw_smooth_zip(0x100000, 0x100000, 0x200004, 8, 8, 8, 1.0, 3, None) == EINVAL  # out misaligned
+    assert L.shw_smooth_zip(0x100000, 0x200000, 0x100000 + n // 2, 8, 8, 8, 1.0, 3, None) == EINVAL  # overlap
+    assert L.shw_smooth_zip(0x100000, 0x200000 - 8, 0x200000, 8, 8, 8, 1.0, 3, None) == EINVAL  # overlap
+    assert L.shw_smooth_zip(0x100000, 0x100000, 0x200000, 8, 8, 8, 0.0, 3, None) == EINVAL  # sigma
+    assert L.shw_smooth_zip(0x100000, 0x100000, 0x200000, 8, 8, 8, 1.0, 17, None) == EUNSUP
+
+
 def test_smooth_and_pack_reject_invalid_arguments_on_host(L):
     EINVAL, EUNSUP, ENOMEM = 1, 2, 4
     assert L.shw_smooth(0, 0x1000, 8, 8, 8, 1.0, 3, None) == EINVAL
@@ -178,6 +204,9 @@ def test_batch_plan_rejects_invalid_arguments_on_host(L):
     assert L.shw_batch_plan_create(b(h), items, 2, b(_params(lut=0)), 0, None) == 1
     assert L.shw_batch_plan_create(b(h), items, 2, b(_params(step=0.0)), 0, None) == 1
     assert L.shw_batch_plan_create(b(h), items, 2, b(_params(smooth=1, arm=2)), 0, None) == 2  # no in-ray smoothing
+    items[1].vol = _vol(storage=3)
+    assert L.shw_batch_plan_create(b(h), items, 2, b(p), 0, None) == 2      # no pair storage
+    items[1].vol = _vol()
     items[1].mode = 4
     assert L.shw_batch_plan_create(b(h), items, 2, b(p), 0, None) == 2      # ratio: unsupported in a batch
     items[1].mode = 7
