@@ -90,12 +90,16 @@ typedef enum {
     SHW_F32 = 0,        /* linear float32 [nz][ny][nx] */
     SHW_BF16_BRICK = 1, /* bricks written by shw_pack_bricks, bfloat16 */
     SHW_F16_BRICK = 2,  /* bricks written by shw_pack_bricks, IEEE binary16 */
-    SHW_F32_PAIR = 3    /* the two co-registered cubes of a line ratio interleaved: float32
+    SHW_F32_PAIR = 3,   /* the two co-registered cubes of a line ratio interleaved: float32
                            [nz][ny][nx][2], element 0 the first cube (the ratio's denominator),
                            element 1 the second; 8-byte aligned.  Only SHW_RATIO and SHW_RATIO_MIP
                            render it (vol2 = NULL; other modes SHW_EUNSUPPORTED), without in-ray
                            smoothing; results equal the two-cube render bit for bit.  Written by
                            shw_smooth_zip */
+    SHW_BF16_PAIR_BRICK = 4, /* the pair storage as bricks: 32-bit elements, the low half the first
+                                cube's bfloat16, the high half the second's; written by
+                                shw_pack_bricks from an SHW_F32_PAIR buffer; the line ratios only */
+    SHW_F16_PAIR_BRICK = 5   /* the same with IEEE binary16 halves */
 } shw_storage;
 
 /* A cube.  data: device.  For SHW_F32 it is the linear float32 array; for the
@@ -208,14 +212,16 @@ shw_status shw_smooth_zip(const float *in, const float *first, float *out_pair, 
 /* ---- reduced-precision brick storage -------------------------------------- */
 
 /* Bytes of the brick buffer for a cube of these dims: ceil(n/32) bricks per axis,
- * each (32+2)^3 elements of 2 bytes (a 1-voxel apron on every face).
- * Returns 0 for invalid arguments. */
+ * each (32+2)^3 elements of 2 bytes (a 1-voxel apron on every face); 4-byte elements
+ * for the pair storages.  Returns 0 for invalid arguments. */
 size_t shw_bricked_bytes(int32_t nx, int32_t ny, int32_t nz, int32_t storage);
 
 /* Pack a float32 cube into bricks, rounding to nearest even.  Brick (bx, by, bz)
  * starts at element ((bz*nby + by)*nbx + bx) * 34^3 and stores, at
  * ((lz*34 + ly)*34 + lx), the voxel (32 bx + lx - 1, 32 by + ly - 1, 32 bz + lz - 1)
- * clamped to the cube.  in: device float32; out: device, out_bytes >= shw_bricked_bytes. */
+ * clamped to the cube.  in: device float32 [nz][ny][nx], or for the pair storages the
+ * SHW_F32_PAIR buffer [nz][ny][nx][2] (8-byte aligned); out: device, 2-byte aligned (4 for
+ * pairs), out_bytes >= shw_bricked_bytes. */
 shw_status shw_pack_bricks(const float *in, int32_t nx, int32_t ny, int32_t nz, int32_t storage,
                            void *out, size_t out_bytes, void *stream);
 

@@ -17,7 +17,7 @@ SHW_OK, SHW_EINVAL, SHW_EUNSUPPORTED, SHW_ECUDA, SHW_ENOMEM, SHW_ETIMEOUT, SHW_E
 MODES = {"mip": 0, "avg": 1, "composite": 2, "spectral": 3, "ratio": 4, "moment1": 5,
          "composite_spectral": 6, "mip_rgb": 7, "composite_rgb": 8, "ratio_mip": 9}
 INTERP = {"nearest": 0, "trilinear": 1}
-STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "pair": 3}
+STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "pair": 3, "bf16_pair": 4, "f16_pair": 5}
 ABI_VERSION = 3
 LUT_SIZE = 256
 MAX_SMOOTH_RADIUS = 16

@@ -188,9 +188,15 @@ def bricked_bytes(dims, storage="bf16") -> int:
 
 
 def pack_bricks(cube: torch.Tensor, storage: str = "bf16") -> BrickVolume:
-    """Round a float32 cube to bf16/f16 32^3 bricks with a 1-voxel apron (shw_pack_bricks)."""
+    """Round a float32 cube to bf16/f16 32^3 bricks with a 1-voxel apron (shw_pack_bricks).
+    A [nz, ny, nx, 2] pair buffer (the line ratios' storage) packs into pair bricks, both
+    cubes' 16-bit values in one 32-bit element (storage "bf16_pair" / "f16_pair")."""
     _need_cuda(cube, "cube", torch.float32)
-    nz, ny, nx = cube.shape
+    if cube.dim() == 4 and cube.shape[3] == 2:
+        nz, ny, nx, _ = cube.shape
+        storage = storage if storage.endswith("_pair") else storage + "_pair"
+    else:
+        nz, ny, nx = cube.shape
     nbytes = bricked_bytes((nx, ny, nz), storage)
     data = torch.empty(nbytes // 2, dtype=torch.int16, device=cube.device)
     check(lib().shw_pack_bricks(cube.data_ptr(), nx, ny, nz, STORAGE[storage], data.data_ptr(), nbytes,

@@ -117,11 +117,10 @@ static bool finite3(const float v[3]) { return std::isfinite(v[0]) && std::isfin
 bool valid_volume(const shw_volume *v)
 {
     if (!v || !v->data || v->nx <= 0 || v->ny <= 0 || v->nz <= 0) return false;
-    if (v->storage != SHW_F32 && v->storage != SHW_BF16_BRICK && v->storage != SHW_F16_BRICK &&
-        v->storage != SHW_F32_PAIR)
-        return false;
+    if (v->storage < SHW_F32 || v->storage > SHW_F16_PAIR_BRICK) return false;
     if (v->storage == SHW_F32 && !aligned(v->data, 4)) return false;
     if (v->storage == SHW_F32_PAIR && !aligned(v->data, 8)) return false;
+    if (v->storage >= SHW_BF16_PAIR_BRICK && !aligned(v->data, 4)) return false;
     if (!aligned(v->data, 2)) return false;
     return true;
 }
@@ -259,7 +258,7 @@ shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_c
     if ((out_scalar && !aligned(out_scalar, 4)) || (out_index && !aligned(out_index, 4)) ||
         (out_nsamples && !aligned(out_nsamples, 4)))
         return SHW_EINVAL;
-    const bool pair = vol->storage == SHW_F32_PAIR;
+    const bool pair = vol->storage >= SHW_F32_PAIR;  // both cubes in one volume
     if (pair) {
         // both cubes in one volume: the line ratios only, no second volume, no in-ray smoothing
         if (vol2) return SHW_EINVAL;
@@ -318,7 +317,7 @@ shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_c
     }
     const shw_volume *v2 = (!pair && (p->mode == SHW_RATIO || p->mode == SHW_RATIO_MIP)) ? vol2 : nullptr;
     cudaStream_t st = as_stream(stream);
-    if (pair) return render_f32_pair(p->mode, p->interp, *vol, *cam, a, st);
+    if (pair) return render_pair(p->mode, p->interp, *vol, *cam, a, st);
     if (p->smooth != SHW_SMOOTH_NONE)
         return vol->storage == SHW_F32 ? render_smooth_f32(p->mode, p->interp, *vol, v2, *cam, a, st)
                                        : render_smooth_b16(p->mode, p->interp, *vol, v2, *cam, a, st);

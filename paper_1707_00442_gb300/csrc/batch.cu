@@ -304,7 +304,7 @@ shw_status shw_batch_plan_create(shw_batch_plan **out, const shw_batch_item *ite
         if (b.mode != SHW_MIP && b.mode != SHW_AVG && b.mode != SHW_COMPOSITE && b.mode != SHW_SPECTRAL)
             return (b.mode >= SHW_RATIO && b.mode <= SHW_RATIO_MIP) ? SHW_EUNSUPPORTED : SHW_EINVAL;
         if ((long long)b.vol.nx * b.vol.ny * b.vol.nz >= (1LL << 31)) return SHW_EUNSUPPORTED;
-        if (b.vol.storage == SHW_F32_PAIR) return SHW_EUNSUPPORTED;  // the line ratios' storage
+        if (b.vol.storage >= SHW_F32_PAIR) return SHW_EUNSUPPORTED;  // the line ratios' storages
         if (max_samples(&b.vol, p->step) > (1LL << 30)) return SHW_EINVAL;
     }
     shw_batch_plan *pl = new (std::nothrow) shw_batch_plan();
@@ -475,7 +475,7 @@ extern "C" shw_status shw_render_batch_noalloc(const shw_batch_item *items, int3
         if (b.mode != SHW_MIP && b.mode != SHW_AVG && b.mode != SHW_COMPOSITE && b.mode != SHW_SPECTRAL)
             return (b.mode >= SHW_RATIO && b.mode <= SHW_RATIO_MIP) ? SHW_EUNSUPPORTED : SHW_EINVAL;
         if ((long long)b.vol.nx * b.vol.ny * b.vol.nz >= (1LL << 31)) return SHW_EUNSUPPORTED;
-        if (b.vol.storage == SHW_F32_PAIR) return SHW_EUNSUPPORTED;  // the line ratios' storage
+        if (b.vol.storage >= SHW_F32_PAIR) return SHW_EUNSUPPORTED;  // the line ratios' storages
         if (max_samples(&b.vol, p->step) > (1LL << 30)) return SHW_EINVAL;
         nwork += (long long)ceil_div(b.cam.width, tile) * ceil_div(b.cam.height, tile);
         cost[i] = (double)b.cam.width * b.cam.height * std::cbrt((double)b.vol.nx * b.vol.ny * b.vol.nz) / p->step;

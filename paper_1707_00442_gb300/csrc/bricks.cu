@@ -44,6 +44,27 @@ __global__ void __launch_bounds__(256) pack_kernel(const float *__restrict__ in,
     }
 }
 
+// The pair storages: both cubes of a line ratio rounded into one 32-bit element (low half
+// the first cube).  in: the float32 pair buffer.
+template <typename T>
+__global__ void __launch_bounds__(256) pack_pair_kernel(const float2 *__restrict__ in, unsigned *__restrict__ out,
+                                                        int nx, int ny, int nz, int nbx, int nby, long long total)
+{
+    constexpr int S = kBrickStored;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long brick = i / kBrickElems;
+        const int e = (int)(i - brick * kBrickElems);
+        const int lz = e / (S * S), ly = (e / S) % S, lx = e % S;
+        const int bx = (int)(brick % nbx), by = (int)((brick / nbx) % nby), bz = (int)(brick / ((long long)nbx * nby));
+        const int x = min(max(bx * kBrick + lx - 1, 0), nx - 1);
+        const int y = min(max(by * kBrick + ly - 1, 0), ny - 1);
+        const int z = min(max(bz * kBrick + lz - 1, 0), nz - 1);
+        const float2 v = __ldg(in + ((size_t)z * ny + y) * nx + x);
+        out[i] = (unsigned)round_store<T>(v.x) | ((unsigned)round_store<T>(v.y) << 16);
+    }
+}
+
 }  // namespace shw
 
 using namespace shw;
@@ -53,23 +74,35 @@ extern "C" {
 size_t shw_bricked_bytes(int32_t nx, int32_t ny, int32_t nz, int32_t storage)
 {
     if (nx <= 0 || ny <= 0 || nz <= 0) return 0;
-    if (storage != SHW_BF16_BRICK && storage != SHW_F16_BRICK) return 0;
+    const bool pair = storage == SHW_BF16_PAIR_BRICK || storage == SHW_F16_PAIR_BRICK;
+    if (storage != SHW_BF16_BRICK && storage != SHW_F16_BRICK && !pair) return 0;
     const size_t nb = (size_t)ceil_div(nx, kBrick) * ceil_div(ny, kBrick) * ceil_div(nz, kBrick);
-    return nb * kBrickElems * 2;
+    return nb * kBrickElems * (pair ? 4 : 2);
 }
 
 shw_status shw_pack_bricks(const float *in, int32_t nx, int32_t ny, int32_t nz, int32_t storage, void *out,
                            size_t out_bytes, void *stream)
 {
     if (!in || !out || nx <= 0 || ny <= 0 || nz <= 0 || !aligned(in, 4) || !aligned(out, 2)) return SHW_EINVAL;
-    if (storage != SHW_BF16_BRICK && storage != SHW_F16_BRICK) return SHW_EINVAL;
+    const bool pair = storage == SHW_BF16_PAIR_BRICK || storage == SHW_F16_PAIR_BRICK;
+    if (storage != SHW_BF16_BRICK && storage != SHW_F16_BRICK && !pair) return SHW_EINVAL;
+    if (pair && (!aligned(in, 8) || !aligned(out, 4))) return SHW_EINVAL;
     const size_t need = shw_bricked_bytes(nx, ny, nz, storage);
     if (out_bytes < need) return SHW_ENOMEM;
-    const long long total = (long long)(need / 2);
+    const long long total = (long long)(need / (pair ? 4 : 2));
     const int nbx = ceil_div(nx, kBrick), nby = ceil_div(ny, kBrick);
     long long blocks = (total + 255) / 256;
     if (blocks > 152LL * 64) blocks = 152LL * 64;  // grid-stride beyond 64 CTAs per SM
     cudaStream_t st = as_stream(stream);
+    if (pair) {
+        const float2 *ip = reinterpret_cast<const float2 *>(in);
+        auto *op = static_cast<unsigned *>(out);
+        if (storage == SHW_BF16_PAIR_BRICK)
+            pack_pair_kernel<__nv_bfloat16><<<(unsigned)blocks, 256, 0, st>>>(ip, op, nx, ny, nz, nbx, nby, total);
+        else
+            pack_pair_kernel<__half><<<(unsigned)blocks, 256, 0, st>>>(ip, op, nx, ny, nz, nbx, nby, total);
+        return after_launch();
+    }
     auto *o = static_cast<unsigned short *>(out);
     if (storage == SHW_BF16_BRICK)
         pack_kernel<__nv_bfloat16><<<(unsigned)blocks, 256, 0, st>>>(in, o, nx, ny, nz, nbx, nby, total);

@@ -948,9 +948,11 @@ shw_status render_f32(int mode, int interp, const shw_volume &v, const shw_volum
                       const RenderArgs &a, cudaStream_t st);
 shw_status render_f32_big(int mode, int interp, const shw_volume &v, const shw_volume *v2, const shw_camera &cam,
                           const RenderArgs &a, cudaStream_t st);
-// the line ratios on the interleaved pair storage
+// the line ratios on the interleaved pair storages (any of SHW_F32_PAIR, SHW_*_PAIR_BRICK)
 shw_status render_f32_pair(int mode, int interp, const shw_volume &v, const shw_camera &cam, const RenderArgs &a,
                            cudaStream_t st);
+shw_status render_pair(int mode, int interp, const shw_volume &v, const shw_camera &cam, const RenderArgs &a,
+                       cudaStream_t st);
 // in-ray smoothing (a.smooth != SHW_SMOOTH_NONE), any storage
 shw_status render_smooth_f32(int mode, int interp, const shw_volume &v, const shw_volume *v2,
                              const shw_camera &cam, const RenderArgs &a, cudaStream_t st);

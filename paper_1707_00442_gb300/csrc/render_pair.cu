@@ -1,4 +1,5 @@
-// render_pair.cu -- the line ratios (Algorithms 12-14) on the interleaved pair storage.
+// render_pair.cu -- the line ratios (Algorithms 12-14) on the interleaved pair storages
+// (float32 pairs and 16-bit pair bricks).
 #include "render_impl.cuh"
 
 namespace shw {
@@ -14,6 +15,26 @@ shw_status render_f32_pair(int mode, int interp, const shw_volume &v, const shw_
     }
     SamplerF32Pair<long long> s{p, v.nx, v.ny, v.nz, (long long)v.nx, (long long)v.nx * v.ny};
     return launch_render_modes<false>(mode, interp, s, s, cam, a, st);
+}
+
+template <typename T>
+static shw_status render_bricks_pair(int mode, int interp, const shw_volume &v, const shw_camera &cam,
+                                     const RenderArgs &a, cudaStream_t st)
+{
+    SamplerBrickPair<T> s{static_cast<const unsigned *>(v.data), v.nx, v.ny, v.nz, ceil_div(v.nx, kBrick),
+                          ceil_div(v.ny, kBrick)};
+    return launch_render_modes<false>(mode, interp, s, s, cam, a, st);
+}
+
+shw_status render_pair(int mode, int interp, const shw_volume &v, const shw_camera &cam, const RenderArgs &a,
+                       cudaStream_t st)
+{
+    switch (v.storage) {
+    case SHW_F32_PAIR: return render_f32_pair(mode, interp, v, cam, a, st);
+    case SHW_BF16_PAIR_BRICK: return render_bricks_pair<__nv_bfloat16>(mode, interp, v, cam, a, st);
+    case SHW_F16_PAIR_BRICK: return render_bricks_pair<__half>(mode, interp, v, cam, a, st);
+    default: return SHW_EINVAL;
+    }
 }
 
 }  // namespace shw

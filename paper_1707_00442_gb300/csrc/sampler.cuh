@@ -228,6 +228,67 @@ struct SamplerF32Pair {
     }
 };
 
+// One 32-bit element of the pair bricks -> (first, second) in FP32.
+template <typename T>
+__device__ __forceinline__ float2 pair_to_f32(unsigned w);
+template <>
+__device__ __forceinline__ float2 pair_to_f32<__nv_bfloat16>(unsigned w)
+{
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+template <>
+__device__ __forceinline__ float2 pair_to_f32<__half>(unsigned w)
+{
+    return __half22float2(__halves2half2(__ushort_as_half((unsigned short)(w & 0xffffu)),
+                                         __ushort_as_half((unsigned short)(w >> 16))));
+}
+
+// The pair storage as 32^3 bricks with the 1-voxel apron (layout of SamplerBrick), each
+// element both cubes' 16-bit values.
+template <typename T>
+struct SamplerBrickPair {
+    static constexpr bool kLinearF32 = false;
+    static constexpr bool kPair = true;
+    const unsigned *__restrict__ v;
+    int nx, ny, nz;
+    int nbx, nby;
+
+    static constexpr int S = kBrickStored;
+
+    template <bool CLAMP = true>
+    __device__ __forceinline__ float2 nearest2(long long X, long long Y, long long Z) const
+    {
+        int x = fx_round(X), y = fx_round(Y), z = fx_round(Z);
+        if (CLAMP) {
+            x = clampi(x, 0, nx - 1);
+            y = clampi(y, 0, ny - 1);
+            z = clampi(z, 0, nz - 1);
+        }
+        const int bx = x >> 5, by = y >> 5, bz = z >> 5;
+        const long long brick = ((long long)bz * nby + by) * nbx + bx;
+        const unsigned *p = v + (brick * kBrickElems + (((z & 31) + 1) * S + ((y & 31) + 1)) * S + (x & 31) + 1);
+        return pair_to_f32<T>(__ldg(p));
+    }
+
+    template <bool CLAMP = true>
+    __device__ __forceinline__ void corners2(int ix, int iy, int iz, float2 c[8]) const
+    {
+        // ix in [-1, n-1]: brick of max(ix, 0), local index ix - 32 b + 1 in [0, 32]
+        const int bx = max(ix, 0) >> 5, by = max(iy, 0) >> 5, bz = max(iz, 0) >> 5;
+        const int lx = ix - (bx << 5) + 1, ly = iy - (by << 5) + 1, lz = iz - (bz << 5) + 1;
+        const long long brick = ((long long)bz * nby + by) * nbx + bx;
+        const unsigned *p = v + (brick * kBrickElems + (lz * S + ly) * S + lx);
+        c[0] = pair_to_f32<T>(__ldg(p));
+        c[1] = pair_to_f32<T>(__ldg(p + 1));
+        c[2] = pair_to_f32<T>(__ldg(p + S));
+        c[3] = pair_to_f32<T>(__ldg(p + S + 1));
+        c[4] = pair_to_f32<T>(__ldg(p + S * S));
+        c[5] = pair_to_f32<T>(__ldg(p + S * S + 1));
+        c[6] = pair_to_f32<T>(__ldg(p + S * S + S));
+        c[7] = pair_to_f32<T>(__ldg(p + S * S + S + 1));
+    }
+};
+
 // The pair sampler's corner cache (see CellCache below).
 struct CellCachePair {
     int ix = -4, iy = -4, iz = -4;

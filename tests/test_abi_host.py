@@ -154,6 +154,19 @@ def test_pair_storage_rules_on_host(L):
     assert L.shw_smooth_zip(0x100000, 0x200000 - 8, 0x200000, 8, 8, 8, 1.0, 3, None) == EINVAL  # overlap
     assert L.shw_smooth_zip(0x100000, 0x100000, 0x200000, 8, 8, 8, 0.0, 3, None) == EINVAL  # sigma
     assert L.shw_smooth_zip(0x100000, 0x100000, 0x200000, 8, 8, 8, 1.0, 17, None) == EUNSUP
+    # pair bricks: 4-byte elements, an 8-byte aligned float32 pair buffer in, line ratios only
+    assert L.shw_bricked_bytes(64, 64, 64, 4) == L.shw_bricked_bytes(64, 64, 64, 5) == 8 * 34 ** 3 * 4
+    assert L.shw_bricked_bytes(64, 64, 64, 6) == 0
+    assert L.shw_pack_bricks(0x100004, 64, 64, 64, 4, 0x800000, 1 << 30, None) == EINVAL  # pair input 8-aligned
+    assert L.shw_pack_bricks(0x100000, 64, 64, 64, 4, 0x800002, 1 << 30, None) == EINVAL  # 4-byte elements
+    assert L.shw_pack_bricks(0x100000, 64, 64, 64, 5, 0x800000, 1000, None) == 4          # ENOMEM
+    for st in (4, 5):
+        assert L.shw_render(b(_vol(storage=st)), None, b(ok_c), b(_params(mode=0)), out, None, None, None, None, 0,
+                            None) == EUNSUP
+        assert L.shw_render(b(_vol(storage=st, data=0x1002)), None, b(ok_c), b(_params(mode=4)), out, None, None,
+                            None, None, 0, None) == EINVAL
+    assert L.shw_render(b(_vol(storage=6)), None, b(ok_c), b(_params(mode=4)), out, None, None, None, None, 0,
+                        None) == EINVAL
 
 
 def test_smooth_and_pack_reject_invalid_arguments_on_host(L):

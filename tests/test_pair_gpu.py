@@ -111,3 +111,28 @@ def test_pair_storage_rejections(m, ragged):
         m.render(pr, cam, "ratio", lut=lut, smooth="box", smooth_arm=1)
     assert e.value.status == 2
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+@pytest.mark.parametrize("mode", ["ratio", "ratio_mip"])
+@pytest.mark.parametrize("interp", ["trilinear", "nearest"])
+def test_pair_bricks_equal_two_brick_render(m, storage, mode, interp):
+    """Pair bricks (both cubes' 16-bit values in one 32-bit element) render the line ratios
+    exactly like two separate brick volumes, and like the oracle on the rounded cubes."""
+    dims = (70, 45, 66)
+    c1 = scene.tiny_cube(config_id=33, dims=dims, n_sources=3)
+    c2 = scene.ratio_cube(c1, config_id=33)
+    cam = scene.orbit_camera(dims, -25, 30, 80, 64)
+    lut = scene.ratio_lut()
+    kw = dict(lo=0.0, hi=1.0, ratio_floor=1.0, interp=interp)
+    pb = m.pack_bricks(_pair(c1, c2), storage)
+    assert pb.storage == storage + "_pair"
+    one = gpu_render(m, pb, cam, mode, to_dev(lut), **kw)
+    two = gpu_render(m, m.pack_bricks(to_dev(c1), storage), cam, mode, to_dev(lut),
+                     vol2=m.pack_bricks(to_dev(c2), storage), **kw)
+    for k in two:
+        assert np.array_equal(two[k], one[k]), k
+    rnd = oracle.round_bf16 if storage == "bf16" else oracle.round_f16
+    o = oracle.render(rnd(c1), cam, mode, lut=lut, cube2=rnd(c2), eps_pos=1e-6, eps_val=1e-4, **kw)
+    scale = float(o["scalar"].max() - o["scalar"].min()) or 1.0
+    compare(one, o, mode, scale=scale, max_fragile=0.05, what=f"{storage}_pair/{mode}/{interp}")
