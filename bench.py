@@ -188,6 +188,44 @@ class Step:
         return per
 
 
+def bind_to_gpu_node(torch, dev):
+    """Run this process on the host cores next to the GPU (its PCI device's local CPU list),
+    so that the pinned input buffers are placed in the memory attached to them.  Best
+    effort; returns the NUMA node, or None where the system does not say."""
+    try:
+        bus = torch.cuda.get_device_properties(dev).pci_bus_id.lower()
+        base = f"/sys/bus/pci/devices/{bus}"
+        if not os.path.exists(base) and bus.count(":") == 2:
+            base = f"/sys/bus/pci/devices/{bus[4:] if len(bus.split(':')[0]) > 4 else bus}"
+        cpus = open(os.path.join(base, "local_cpulist")).read().strip()
+        node = int(open(os.path.join(base, "numa_node")).read().strip())
+        sel = set()
+        for part in cpus.split(","):
+            a, _, b = part.partition("-")
+            sel.update(range(int(a), int(b or a) + 1))
+        if sel:
+            os.sched_setaffinity(0, sel)
+        log(f"host: bound to the GPU's local cores {cpus} (NUMA node {node})")
+        return node
+    except Exception as e:  # noqa: BLE001 -- a hint only
+        log(f"host: GPU-local cores unknown ({e}); running unbound")
+        return None
+
+
+def copy_bandwidth(torch, dst, src, reps=3):
+    """Host-to-device copy rate of one pinned buffer (GB/s), for the end-to-end record."""
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dst.copy_(src, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return src.numel() * src.element_size() / (statistics.median(ts) * 1e-3) / 1e9
+
+
 class E2EPipeline:
     """The step fed from and drained to host memory, as a stream of frames would run it:
     uploads on one stream, kernels on the current stream, downloads on a third.  A cube's
@@ -310,11 +348,13 @@ def run_ours(args):
     shw._lib.lib()  # the CUDA library must load: there is no fallback
 
     W = WORKLOADS[args.workload]
+    host_node = bind_to_gpu_node(torch, dev)
     cube, cube2 = make_inputs(W)
     nvox = cube.size
     cube_h = torch.from_numpy(cube).pin_memory()
     cube2_h = torch.from_numpy(cube2).pin_memory()
     cube_t, cube2_t = cube_h.to(dev), cube2_h.to(dev)
+    h2d_gbs = copy_bandwidth(torch, cube_t, cube_h)
     step = Step(shw, torch, cube_t, cube2_t, W)
     samples_per = step.count_samples()
     samples_step = sum(samples_per.values())
@@ -397,7 +437,8 @@ def run_ours(args):
             "roofline": dr,
             "roofline_kernels": roof,
             "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e / args.steps, 3)},
+                    "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e / args.steps, 3),
+                    "h2d_gbs": round(h2d_gbs, 1), "host_numa_node": host_node},
             "gpu_launches": int(launches),
             "clocks": clk,
         }
