@@ -193,10 +193,14 @@ def bind_to_gpu_node(torch, dev):
     so that the pinned input buffers are placed in the memory attached to them.  Best
     effort; returns the NUMA node, or None where the system does not say."""
     try:
-        bus = torch.cuda.get_device_properties(dev).pci_bus_id.lower()
+        pr = torch.cuda.get_device_properties(dev)
+        bus = pr.pci_bus_id
+        if isinstance(bus, int):  # numeric fields (domain, bus, device)
+            bus = f"{getattr(pr, 'pci_domain_id', 0):04x}:{bus:02x}:{getattr(pr, 'pci_device_id', 0):02x}.0"
+        bus = bus.lower()
         base = f"/sys/bus/pci/devices/{bus}"
-        if not os.path.exists(base) and bus.count(":") == 2:
-            base = f"/sys/bus/pci/devices/{bus[4:] if len(bus.split(':')[0]) > 4 else bus}"
+        if not os.path.exists(base) and len(bus.split(":")[0]) > 4:  # an 8-digit domain
+            base = f"/sys/bus/pci/devices/{bus[len(bus.split(':')[0]) - 4:]}"
         cpus = open(os.path.join(base, "local_cpulist")).read().strip()
         node = int(open(os.path.join(base, "numa_node")).read().strip())
         sel = set()
@@ -240,6 +244,9 @@ class E2EPipeline:
         self.cube_h, self.cube2_h, self.rgba_h = cube_h, cube2_h, rgba_h
         dev = step.cube.device
         self.cin, self.cout = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+        # two sets of device images, alternating by step, so no render waits for the previous
+        # step's download of its image
+        self.outs = [step.outs, {m: {"rgba": torch.empty_like(o["rgba"])} for m, o in step.outs.items()}]
 
     def _ev(self, stream):
         e = self.torch.cuda.Event()
@@ -250,9 +257,10 @@ class E2EPipeline:
         torch, st, shw, w = self.torch, self.step, self.step.shw, self.step.w
         main = torch.cuda.current_stream()
         free1 = free2 = self._ev(main)
-        out_free = {m: free1 for m in WL.MODES}
+        out_free = [{m: free1 for m in WL.MODES}, {m: free1 for m in WL.MODES}]
         first = [m for m in WL.MODES if m != "ratio"]
-        for _ in range(steps):
+        for i in range(steps):
+            outs, ofree = self.outs[i & 1], out_free[i & 1]
             self.cin.wait_event(free1)
             with torch.cuda.stream(self.cin):
                 st.cube.copy_(self.cube_h, non_blocking=True)
@@ -269,16 +277,38 @@ class E2EPipeline:
                     main.wait_event(in2)
                     shw.smooth_zip(st.cube2, st.s1, w["sigma"], w["radius"], out=st.pair)
                     free2 = self._ev(main)
-                main.wait_event(out_free[m])
+                main.wait_event(ofree[m])
                 kw = dict(WL.MODE_PARAMS[m])
                 shw.render(st.vol_of(m), st.cam, m, lut=st.rlut if m == "ratio" else st.lut, step=w["step"],
-                           scalar=False, index=False, nsamples=False, out=st.outs[m], **kw)
+                           scalar=False, index=False, nsamples=False, out=outs[m], **kw)
                 self.cout.wait_event(self._ev(main))
                 with torch.cuda.stream(self.cout):
-                    self.rgba_h[m].copy_(st.outs[m]["rgba"], non_blocking=True)
-                out_free[m] = self._ev(self.cout)
+                    self.rgba_h[m].copy_(outs[m]["rgba"], non_blocking=True)
+                ofree[m] = self._ev(self.cout)
         main.wait_stream(self.cin)
         main.wait_stream(self.cout)
+
+    def copies_only(self, steps):
+        """CUDA-event time (ms) of `steps` steps' uploads and downloads alone, on the same streams."""
+        torch, st = self.torch, self.step
+        main = torch.cuda.current_stream()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(main)
+        self.cin.wait_stream(main)
+        self.cout.wait_stream(main)
+        for _ in range(steps):
+            with torch.cuda.stream(self.cin):
+                st.cube.copy_(self.cube_h, non_blocking=True)
+                st.cube2.copy_(self.cube2_h, non_blocking=True)
+            with torch.cuda.stream(self.cout):
+                for m in WL.MODES:
+                    self.rgba_h[m].copy_(st.outs[m]["rgba"], non_blocking=True)
+        main.wait_stream(self.cin)
+        main.wait_stream(self.cout)
+        e1.record(main)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
 
 
 # --------------------------------------------------------------------------- roofline
@@ -405,6 +435,7 @@ def run_ours(args):
     e1.record()
     barrier()
     ms_e2e = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    ms_copies = e2e.copies_only(args.steps)  # the same uploads and downloads without kernels
     h2d = 2 * nvox * 4
     d2h = sum(int(np.prod(rgba_h[m].shape)) * 4 for m in WL.MODES)
 
@@ -438,7 +469,8 @@ def run_ours(args):
             "roofline_kernels": roof,
             "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e / args.steps, 3),
-                    "h2d_gbs": round(h2d_gbs, 1), "host_numa_node": host_node},
+                    "h2d_gbs": round(h2d_gbs, 1), "host_numa_node": host_node,
+                    "copies_only_ms_per_step": round(ms_copies / args.steps, 3)},
             "gpu_launches": int(launches),
             "clocks": clk,
         }
