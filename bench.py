@@ -739,6 +739,10 @@ def run_case(args):
     if args.case == "smooth":
         out = torch.empty_like(cube)
         fn = lambda: shw.smooth(cube, WL.SURVEY["sigma"], WL.SURVEY["radius"], out=out)  # noqa: E731
+    elif args.case == "smooth-zip":
+        first = torch.from_numpy(scene.ratio_cube(cube.cpu().numpy())).cuda()
+        out = torch.empty(tuple(cube.shape) + (2,), dtype=torch.float32, device="cuda")
+        fn = lambda: shw.smooth_zip(cube, first, WL.SURVEY["sigma"], WL.SURVEY["radius"], out=out)  # noqa: E731
     elif args.case == "in-ray-smoothing":
         print(json.dumps(run_in_ray_smoothing(shw, torch, "cuda")), flush=True)
         shw.sync_status()
@@ -753,7 +757,11 @@ def run_case(args):
         elif args.smooth.startswith("gauss"):
             n = int(args.smooth[5:])
             kw.update(smooth="taps", smooth_taps=shw.binomial_taps(9, drop=2) if n == 9 else shw.binomial_taps(n))
-        fn = lambda: shw.render(cube, cam, args.mode, lut=lut, scalar=False, index=False,  # noqa: E731
+        vol = cube
+        if args.mode in ("ratio", "ratio_mip"):  # the survey step's form: the pair storage
+            vol = torch.stack([cube, torch.from_numpy(scene.ratio_cube(cube.cpu().numpy())).cuda()], dim=-1)
+            lut = torch.from_numpy(scene.ratio_lut()).cuda()
+        fn = lambda: shw.render(vol, cam, args.mode, lut=lut, scalar=False, index=False,  # noqa: E731
                                 nsamples=False, out=o, **kw)
     t = _timeit(torch, fn, reps=args.steps, warm=args.warmup)
     shw.sync_status()
@@ -772,7 +780,7 @@ def main():
     ap.add_argument("--workload", default="survey", choices=sorted(WORKLOADS),
                     help="survey: the headline workload; survey-small: the same step on a smaller cube "
                          "(profiler captures)")
-    ap.add_argument("--case", choices=["moment-map", "render", "smooth", "in-ray-smoothing"],
+    ap.add_argument("--case", choices=["moment-map", "render", "smooth", "smooth-zip", "in-ray-smoothing"],
                     help="run one small case of one kernel family for a profiler capture, then exit")
     ap.add_argument("--dims", default="384,384,768", help="--case: cube dims nx,ny,nz")
     ap.add_argument("--mode", default="mip", help="--case: transfer function")

@@ -150,12 +150,15 @@ __device__ __forceinline__ void clamp_tile_edges(float *tile, int c_lo, int c_hi
     }
 }
 
+#ifndef SHW_SMOOTH_ZIP_MINB
+#define SHW_SMOOTH_ZIP_MINB 2  // the zip form holds the first cube's values of a plane in registers too
+#endif
 #ifndef SHW_SMOOTH_MINB
 #define SHW_SMOOTH_MINB 3  // 80 registers, no spills, with the weight pairs in the parameters
 #endif
 
 template <int R, bool ZIP>
-__global__ void __launch_bounds__(kSmThreads, SHW_SMOOTH_MINB)
+__global__ void __launch_bounds__(kSmThreads, ZIP ? SHW_SMOOTH_ZIP_MINB : SHW_SMOOTH_MINB)
     smooth_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict__ out, int nx, int ny, int nz,
                       int zchunk, SmoothWeights W, unsigned *err, const float *__restrict__ first)
 {
@@ -213,6 +216,20 @@ __global__ void __launch_bounds__(kSmThreads, SHW_SMOOTH_MINB)
             const int i = base + slot;
             if (i >= nplanes) break;
             const int stage = i % kSmStages;
+            // ZIP: this plane's output pairs take the first cube's values; load them now, so
+            // the latency hides behind the passes (a lane outside the cube loads nothing)
+            float2 fpre[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+            if constexpr (ZIP) {
+                if (i >= 2 * R && gx < nx) {
+                    const size_t zrow = (size_t)(zfirst + i - R) * plane;
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        const int gy = y0 + 2 * rg + j;
+                        if (gy < ny)
+                            fpre[j] = __ldg(reinterpret_cast<const float2 *>(first + zrow + (size_t)gy * nx + gx));
+                    }
+                }
+            }
             const bool ok = mbar_wait(&bars[stage], (uint32_t)((i / kSmStages) & 1), err);
 #if !SHW_SMOOTH_ONEBAR
             if (__syncthreads_or(!ok)) {
@@ -288,7 +305,7 @@ __global__ void __launch_bounds__(kSmThreads, SHW_SMOOTH_MINB)
                         const size_t o = (size_t)zo * plane + (size_t)gy * nx + gx;
                         if constexpr (ZIP) {
                             // (first, smoothed) for the voxels gx and gx + 1: one 16-byte store
-                            const float2 f = __ldg(reinterpret_cast<const float2 *>(first + o));
+                            const float2 f = fpre[j];
                             *reinterpret_cast<float4 *>(out + 2 * o) = make_float4(f.x, acc.x, f.y, acc.y);
                         } else {
                             *reinterpret_cast<float2 *>(out + o) = acc;
