@@ -962,6 +962,10 @@ shw_status render_bf16(int mode, int interp, const shw_volume &v, const shw_volu
                        const RenderArgs &a, cudaStream_t st);
 shw_status render_f16(int mode, int interp, const shw_volume &v, const shw_volume *v2, const shw_camera &cam,
                       const RenderArgs &a, cudaStream_t st);
+shw_status render_bf16_big(int mode, int interp, const shw_volume &v, const shw_volume *v2, const shw_camera &cam,
+                           const RenderArgs &a, cudaStream_t st);
+shw_status render_f16_big(int mode, int interp, const shw_volume &v, const shw_volume *v2, const shw_camera &cam,
+                          const RenderArgs &a, cudaStream_t st);
 // the plane sweep for orthographic spectral-axis views (render_axis.cu); SHW_EUNSUPPORTED if it does not apply
 shw_status render_axis(int mode, int interp, const shw_volume &v, const shw_camera &cam, const RenderArgs &a,
                        cudaStream_t st);

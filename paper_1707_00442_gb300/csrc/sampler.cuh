@@ -115,7 +115,8 @@ __device__ __forceinline__ float to_f32<__half>(unsigned short raw)
 // 32^3 bricks with a 1-voxel replicated apron, stored as 34^3 16-bit values
 // (layout documented with shw_pack_bricks).  The apron makes the 8 corners of
 // every cell live in one brick, at fixed offsets from the cell's base.
-template <typename T>
+// Idx: int when the brick buffer holds < 2^31 elements (cheaper address arithmetic), else long long.
+template <typename T, typename Idx = long long>
 struct SamplerBrick {
     static constexpr bool kLinearF32 = false;
     static constexpr bool kPair = false;
@@ -130,8 +131,8 @@ struct SamplerBrick {
         // ix in [-1, n-1]: brick of max(ix, 0), local index ix - 32 b + 1 in [0, 32]
         const int bx = max(ix, 0) >> 5, by = max(iy, 0) >> 5, bz = max(iz, 0) >> 5;
         const int lx = ix - (bx << 5) + 1, ly = iy - (by << 5) + 1, lz = iz - (bz << 5) + 1;
-        const long long brick = ((long long)bz * nby + by) * nbx + bx;
-        return v + (brick * kBrickElems + (lz * S + ly) * S + lx);
+        const Idx brick = ((Idx)bz * nby + by) * nbx + bx;
+        return v + (brick * (Idx)kBrickElems + (lz * S + ly) * S + lx);
     }
 
     template <bool CLAMP = true>
@@ -144,8 +145,8 @@ struct SamplerBrick {
             z = clampi(z, 0, nz - 1);
         }
         const int bx = x >> 5, by = y >> 5, bz = z >> 5;
-        const long long brick = ((long long)bz * nby + by) * nbx + bx;
-        const unsigned short *p = v + (brick * kBrickElems + (((z & 31) + 1) * S + ((y & 31) + 1)) * S + (x & 31) + 1);
+        const Idx brick = ((Idx)bz * nby + by) * nbx + bx;
+        const unsigned short *p = v + (brick * (Idx)kBrickElems + (((z & 31) + 1) * S + ((y & 31) + 1)) * S + (x & 31) + 1);
         return to_f32<T>(__ldg(p));
     }
 
