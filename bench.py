@@ -485,10 +485,10 @@ def run_ours(args):
 # ncu dram bytes (read + write) per launch of the dominant kernel, from one capture of the
 # current build (profiles/survey_step_dram_traffic.md); reset to absent when the kernel changes
 TRAFFIC_PER_LAUNCH: dict = {
-    "smooth": 1280741120 + 1035349248, "smooth2": 2325389056 + 2100782848,
-    "render_mip": 1518867456 + 22110976, "render_avg": 1582366208 + 22686464,
-    "render_composite": 1395104256 + 24589312, "render_spectral": 1561487872 + 22204416,
-    "render_ratio": 2634651904 + 24575744}
+    "smooth": 1273792768 + 1034413824, "smooth2": 2353712128 + 2102823680,
+    "render_mip": 1522822912 + 23123712, "render_avg": 1588480768 + 22132992,
+    "render_composite": 1364563456 + 24787456, "render_spectral": 1565263104 + 22183936,
+    "render_ratio": 2565604608 + 25061376}
 
 
 # --------------------------------------------------------------------------- variants

@@ -21,8 +21,14 @@ template <typename T>
 static shw_status render_bricks_pair(int mode, int interp, const shw_volume &v, const shw_camera &cam,
                                      const RenderArgs &a, cudaStream_t st)
 {
-    SamplerBrickPair<T> s{static_cast<const unsigned *>(v.data), v.nx, v.ny, v.nz, ceil_div(v.nx, kBrick),
-                          ceil_div(v.ny, kBrick)};
+    const unsigned *p = static_cast<const unsigned *>(v.data);
+    const int nbx = ceil_div(v.nx, kBrick), nby = ceil_div(v.ny, kBrick);
+    const long long elems = (long long)nbx * nby * ceil_div(v.nz, kBrick) * kBrickElems;
+    if (elems < (1LL << 31)) {  // 32-bit element offsets
+        SamplerBrickPair<T, int> s{p, v.nx, v.ny, v.nz, nbx, nby};
+        return launch_render_modes<false>(mode, interp, s, s, cam, a, st);
+    }
+    SamplerBrickPair<T, long long> s{p, v.nx, v.ny, v.nz, nbx, nby};
     return launch_render_modes<false>(mode, interp, s, s, cam, a, st);
 }
 

@@ -246,7 +246,7 @@ __device__ __forceinline__ float2 pair_to_f32<__half>(unsigned w)
 
 // The pair storage as 32^3 bricks with the 1-voxel apron (layout of SamplerBrick), each
 // element both cubes' 16-bit values.
-template <typename T>
+template <typename T, typename Idx = long long>
 struct SamplerBrickPair {
     static constexpr bool kLinearF32 = false;
     static constexpr bool kPair = true;
@@ -266,8 +266,8 @@ struct SamplerBrickPair {
             z = clampi(z, 0, nz - 1);
         }
         const int bx = x >> 5, by = y >> 5, bz = z >> 5;
-        const long long brick = ((long long)bz * nby + by) * nbx + bx;
-        const unsigned *p = v + (brick * kBrickElems + (((z & 31) + 1) * S + ((y & 31) + 1)) * S + (x & 31) + 1);
+        const Idx brick = ((Idx)bz * nby + by) * nbx + bx;
+        const unsigned *p = v + (brick * (Idx)kBrickElems + (((z & 31) + 1) * S + ((y & 31) + 1)) * S + (x & 31) + 1);
         return pair_to_f32<T>(__ldg(p));
     }
 
@@ -277,8 +277,8 @@ struct SamplerBrickPair {
         // ix in [-1, n-1]: brick of max(ix, 0), local index ix - 32 b + 1 in [0, 32]
         const int bx = max(ix, 0) >> 5, by = max(iy, 0) >> 5, bz = max(iz, 0) >> 5;
         const int lx = ix - (bx << 5) + 1, ly = iy - (by << 5) + 1, lz = iz - (bz << 5) + 1;
-        const long long brick = ((long long)bz * nby + by) * nbx + bx;
-        const unsigned *p = v + (brick * kBrickElems + (lz * S + ly) * S + lx);
+        const Idx brick = ((Idx)bz * nby + by) * nbx + bx;
+        const unsigned *p = v + (brick * (Idx)kBrickElems + (lz * S + ly) * S + lx);
         c[0] = pair_to_f32<T>(__ldg(p));
         c[1] = pair_to_f32<T>(__ldg(p + 1));
         c[2] = pair_to_f32<T>(__ldg(p + S));
