@@ -48,7 +48,8 @@ static_assert((kAxStages & (kAxStages - 1)) == 0, "the ring depth is a power of 
 
 // The fixed staged box: enough for a 64 x 16 tile at up to one voxel per pixel,
 // axis-aligned (extent 63 x 15, plus the alignment and rounding margins).
-constexpr int kFixBW = 72, kFixBH = 21;
+// fixed box: a 64 x kAxTY tile at up to one voxel per pixel, plus the margins of render_axis
+constexpr int kFixBW = 72, kFixBH = kAxTY + 5;
 constexpr int kFixStride = (kFixBW * kFixBH + 31) & ~31;  // floats per stage, 128-byte multiple
 
 // bounded waits that sleep between polls: kAxWaitPolls x kAxSleepNs is about a second
