@@ -87,3 +87,29 @@ def test_survey_smooth_sampled(m, survey):
     o = oracle.smooth_points(survey[2], oracle.gauss_weights(sig, r), ids)
     gv = g.reshape(-1)[torch.from_numpy(ids).cuda()].cpu().numpy()
     assert np.abs(gv - o).max() <= TOL_F32 * float(cube.max() - cube.min())
+
+
+def test_survey_step_ratio_on_pair_storage(m, survey, pixels):
+    """The benchmark's form of the line ratio at full size: the first cube smoothed, the second
+    smoothed into the pair storage (shw_smooth_zip), the ratio rendered from the pair.  The
+    pair holds exactly the two smoothed cubes, and the image matches the oracle run on them."""
+    cube, c2 = survey[0], survey[1]
+    sig, r = W.SURVEY["sigma"], W.SURVEY["radius"]
+    s1 = m.smooth(to_dev(cube), sig, r)
+    s2 = m.smooth(to_dev(c2), sig, r)
+    pair = m.smooth_zip(to_dev(c2), s1, sig, r)
+    m.sync_status()
+    assert torch.equal(pair[..., 0], s1) and torch.equal(pair[..., 1], s2)
+    cam = W.survey_camera()
+    lut = scene.ratio_lut()
+    kw = dict(W.MODE_PARAMS["ratio"])
+    out = m.render(pair, cam, "ratio", lut=to_dev(lut), step=W.SURVEY["step"], **kw)
+    m.sync_status()
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    s1h, s2h = s1.cpu().numpy().astype(np.float64), s2.cpu().numpy().astype(np.float64)
+    del s1, s2, pair
+    o = oracle.render(s1h, cam, "ratio", lut=lut, cube2=s2h, pixels=pixels, step=W.SURVEY["step"],
+                      eps_pos=1e-6, eps_val=1e-4, **kw)
+    scale = float(o["scalar"].max() - o["scalar"].min()) or 1.0
+    st = compare(g, o, "ratio", scale=scale, pixels=pixels, what="survey/ratio-pair")
+    print("ratio-pair", st)
