@@ -7,8 +7,11 @@
  * at a fixed step (Algorithm 1) and folds them with one transfer function --
  * maximum intensity (Eq. 1, Algorithm 2), average (Eq. 3), front-to-back alpha
  * compositing through an RGBA colour map (Eq. 2, Algorithm 3), spectral-position
- * colouring (Algorithm 4) or the per-sample ratio of two cubes (Algorithm 14) --
- * and smooths cubes with a separable 3-D Gaussian (Eqs. 5-6, Algorithm 9).
+ * colouring (Algorithm 4) or the per-sample ratio of two cubes (Algorithm 14); also the
+ * first moment (Eq. 4), AVIP_1 / MIP_RGB / AVIP_RGB (Algorithms 5-7), the line ratio's
+ * Method 1 (Algorithms 12-13), per-sample clipping and domain scaling (Algorithms 10-11)
+ * and in-ray box / per-axis tap smoothing (Algorithms 8-9) -- and smooths cubes with a
+ * separable 3-D Gaussian (Eqs. 5-6, Algorithm 9).
  *
  * Conventions shared by every call
  * --------------------------------
