@@ -195,8 +195,10 @@ def pack_bricks(cube: torch.Tensor, storage: str = "bf16") -> BrickVolume:
     if cube.dim() == 4 and cube.shape[3] == 2:
         nz, ny, nx, _ = cube.shape
         storage = storage if storage.endswith("_pair") else storage + "_pair"
-    else:
+    elif cube.dim() == 3 and not storage.endswith("_pair"):
         nz, ny, nx = cube.shape
+    else:
+        raise ValueError("pair bricks pack a [nz, ny, nx, 2] pair buffer; a cube must be [nz, ny, nx]")
     nbytes = bricked_bytes((nx, ny, nz), storage)
     data = torch.empty(nbytes // 2, dtype=torch.int16, device=cube.device)
     check(lib().shw_pack_bricks(cube.data_ptr(), nx, ny, nz, STORAGE[storage], data.data_ptr(), nbytes,
