@@ -459,7 +459,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": W["name"], "cube": "x".join(map(str, W["dims"])) + " f32 + ratio cube",
                        "image": f"{W['width']}x{W['height']} perspective yaw30 pitch20 fov45", "step_vox": W["step"],
-                       "modes": WL.MODES, "smooth": "sigma 2, radius 6, both cubes", "interp": "trilinear",
+                       "modes": WL.MODES, "smooth": "sigma 2, radius 6, both cubes (the second into the line ratio's pair storage)", "interp": "trilinear",
                        "l2": "inputs larger than L2 (1 GiB cubes vs 129 MB L2)",
                        "samples_per_step": samples_step, "parallelism": f"replicas x{world}"},
             "fps": {m: round(1000.0 / per_kernel[f"render_{m}"], 1) for m in WL.MODES},
