@@ -644,9 +644,13 @@ def run_in_ray_smoothing(shw, torch, dev):
             rows[name] = {"fetches_per_step": fetches, "ms": round(t, 3), "fps": round(1e3 / t, 1),
                           "gsamples_per_s": round(ns / (t * 1e-3) / 1e9, 2),
                           "gfetches_per_s": round(fetches * ns / (t * 1e-3) / 1e9, 1)}
+            if name.startswith("box") and P["step"] in (0.5, 1.0):
+                rows[name]["note"] = "lattice running sums: about 2 fetches per step done"
         out[m] = rows
     del cube
     return {"workload": P["name"], "views": f"yaw {list(P['yaws'])}, pitch {P['pitch']}; median view",
+            "fetches": "fetches_per_step is Section 6's count for the kernel (N for an N-box, "
+                       "3(N-1)/2+1 for an N-tap Gaussian); gfetches_per_s counts those",
             "compositing": f"opacity scale {P['opacity_scale']}, clip [{P['clip'][0]}, {P['clip'][1]}]",
             "modes": out}
 

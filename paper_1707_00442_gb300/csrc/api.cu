@@ -3,6 +3,7 @@
 // call returns an error without touching the GPU.
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include <cudaTypedefs.h>
@@ -296,6 +297,9 @@ shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_c
     if (p->smooth == SHW_SMOOTH_BOX) {
         a.smooth_n = p->smooth_arm;
         a.smooth_c0 = (float)(1.0 / (2.0 * p->smooth_arm + 1.0));
+        // a step of exactly 1 or 1/2 voxel puts the box's neighbours on the ray's own samples
+        if (p->smooth_arm > 0 && (p->step == 1.0f || p->step == 0.5f) && !getenv("SHW_BOX_DIRECT"))
+            a.box_lattice = p->step == 1.0f ? 1 : 2;
     } else if (p->smooth == SHW_SMOOTH_TAPS) {
         a.smooth_n = p->smooth_ntaps;
         a.smooth_c0 = p->smooth_c0;

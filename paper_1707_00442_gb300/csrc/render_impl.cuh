@@ -42,6 +42,7 @@ struct RenderArgs {
     int filter, alpha_thr;  // shw_filter; the alpha-threshold option of spectral / first-moment colouring
     float tmin, tmax, tinv; // the filter's thresholds; 1 / (tmax - tmin) for domain scaling
     int smooth;             // shw_smooth_kind of in-ray smoothing
+    int box_lattice;        // box smoothing with a step of exactly 1/box_lattice voxel (1, 2): running sums
     int smooth_n;           // box: neighbours on each side; taps: fetches on each side per axis
     float smooth_c0;        // box: 1 / (2 arm + 1); taps: weight of the value entering each axis pass
     float smooth_w[SHW_MAX_SMOOTH_TAPS];          // taps: weights
@@ -292,6 +293,63 @@ __device__ __forceinline__ void two_samples(const S &s, const S &s2, long long X
         c1 = ray_sample<CLAMP, SM, INTERP>(s, X, Y, Z, cc, a, U);
         c2 = ray_sample<CLAMP, SM, INTERP>(s2, X, Y, Z, cc2, a, U);
     }
+}
+
+// ---- in-ray box smoothing on the ray's own sample lattice ---------------------
+
+#ifndef SHW_BOX_RESUM
+#define SHW_BOX_RESUM 64  // the running sums are recomputed directly every this many samples of a class
+#endif
+
+// Box smoothing (Algorithm 8) when the step is exactly 1/M voxel: the neighbours of sample
+// k one voxel apart along the ray are the samples k +- i M of the same ray (P + j D, exact in
+// fixed point; M D equals the unit direction to 2^-32 voxel).  The box value of sample k is a
+// sum over the lattice class of k, kept as M running sums: sum(k) = sum(k - M) + r(k + arm M)
+// - r(k - (arm + 1) M), two fetches per sample instead of 2 arm + 1.  A sum is recomputed
+// directly every SHW_BOX_RESUM samples of its class (bounding rounding drift) and whenever it
+// is not finite (a NaN or infinite tap inside the window gives the direct definition's value).
+template <int M, int MODE, int INTERP, class S, class St>
+__device__ __forceinline__ void march_box_lattice(const S &s, const RenderArgs &a, St &st, const long long P[3],
+                                                  const long long D[3], int N, int &kdone)
+{
+    const int arm = a.smooth_n;
+    CellCache ca, cb, cd;  // leading, trailing and direct fetches: each walks the ray monotonically
+    auto raw = [&](int j, CellCache &cc) {
+        return sample<true, INTERP>(s, P[0] + (long long)j * D[0], P[1] + (long long)j * D[1],
+                                    P[2] + (long long)j * D[2], cc);
+    };
+    auto direct = [&](int k) {  // the definition's order: the sample, then the pairs +-i
+        float t = raw(k, cd);
+        for (int i = 1; i <= arm; ++i) {
+            t += raw(k + i * M, cd);
+            t += raw(k - i * M, cd);
+        }
+        return t;
+    };
+    float sum[M];
+    for (int k0 = 0; k0 < N; k0 += M) {
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+            const int k = k0 + c;
+            if (k >= N) break;
+            float t;
+            if (k0 == 0 || (k0 / M) % SHW_BOX_RESUM == 0) {
+                t = direct(k);
+            } else {
+                t = sum[c] + raw(k + arm * M, ca) - raw(k - (arm + 1) * M, cb);
+                if (!isfinite(t)) t = direct(k);
+            }
+            sum[c] = t;
+            float v = t * a.smooth_c0;
+            v = filter_value(isnan(v) ? a.lo : v, a);
+            v = isnan(v) ? a.lo : v;  // a NaN sample counts as DATAMIN
+            if (st.update(v, k)) {
+                kdone = k + 1;
+                return;
+            }
+        }
+    }
+    kdone = N;
 }
 
 // ---- transfer-function state per mode --------------------------------------
@@ -752,7 +810,17 @@ __device__ __forceinline__ void render_pixel(const S &s, const S &s2, const shw_
         CacheOf<S> cc, cc2;
         if constexpr (SM) {
             // smoothing: taps reach past the interior, so every sample fetches with clamping
-            march<true, MODE, INTERP, true>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, 0, N, done, r.U);
+            if constexpr (!two_cubes<MODE> && !S::kPair) {
+                if (a.box_lattice == 2) {
+                    march_box_lattice<2, MODE, INTERP>(s, a, st, r.P, r.D, N, done);
+                } else if (a.box_lattice == 1) {
+                    march_box_lattice<1, MODE, INTERP>(s, a, st, r.P, r.D, N, done);
+                } else {
+                    march<true, MODE, INTERP, true>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, 0, N, done, r.U);
+                }
+            } else {
+                march<true, MODE, INTERP, true>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, 0, N, done, r.U);
+            }
         } else {
         bool stop = march<true, MODE, INTERP>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, 0, ka, done);
         if (!stop) {

@@ -161,3 +161,27 @@ def test_smoothing_rejected_where_unsupported(m, ragged):
         m.render(to_dev(cube), cam, "mip", lut=lut, smooth="box", smooth_arm=17)
     assert e.value.status == 1
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("step", [0.5, 1.0])
+@pytest.mark.parametrize("mode", ["mip", "avg", "composite", "moment1"])
+def test_box_lattice_matches_direct(m, ragged, step, mode, monkeypatch):
+    """With a step of 1 or 1/2 voxel the box runs as running sums over the ray's own samples;
+    it agrees with the direct per-sample sums (SHW_BOX_DIRECT) to FP32 rounding."""
+    cube, c2 = ragged
+    cube = cube.copy()
+    cube.reshape(-1)[np.random.default_rng(4).integers(0, cube.size, 40)] = np.nan  # windows with NaN taps
+    cam = scene.orbit_camera(RAGGED_DIMS, 30, 20, 100, 75)
+    lut = to_dev(scene.linear_lut())
+    kw = dict(_kw(mode), step=step, smooth="box", smooth_arm=4)
+    lat = gpu_render(m, to_dev(cube), cam, mode, lut, **kw)
+    monkeypatch.setenv("SHW_BOX_DIRECT", "1")
+    dct = gpu_render(m, to_dev(cube), cam, mode, lut, **kw)
+    scale = 1.0 if mode == "composite" else (float(cube.shape[0]) if mode == "moment1" else
+                                              float(np.nanmax(cube) - np.nanmin(cube)))
+    if mode != "composite":  # (compositing's exit sample is a rounding decision: oracle check only)
+        assert np.array_equal(lat["nsamples"], dct["nsamples"])
+        assert np.abs(lat["rgba"] - dct["rgba"]).max() <= TOL_F32
+        assert np.nanmax(np.abs(lat["scalar"] - dct["scalar"])) <= TOL_F32 * scale
+    o = oracle.render(cube, cam, mode, lut=scene.linear_lut(), eps_pos=1e-6, eps_val=1e-4, **kw)
+    compare(lat, o, mode, scale=scale, max_fragile=0.05, what=f"lattice/{mode}/{step}")
