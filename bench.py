@@ -56,6 +56,16 @@ def load_peaks():
 
 # --------------------------------------------------------------------------- clocks
 
+def _pci_key(pci: str):
+    """(domain, bus, device, function) of a PCI id string, or the string itself."""
+    try:
+        dom, bus, rest = pci.strip().lower().split(":")
+        dev, fn = rest.split(".")
+        return (int(dom, 16), int(bus, 16), int(dev, 16), int(fn, 16))
+    except ValueError:
+        return pci
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle-reason samples taken while the timed region runs."""
     Q = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -69,9 +79,8 @@ class ClockSampler:
         self.thread = None
 
     def start(self):
+        # every GPU the tool lists; stop() keeps the rows of this one (by PCI bus id)
         cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
-        if self.bus_id:
-            cmd += ["-i", self.bus_id]
         try:
             self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
@@ -98,10 +107,12 @@ class ClockSampler:
             self.thread.join(timeout=2)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 10:
-                continue
+        rows = [[x.strip() for x in ln.split(",")] for ln in self.lines]
+        rows = [f for f in rows if len(f) >= 10]
+        if self.bus_id:  # this GPU's rows, the PCI ids compared field by field (domain widths differ)
+            mine = [f for f in rows if _pci_key(f[1]) == _pci_key(self.bus_id)]
+            rows = mine if mine else rows
+        for f in rows:
             try:
                 sm.append(float(f[2]))
                 mx.append(float(f[3]))
@@ -188,16 +199,25 @@ class Step:
         return per
 
 
+def pci_id(torch, dev):
+    """The device's PCI location as domain:bus:device.function (lower-case hex), or None.
+    Some PyTorch versions give the fields as numbers, others the whole string."""
+    try:
+        pr = torch.cuda.get_device_properties(dev)
+        bus = pr.pci_bus_id
+        if isinstance(bus, int):
+            return f"{getattr(pr, 'pci_domain_id', 0):04x}:{bus:02x}:{getattr(pr, 'pci_device_id', 0):02x}.0"
+        return str(bus).lower()
+    except Exception:  # noqa: BLE001 -- optional information
+        return None
+
+
 def bind_to_gpu_node(torch, dev):
     """Run this process on the host cores next to the GPU (its PCI device's local CPU list),
     so that the pinned input buffers are placed in the memory attached to them.  Best
     effort; returns the NUMA node, or None where the system does not say."""
     try:
-        pr = torch.cuda.get_device_properties(dev)
-        bus = pr.pci_bus_id
-        if isinstance(bus, int):  # numeric fields (domain, bus, device)
-            bus = f"{getattr(pr, 'pci_domain_id', 0):04x}:{bus:02x}:{getattr(pr, 'pci_device_id', 0):02x}.0"
-        bus = bus.lower()
+        bus = pci_id(torch, dev)
         base = f"/sys/bus/pci/devices/{bus}"
         if not os.path.exists(base) and len(bus.split(":")[0]) > 4:  # an 8-digit domain
             base = f"/sys/bus/pci/devices/{bus[len(bus.split(':')[0]) - 4:]}"
@@ -399,12 +419,7 @@ def run_ours(args):
         step.run()
     barrier()
 
-    bus = None
-    try:
-        bus = torch.cuda.get_device_properties(dev).pci_bus_id
-    except Exception:
-        bus = None
-    clocks = ClockSampler(bus_id=None if bus is None else str(bus))
+    clocks = ClockSampler(bus_id=pci_id(torch, dev))
     clocks.start()
 
     events = {}
