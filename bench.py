@@ -109,8 +109,10 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         rows = [[x.strip() for x in ln.split(",")] for ln in self.lines]
         rows = [f for f in rows if len(f) >= 10]
+        matched = False
         if self.bus_id:  # this GPU's rows, the PCI ids compared field by field (domain widths differ)
             mine = [f for f in rows if _pci_key(f[1]) == _pci_key(self.bus_id)]
+            matched = bool(mine)
             rows = mine if mine else rows
         for f in rows:
             try:
@@ -124,7 +126,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "gpu_pci": self.bus_id if matched else "all listed GPUs"}
 
 
 # --------------------------------------------------------------------------- workload
