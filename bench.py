@@ -105,6 +105,10 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
+        return self.summary()
+
+    def summary(self):
+        """Median SM clock, maximum clock and throttle reasons of this GPU's samples."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         rows = [[x.strip() for x in ln.split(",")] for ln in self.lines]

@@ -1,0 +1,64 @@
+"""bench.py's host-side arithmetic on CPU: the roofline record of each kernel (algorithmic
+bytes or flops over the measured time, against the measured peak), the PCI ids that pick
+the benchmarked GPU's clock samples, and the clock record itself."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+PEAKS = {"hbm_gbs": 6000.0}
+
+
+def test_smooth_roofline_counts_read_and_write():
+    nvox = 512 * 512 * 1024
+    r = bench.kernel_roofline("smooth", 1.0, nvox, {}, PEAKS, 2000.0)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["algorithmic_bytes"] == 8 * nvox
+    assert r["achieved"] == pytest.approx(8 * nvox / 1e-3 / 1e9, rel=1e-3)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6000.0, rel=1e-3)
+    # the zip form also reads the first cube's result and writes the 8-byte pair
+    z = bench.kernel_roofline("smooth2", 1.0, nvox, {}, PEAKS, 2000.0)
+    assert z["algorithmic_bytes"] == 16 * nvox
+
+
+def test_render_roofline_is_alu_flops_per_sample():
+    samples = {"mip": 10 ** 9, "composite": 10 ** 9, "ratio": 10 ** 9}
+    r = bench.kernel_roofline("render_mip", 2.0, 1, samples, PEAKS, 2000.0)
+    peak = 152 * 128 * 2 * 2000e6 / 1e12
+    assert r["bound"] == "alu" and r["peak"] == pytest.approx(peak, rel=1e-3)
+    assert r["achieved"] == pytest.approx(bench.ALG_FLOPS_PER_SAMPLE["mip"] * 1e9 / 2e-3 / 1e12, rel=1e-3)
+    assert r["gsamples_per_s"] == pytest.approx(500.0)
+    # the ratio samples two cubes per step, compositing does the most per sample
+    c = bench.kernel_roofline("render_composite", 2.0, 1, samples, PEAKS, 2000.0)
+    q = bench.kernel_roofline("render_ratio", 2.0, 1, samples, PEAKS, 2000.0)
+    assert c["achieved"] > r["achieved"] and q["achieved"] > r["achieved"]
+
+
+def test_pci_key_ignores_domain_width_and_case():
+    k = bench._pci_key
+    assert k("00000008:01:00.0") == k("0008:01:00.0") == k("0008:01:00.0 ")
+    assert k("0000:0A:00.0") == k("0000:0a:00.0")
+    assert k("0009:01:00.0") != k("0008:01:00.0")
+    assert k("not-a-bus-id") == "not-a-bus-id"
+
+
+def test_clock_record_keeps_this_gpus_rows():
+    cs = bench.ClockSampler(bus_id="0000:00:07.0")
+    cs.lines = [
+        "0, 00000000:00:07.0, 1980, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Active",
+        "1, 00000000:00:08.0, 1200, 2070, 300.0, 0x0, Active, Not Active, Not Active, Not Active",
+        "0, 00000000:00:07.0, 2070, 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+    ]
+    r = cs.summary()
+    assert r["samples"] == 2 and r["sm_mhz"] == pytest.approx(2025.0) and r["sm_max_mhz"] == 2070.0
+    assert r["reasons"] == ["sw_power_cap"] and r["gpu_pci"] == "0000:00:07.0"
+    other = bench.ClockSampler(bus_id="0000:00:09.0")
+    other.lines = cs.lines
+    r2 = other.summary()
+    assert r2["samples"] == 3 and r2["gpu_pci"] == "all listed GPUs"
