@@ -160,7 +160,7 @@ typedef enum {
     SHW_SMOOTH_NONE = 0,
     SHW_SMOOTH_BOX = 1, /* Algorithm 8: (v(p) + sum_{i=1..arm} v(p + i u) + v(p - i u)) / (2 arm + 1),
                            u the ray's unit direction (neighbours one voxel apart along the ray);
-                           2 arm + 1 fetches per sample.  With a step of exactly 1 or 1/2 voxel and a
+                           2 arm + 1 fetches per sample.  With a step of exactly 1/2 voxel and a
                            single cube the neighbours are the ray's own samples, and the box runs
                            as running sums (about 2 fetches per sample; equal to the direct sums to
                            FP32 rounding); the environment variable SHW_BOX_DIRECT selects the

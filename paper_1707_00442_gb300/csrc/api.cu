@@ -297,9 +297,9 @@ shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_c
     if (p->smooth == SHW_SMOOTH_BOX) {
         a.smooth_n = p->smooth_arm;
         a.smooth_c0 = (float)(1.0 / (2.0 * p->smooth_arm + 1.0));
-        // a step of exactly 1 or 1/2 voxel puts the box's neighbours on the ray's own samples
-        if (p->smooth_arm > 0 && (p->step == 1.0f || p->step == 0.5f) && !getenv("SHW_BOX_DIRECT"))
-            a.box_lattice = p->step == 1.0f ? 1 : 2;
+        // a step of exactly 1/2 voxel puts the box's neighbours on the ray's own samples
+        const bool single = p->mode != SHW_RATIO && p->mode != SHW_RATIO_MIP;
+        if (p->smooth_arm > 0 && p->step == 0.5f && single && !getenv("SHW_BOX_DIRECT")) a.box_lattice = 2;
     } else if (p->smooth == SHW_SMOOTH_TAPS) {
         a.smooth_n = p->smooth_ntaps;
         a.smooth_c0 = p->smooth_c0;
@@ -322,6 +322,9 @@ shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_c
     const shw_volume *v2 = (!pair && (p->mode == SHW_RATIO || p->mode == SHW_RATIO_MIP)) ? vol2 : nullptr;
     cudaStream_t st = as_stream(stream);
     if (pair) return render_pair(p->mode, p->interp, *vol, *cam, a, st);
+    if (a.box_lattice == 2)
+        return vol->storage == SHW_F32 ? render_smooth_lat_f32(p->mode, p->interp, *vol, *cam, a, st)
+                                       : render_smooth_lat_b16(p->mode, p->interp, *vol, *cam, a, st);
     if (p->smooth != SHW_SMOOTH_NONE)
         return vol->storage == SHW_F32 ? render_smooth_f32(p->mode, p->interp, *vol, v2, *cam, a, st)
                                        : render_smooth_b16(p->mode, p->interp, *vol, v2, *cam, a, st);

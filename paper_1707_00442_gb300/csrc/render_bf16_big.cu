@@ -11,7 +11,7 @@ shw_status render_bf16_big(int mode, int interp, const shw_volume &v, const shw_
                                   ceil_div(v.nx, kBrick), ceil_div(v.ny, kBrick)};
     SamplerBrick<__nv_bfloat16, long long> s2 = s;
     if (v2) s2.v = static_cast<const unsigned short *>(v2->data);
-    return launch_render_modes<false>(mode, interp, s, s2, cam, a, st);
+    return launch_render_modes<0>(mode, interp, s, s2, cam, a, st);
 }
 
 }  // namespace shw

@@ -14,7 +14,7 @@ shw_status render_f16(int mode, int interp, const shw_volume &v, const shw_volum
                             ceil_div(v.ny, kBrick)};
     SamplerBrick<__half, int> s2 = s;
     if (v2) s2.v = static_cast<const unsigned short *>(v2->data);
-    return launch_render_modes<false>(mode, interp, s, s2, cam, a, st);
+    return launch_render_modes<0>(mode, interp, s, s2, cam, a, st);
 }
 
 }  // namespace shw

@@ -12,7 +12,7 @@ shw_status render_f32(int mode, int interp, const shw_volume &v, const shw_volum
     SamplerF32<int> s{static_cast<const float *>(v.data), v.nx, v.ny, v.nz, v.nx, v.nx * v.ny};
     SamplerF32<int> s2 = s;
     if (v2) s2.v = static_cast<const float *>(v2->data);
-    return launch_render_modes<false>(mode, interp, s, s2, cam, a, st);
+    return launch_render_modes<0>(mode, interp, s, s2, cam, a, st);
 }
 
 }  // namespace shw

@@ -11,7 +11,7 @@ shw_status render_f32_big(int mode, int interp, const shw_volume &v, const shw_v
                             (long long)v.nx * v.ny};
     SamplerF32<long long> s2 = s;
     if (v2) s2.v = static_cast<const float *>(v2->data);
-    return launch_render_modes<false>(mode, interp, s, s2, cam, a, st);
+    return launch_render_modes<0>(mode, interp, s, s2, cam, a, st);
 }
 
 }  // namespace shw

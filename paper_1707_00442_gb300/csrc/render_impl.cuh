@@ -42,7 +42,7 @@ struct RenderArgs {
     int filter, alpha_thr;  // shw_filter; the alpha-threshold option of spectral / first-moment colouring
     float tmin, tmax, tinv; // the filter's thresholds; 1 / (tmax - tmin) for domain scaling
     int smooth;             // shw_smooth_kind of in-ray smoothing
-    int box_lattice;        // box smoothing with a step of exactly 1/box_lattice voxel (1, 2): running sums
+    int box_lattice;        // 2: box smoothing with a step of exactly 1/2 voxel runs as running sums
     int smooth_n;           // box: neighbours on each side; taps: fetches on each side per axis
     float smooth_c0;        // box: 1 / (2 arm + 1); taps: weight of the value entering each axis pass
     float smooth_w[SHW_MAX_SMOOTH_TAPS];          // taps: weights
@@ -301,7 +301,7 @@ __device__ __forceinline__ void two_samples(const S &s, const S &s2, long long X
 #define SHW_BOX_RESUM 64  // the running sums are recomputed directly every this many samples of a class
 #endif
 
-// Box smoothing (Algorithm 8) when the step is exactly 1/M voxel: the neighbours of sample
+// Box smoothing (Algorithm 8) when the step is exactly 1/M voxel (M = 2 is instanced): the neighbours of sample
 // k one voxel apart along the ray are the samples k +- i M of the same ray (P + j D, exact in
 // fixed point; M D equals the unit direction to 2^-32 voxel).  The box value of sample k is a
 // sum over the lattice class of k, kept as M running sums: sum(k) = sum(k - M) + r(k + arm M)
@@ -759,7 +759,9 @@ __device__ __forceinline__ void emit_ray(const RenderArgs &a, long long pix, int
 
 // One ray of Algorithm 1 with the transfer function MODE.  lut_c: the colour map in
 // shared memory (read per sample by COMPOSITE); a.lut: the same map in global memory.
-template <int MODE, int INTERP, class S, bool SM = false>
+// SMK: 0 no in-ray smoothing; 1 smoothing by direct fetches; 2 the box on the sample lattice
+// (a step of 1/2 voxel, single-cube modes).
+template <int MODE, int INTERP, class S, int SMK = 0>
 __device__ __forceinline__ void render_pixel(const S &s, const S &s2, const shw_camera &cam, const RenderArgs &a,
                                              const float4 *lut_c, int px, int py)
 {
@@ -808,19 +810,11 @@ __device__ __forceinline__ void render_pixel(const S &s, const S &s2, const shw_
             st.nearest = INTERP == SHW_NEAREST;
         }
         CacheOf<S> cc, cc2;
-        if constexpr (SM) {
+        if constexpr (SMK == 2) {
+            march_box_lattice<2, MODE, INTERP>(s, a, st, r.P, r.D, N, done);
+        } else if constexpr (SMK == 1) {
             // smoothing: taps reach past the interior, so every sample fetches with clamping
-            if constexpr (!two_cubes<MODE> && !S::kPair) {
-                if (a.box_lattice == 2) {
-                    march_box_lattice<2, MODE, INTERP>(s, a, st, r.P, r.D, N, done);
-                } else if (a.box_lattice == 1) {
-                    march_box_lattice<1, MODE, INTERP>(s, a, st, r.P, r.D, N, done);
-                } else {
-                    march<true, MODE, INTERP, true>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, 0, N, done, r.U);
-                }
-            } else {
-                march<true, MODE, INTERP, true>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, 0, N, done, r.U);
-            }
+            march<true, MODE, INTERP, true>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, 0, N, done, r.U);
         } else {
         bool stop = march<true, MODE, INTERP>(s, s2, a, st, cc, cc2, X, Y, Z, DX, DY, DZ, 0, ka, done);
         if (!stop) {
@@ -871,7 +865,7 @@ int sm_count();
 #ifndef SHW_RENDER_MINB
 #define SHW_RENDER_MINB 1  // minimum resident CTAs per SM the persistent kernel is compiled for
 #endif
-template <int MODE, int INTERP, class S, bool SM = false>
+template <int MODE, int INTERP, class S, int SMK = 0>
 __global__ void __launch_bounds__(kRenderThreads, SHW_RENDER_MINB)
     render_kernel_persistent(S s, S s2, shw_camera cam, RenderArgs a, unsigned *ctr, int nwarp_tiles)
 {
@@ -889,7 +883,7 @@ __global__ void __launch_bounds__(kRenderThreads, SHW_RENDER_MINB)
         const int ty = centre_out(rr, a.cty, a.tiles_y), tx = centre_out(cr, a.ctx, a.tiles_x);
         const int px = tx * tw + (wtx >= wty ? 0 : warp * wtx) + (lane & (wtx - 1));
         const int py = ty * th + (wtx >= wty ? warp * wty : 0) + (lane >> ws);
-        if (px < a.width && py < a.height) render_pixel<MODE, INTERP, S, SM>(s, s2, cam, a, a.lut, px, py);
+        if (px < a.width && py < a.height) render_pixel<MODE, INTERP, S, SMK>(s, s2, cam, a, a.lut, px, py);
     }
 }
 
@@ -930,8 +924,8 @@ inline void project_centre(const shw_camera &c, int nx, int ny, int nz, float &p
 }
 
 // Host-side launch for one storage type (instantiated per storage in its own TU).
-// SM: the in-ray smoothing instances (persistent form only).
-template <bool SM, class S>
+// SMK > 0: the in-ray smoothing instances (persistent form only; see render_pixel).
+template <int SMK, class S>
 shw_status launch_render_modes(int mode, int interp, const S &s, const S &s2, const shw_camera &cam,
                                const RenderArgs &a0, cudaStream_t st)
 {
@@ -955,12 +949,12 @@ shw_status launch_render_modes(int mode, int interp, const S &s, const S &s2, co
         const long long g = std::min<long long>((long long)per_sm * nsm, tiles);
         kern<<<(unsigned)std::max<long long>(g, 1), block, 0, st>>>(s, s2, cam, a, ctr, nwarp_tiles);
     };
-    if (SM && (ctr == nullptr || nsm <= 0)) return SHW_ECUDA;
+    if (SMK > 0 && (ctr == nullptr || nsm <= 0)) return SHW_ECUDA;
 #define SHW_LAUNCH(M, I)                                                       \
     do {                                                                       \
-        if constexpr (SM)                                                      \
-            persistent(render_kernel_persistent<M, I, S, true>,                \
-                       resident_per_sm<render_kernel_persistent<M, I, S, true>>()); \
+        if constexpr (SMK > 0)                                                 \
+            persistent(render_kernel_persistent<M, I, S, SMK>,                 \
+                       resident_per_sm<render_kernel_persistent<M, I, S, SMK>>()); \
         else if (ctr != nullptr && nsm > 0)                                    \
             persistent(render_kernel_persistent<M, I, S>,                      \
                        resident_per_sm<render_kernel_persistent<M, I, S>>());  \
@@ -977,6 +971,20 @@ shw_status launch_render_modes(int mode, int interp, const S &s, const S &s2, co
         switch (mode) {
             SHW_CASE(SHW_RATIO)
             SHW_CASE(SHW_RATIO_MIP)
+        default:
+            return SHW_EUNSUPPORTED;
+        }
+    } else if constexpr (SMK == 2) {
+        // the lattice box: single-cube modes
+        switch (mode) {
+            SHW_CASE(SHW_MIP)
+            SHW_CASE(SHW_AVG)
+            SHW_CASE(SHW_COMPOSITE)
+            SHW_CASE(SHW_SPECTRAL)
+            SHW_CASE(SHW_MOMENT1)
+            SHW_CASE(SHW_COMPOSITE_SPECTRAL)
+            SHW_CASE(SHW_MIP_RGB)
+            SHW_CASE(SHW_COMPOSITE_RGB)
         default:
             return SHW_EUNSUPPORTED;
         }
@@ -1021,11 +1029,16 @@ shw_status render_f32_pair(int mode, int interp, const shw_volume &v, const shw_
                            cudaStream_t st);
 shw_status render_pair(int mode, int interp, const shw_volume &v, const shw_camera &cam, const RenderArgs &a,
                        cudaStream_t st);
-// in-ray smoothing (a.smooth != SHW_SMOOTH_NONE), any storage
+// in-ray smoothing (a.smooth != SHW_SMOOTH_NONE), any storage; the _lat forms run the box on
+// the sample lattice (a.box_lattice == 2)
 shw_status render_smooth_f32(int mode, int interp, const shw_volume &v, const shw_volume *v2,
                              const shw_camera &cam, const RenderArgs &a, cudaStream_t st);
 shw_status render_smooth_b16(int mode, int interp, const shw_volume &v, const shw_volume *v2,
                              const shw_camera &cam, const RenderArgs &a, cudaStream_t st);
+shw_status render_smooth_lat_f32(int mode, int interp, const shw_volume &v, const shw_camera &cam,
+                                 const RenderArgs &a, cudaStream_t st);
+shw_status render_smooth_lat_b16(int mode, int interp, const shw_volume &v, const shw_camera &cam,
+                                 const RenderArgs &a, cudaStream_t st);
 shw_status render_bf16(int mode, int interp, const shw_volume &v, const shw_volume *v2, const shw_camera &cam,
                        const RenderArgs &a, cudaStream_t st);
 shw_status render_f16(int mode, int interp, const shw_volume &v, const shw_volume *v2, const shw_camera &cam,

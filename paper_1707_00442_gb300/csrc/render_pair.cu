@@ -11,10 +11,10 @@ shw_status render_f32_pair(int mode, int interp, const shw_volume &v, const shw_
     const long long nvox = (long long)v.nx * v.ny * v.nz;
     if (nvox < (1LL << 31)) {
         SamplerF32Pair<int> s{p, v.nx, v.ny, v.nz, v.nx, v.nx * v.ny};
-        return launch_render_modes<false>(mode, interp, s, s, cam, a, st);
+        return launch_render_modes<0>(mode, interp, s, s, cam, a, st);
     }
     SamplerF32Pair<long long> s{p, v.nx, v.ny, v.nz, (long long)v.nx, (long long)v.nx * v.ny};
-    return launch_render_modes<false>(mode, interp, s, s, cam, a, st);
+    return launch_render_modes<0>(mode, interp, s, s, cam, a, st);
 }
 
 template <typename T>
@@ -26,10 +26,10 @@ static shw_status render_bricks_pair(int mode, int interp, const shw_volume &v, 
     const long long elems = (long long)nbx * nby * ceil_div(v.nz, kBrick) * kBrickElems;
     if (elems < (1LL << 31)) {  // 32-bit element offsets
         SamplerBrickPair<T, int> s{p, v.nx, v.ny, v.nz, nbx, nby};
-        return launch_render_modes<false>(mode, interp, s, s, cam, a, st);
+        return launch_render_modes<0>(mode, interp, s, s, cam, a, st);
     }
     SamplerBrickPair<T, long long> s{p, v.nx, v.ny, v.nz, nbx, nby};
-    return launch_render_modes<false>(mode, interp, s, s, cam, a, st);
+    return launch_render_modes<0>(mode, interp, s, s, cam, a, st);
 }
 
 shw_status render_pair(int mode, int interp, const shw_volume &v, const shw_camera &cam, const RenderArgs &a,

@@ -12,7 +12,7 @@ static shw_status smooth_bricks(int mode, int interp, const shw_volume &v, const
                       ceil_div(v.ny, kBrick)};
     SamplerBrick<T> s2 = s;
     if (v2) s2.v = static_cast<const unsigned short *>(v2->data);
-    return launch_render_modes<true>(mode, interp, s, s2, cam, a, st);
+    return launch_render_modes<1>(mode, interp, s, s2, cam, a, st);
 }
 
 shw_status render_smooth_b16(int mode, int interp, const shw_volume &v, const shw_volume *v2,

@@ -12,13 +12,13 @@ shw_status render_smooth_f32(int mode, int interp, const shw_volume &v, const sh
         SamplerF32<int> s{static_cast<const float *>(v.data), v.nx, v.ny, v.nz, v.nx, v.nx * v.ny};
         SamplerF32<int> s2 = s;
         if (v2) s2.v = static_cast<const float *>(v2->data);
-        return launch_render_modes<true>(mode, interp, s, s2, cam, a, st);
+        return launch_render_modes<1>(mode, interp, s, s2, cam, a, st);
     }
     SamplerF32<long long> s{static_cast<const float *>(v.data), v.nx, v.ny, v.nz, (long long)v.nx,
                             (long long)v.nx * v.ny};
     SamplerF32<long long> s2 = s;
     if (v2) s2.v = static_cast<const float *>(v2->data);
-    return launch_render_modes<true>(mode, interp, s, s2, cam, a, st);
+    return launch_render_modes<1>(mode, interp, s, s2, cam, a, st);
 }
 
 }  // namespace shw

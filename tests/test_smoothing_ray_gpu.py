@@ -166,8 +166,9 @@ def test_smoothing_rejected_where_unsupported(m, ragged):
 @pytest.mark.parametrize("step", [0.5, 1.0])
 @pytest.mark.parametrize("mode", ["mip", "avg", "composite", "moment1"])
 def test_box_lattice_matches_direct(m, ragged, step, mode, monkeypatch):
-    """With a step of 1 or 1/2 voxel the box runs as running sums over the ray's own samples;
-    it agrees with the direct per-sample sums (SHW_BOX_DIRECT) to FP32 rounding."""
+    """With a step of 1/2 voxel the box runs as running sums over the ray's own samples; it
+    agrees with the direct per-sample sums (SHW_BOX_DIRECT) to FP32 rounding.  (A step of 1
+    takes the direct sums either way.)"""
     cube, c2 = ragged
     cube = cube.copy()
     cube.reshape(-1)[np.random.default_rng(4).integers(0, cube.size, 40)] = np.nan  # windows with NaN taps
