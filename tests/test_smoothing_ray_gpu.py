@@ -186,3 +186,39 @@ def test_box_lattice_matches_direct(m, ragged, step, mode, monkeypatch):
         assert np.nanmax(np.abs(lat["scalar"] - dct["scalar"])) <= TOL_F32 * scale
     o = oracle.render(cube, cam, mode, lut=scene.linear_lut(), eps_pos=1e-6, eps_val=1e-4, **kw)
     compare(lat, o, mode, scale=scale, max_fragile=0.05, what=f"lattice/{mode}/{step}")
+
+
+def test_smoothing_edge_cases(m):
+    """Degenerate inputs with in-ray smoothing: a single voxel (every tap clamps onto it), a
+    one-channel slab, the eye inside the cube, a step longer than the cube (N = 0), and the
+    line ratio of a single voxel on the pair storage."""
+    lut = scene.linear_lut()
+    kws = [dict(smooth="box", smooth_arm=3), dict(smooth="taps", smooth_taps=_taps("taps9"))]
+    one = np.array([[[2.5]]], np.float32)
+    cam = scene.orbit_camera((1, 1, 1), 10, 10, 17, 13)
+    for sm in kws:
+        g = gpu_render(m, to_dev(one), cam, "mip", to_dev(lut), **sm)
+        o = oracle.render(one, cam, "mip", lut=lut, eps_pos=1e-6, **sm)
+        compare(g, o, "mip", scale=1.0, what=f"1 voxel/{sm['smooth']}")
+    slab = scene.tiny_cube(dims=(40, 30, 1), n_sources=1)
+    cam = scene.orbit_camera((40, 30, 1), 20, 10, 24, 18)
+    for sm in kws:
+        g = gpu_render(m, to_dev(slab), cam, "avg", to_dev(lut), **sm)
+        o = oracle.render(slab, cam, "avg", lut=lut, eps_pos=1e-6, **sm)
+        compare(g, o, "avg", scale=float(slab.max() - slab.min()), max_fragile=1.0, what=f"slab/{sm['smooth']}")
+    cube = scene.tiny_cube(dims=(48, 48, 48), n_sources=2)
+    c = scene.orbit_camera((48, 48, 48), 20, 10, 64, 48, dist_scale=0.1)
+    for sm in kws:
+        for mode in ("mip", "composite"):
+            g = gpu_render(m, to_dev(cube), c, mode, to_dev(lut), opacity_scale=0.05, **sm)
+            o = oracle.render(cube, c, mode, lut=lut, opacity_scale=0.05, eps_pos=1e-6, eps_val=1e-4, **sm)
+            compare(g, o, mode, scale=1.0 if mode == "composite" else float(cube.max() - cube.min()),
+                    max_fragile=0.05, what=f"eye inside/{mode}/{sm['smooth']}")
+        g = gpu_render(m, to_dev(cube), c, "mip", to_dev(lut), step=100.0, **sm)
+        o = oracle.render(cube, c, "mip", lut=lut, step=100.0, eps_pos=1e-6, **sm)
+        compare(g, o, "mip", scale=float(cube.max() - cube.min()), max_fragile=1.0, what=f"long step/{sm['smooth']}")
+    pr = to_dev(np.stack([np.full((1, 1, 1), 2.0, np.float32), np.full((1, 1, 1), 1.0, np.float32)], axis=-1))
+    g = gpu_render(m, pr, scene.orbit_camera((1, 1, 1), 10, 10, 9, 7), "ratio", to_dev(scene.ratio_lut()),
+                   lo=0.0, hi=1.0, ratio_floor=0.5)
+    hit = g["nsamples"] > 0
+    assert hit.any() and np.all(g["scalar"][hit] == np.float32(0.5))
