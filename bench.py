@@ -503,8 +503,8 @@ def run_ours(args):
     return res, samples_per
 
 
-# ncu dram bytes (read + write) per launch of the dominant kernel, from one capture of the
-# current build (profiles/survey_step_dram_traffic.md); reset to absent when the kernel changes
+# ncu DRAM bytes (read + write) per launch of each step kernel, from one capture of these
+# kernels on one GB300 at the full size; an entry is removed when its kernel changes
 TRAFFIC_PER_LAUNCH: dict = {
     "smooth": 1273792768 + 1034413824, "smooth2": 2353712128 + 2102823680,
     "render_mip": 1522822912 + 23123712, "render_avg": 1588480768 + 22132992,
