@@ -329,6 +329,9 @@ static size_t smooth_tma_smem()
     return (size_t)(kSmStages * (kSmTY + 2 * R) * kSmBW + 2 * (kSmTY + 2 * R) * kSmTX) * 4;
 }
 
+#ifndef SHW_SMOOTH_WAVES
+#define SHW_SMOOTH_WAVES 1  // 1: the z chunk is chosen against the resident-CTA waves
+#endif
 #ifndef SHW_SMOOTH_ZC
 #define SHW_SMOOTH_ZC 128  // largest z chunk of one CTA (planes)
 #endif
@@ -341,6 +344,30 @@ static int smooth_zchunk(int nx, int ny, int nz, int r)
     return zc;
 }
 
+// The TMA kernel's z chunk: each chunk re-reads 2r halo planes, and CTAs run in waves of
+// `resident` (CTAs per SM x SMs), so pick the number of chunks that minimises
+// waves x (planes per chunk + 2r).  resident <= 0: the plain rule above.
+static int smooth_zchunk_waves(int nx, int ny, int nz, int r, long long resident)
+{
+    if (resident <= 0) return smooth_zchunk(nx, ny, nz, r);
+    const long long tiles = (long long)ceil_div(nx, 32) * ceil_div(ny, 32);
+    const int zmin = (4 * r > 16) ? 4 * r : 16;
+    long long best = -1;
+    int best_zc = nz;
+    for (int nch = 1; nch <= nz; ++nch) {
+        const int zc = ceil_div(nz, nch);
+        if (zc < zmin && nch > 1) break;
+        const long long ctas = tiles * ceil_div(nz, zc);
+        const long long waves = (ctas + resident - 1) / resident;
+        const long long cost = waves * (zc + 2LL * r);
+        if (best < 0 || cost < best) {
+            best = cost;
+            best_zc = zc;
+        }
+    }
+    return best_zc;
+}
+
 template <int R, bool ZIP>
 static bool launch_smooth_tma(const float *in, float *out, int nx, int ny, int nz, const SmoothWeights &w,
                               const float *first, cudaStream_t st)
@@ -349,10 +376,26 @@ static bool launch_smooth_tma(const float *in, float *out, int nx, int ny, int n
     if (!encode_tmap_3d_f32(&map, in, nx, ny, nz, kSmBW, kSmTY + 2 * R)) return false;
     unsigned *err = device_error_word();
     const size_t smem = smooth_tma_smem<R>();
-    const int zc = smooth_zchunk(nx, ny, nz, R);
-    const dim3 grid((unsigned)ceil_div(nx, kSmTX), (unsigned)ceil_div(ny, kSmTY), (unsigned)ceil_div(nz, zc));
     if (smem > 48 * 1024)
         cudaFuncSetAttribute(smooth_tma_kernel<R, ZIP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static int per_sm = -1;  // resident CTAs per SM of this instance, queried once
+    if (per_sm < 0) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, smooth_tma_kernel<R, ZIP>, kSmThreads, smem) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            n = 0;
+        }
+        per_sm = n;
+    }
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        nsm = 0;
+    }
+    const int zc = SHW_SMOOTH_WAVES ? smooth_zchunk_waves(nx, ny, nz, R, (long long)per_sm * nsm)
+                                    : smooth_zchunk(nx, ny, nz, R);
+    const dim3 grid((unsigned)ceil_div(nx, kSmTX), (unsigned)ceil_div(ny, kSmTY), (unsigned)ceil_div(nz, zc));
     smooth_tma_kernel<R, ZIP><<<grid, kSmThreads, smem, st>>>(map, out, nx, ny, nz, zc, w, err, first);
     return true;
 }
