@@ -339,8 +339,10 @@ class E2EPipeline:
 
 # --------------------------------------------------------------------------- roofline
 
-def kernel_roofline(name, t_ms, nvox, samples_per, peaks, sm_mhz):
-    """Algorithmic work per launch / measured duration, against the bound of that kernel."""
+def kernel_roofline(name, t_ms, nvox, samples_per, peaks, sm_mhz, image_bytes=0):
+    """Algorithmic work per launch / measured duration, against the bound of that kernel.
+    Renders also report their HBM fraction (cube bytes read once + image written, over the
+    time, against the measured copy rate) and, where a capture exists, the ncu DRAM fraction."""
     hbm = float(peaks["hbm_gbs"])
     if name.startswith("smooth"):
         # read the cube once, write the result once; the second smoothing also reads the
@@ -354,9 +356,20 @@ def kernel_roofline(name, t_ms, nvox, samples_per, peaks, sm_mhz):
     flops = ALG_FLOPS_PER_SAMPLE[mode] * ns
     peak = FP32_LANES_PER_SM * 2 * SMS * float(sm_mhz) * 1e6 / 1e12  # TFLOP/s (FMA = 2)
     ach = flops / (t_ms * 1e-3) / 1e12
-    return {"bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-            "frac": round(ach / peak, 4), "samples": ns,
-            "gsamples_per_s": round(ns / (t_ms * 1e-3) / 1e9, 2)}
+    loaded = peaks.get("clocks_under_load", {}).get("sm_mhz_median")
+    cube_bytes = (8 if mode == "ratio" else 4) * nvox  # the ratio reads both cubes
+    alg_bytes = cube_bytes + image_bytes
+    rec = {"bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+           "frac": round(ach / peak, 4), "samples": ns,
+           "gsamples_per_s": round(ns / (t_ms * 1e-3) / 1e9, 2),
+           "hbm_frac": round(alg_bytes / (t_ms * 1e-3) / 1e9 / hbm, 4), "algorithmic_bytes": alg_bytes}
+    if loaded:  # the ALU fraction against the loaded median clock recorded with the peaks
+        peak_l = FP32_LANES_PER_SM * 2 * SMS * float(loaded) * 1e6 / 1e12
+        rec["frac_at_loaded_median_clock"] = round(ach / peak_l, 4)
+    traffic = TRAFFIC_PER_LAUNCH.get(name)
+    if traffic:
+        rec["dram_frac_ncu_bytes"] = round(traffic / (t_ms * 1e-3) / 1e9 / hbm, 4)
+    return rec
 
 
 SMS = 152
@@ -462,7 +475,8 @@ def run_ours(args):
 
     peaks, peaks_src = load_peaks()
     sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1485.0
-    roof = {k: kernel_roofline(k, t, nvox, samples_per, peaks, sm_mhz) for k, t in per_kernel.items()}
+    img_bytes = step.cam.width * step.cam.height * 16  # the RGBA float32 image each render writes
+    roof = {k: kernel_roofline(k, t, nvox, samples_per, peaks, sm_mhz, img_bytes) for k, t in per_kernel.items()}
     total_by_kind = {k: per_kernel[k] for k in per_kernel}
     dom = max(total_by_kind, key=total_by_kind.get)
 

@@ -37,6 +37,10 @@ def test_render_roofline_is_alu_flops_per_sample():
     c = bench.kernel_roofline("render_composite", 2.0, 1, samples, PEAKS, 2000.0)
     q = bench.kernel_roofline("render_ratio", 2.0, 1, samples, PEAKS, 2000.0)
     assert c["achieved"] > r["achieved"] and q["achieved"] > r["achieved"]
+    # HBM fraction: the cube once (both cubes for the ratio) plus the image
+    h = bench.kernel_roofline("render_ratio", 2.0, 10 ** 9, samples, PEAKS, 2000.0, image_bytes=160)
+    assert h["algorithmic_bytes"] == 8 * 10 ** 9 + 160
+    assert h["hbm_frac"] == pytest.approx((8e9 + 160) / 2e-3 / 1e9 / 6000.0, rel=1e-3)
 
 
 def test_pci_key_ignores_domain_width_and_case():
