@@ -113,3 +113,41 @@ def test_survey_step_ratio_on_pair_storage(m, survey, pixels):
     scale = float(o["scalar"].max() - o["scalar"].min()) or 1.0
     st = compare(g, o, "ratio", scale=scale, pixels=pixels, what="survey/ratio-pair")
     print("ratio-pair", st)
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_survey_bricks_error_vs_fp64(m, survey, pixels, storage):
+    """The reduced-precision path at full size: every mode rendered from 16-bit bricks of the
+    smoothed survey cubes (the ratio from pair bricks), against the FP64 oracle on the float32
+    smoothed cubes at sampled pixels.  Prints max-abs and RMS error per mode; the scalar of the
+    single-cube modes within 2e-3 of the data range (near-ties at that margin skipped)."""
+    from parity import TOL_REDUCED
+    cube, c2 = survey[0], survey[1]
+    sig, r = W.SURVEY["sigma"], W.SURVEY["radius"]
+    s1 = m.smooth(to_dev(cube), sig, r)
+    pair = m.smooth_zip(to_dev(c2), s1, sig, r)
+    b1, bp = m.pack_bricks(s1, storage), m.pack_bricks(pair, storage)
+    m.sync_status()
+    s1h = s1.cpu().numpy().astype(np.float64)
+    s2h = pair[..., 1].cpu().numpy().astype(np.float64)
+    del s1, pair
+    cam = W.survey_camera()
+    rng_ = float(s1h.max() - s1h.min())
+    for mode in W.MODES:
+        lut = scene.ratio_lut() if mode == "ratio" else scene.linear_lut()
+        kw = dict(W.MODE_PARAMS[mode])
+        out = m.render(bp if mode == "ratio" else b1, cam, mode, lut=to_dev(lut), step=W.SURVEY["step"], **kw)
+        m.sync_status()
+        g = {k: v.cpu().numpy() for k, v in out.items()}
+        scale = 1.0 if mode == "composite" else rng_
+        o = oracle.render(s1h, cam, mode, lut=lut, cube2=s2h if mode == "ratio" else None, pixels=pixels,
+                          step=W.SURVEY["step"], eps_pos=1e-6, eps_val=TOL_REDUCED * scale, **kw)
+        flat = lambda a: a.reshape(-1, *a.shape[2:])[pixels]  # noqa: E731
+        ok = o["nsamples"] > 0
+        es = np.abs(flat(g["scalar"]).astype(np.float64) - o["scalar"])[ok]
+        er = np.abs(flat(g["rgba"]).astype(np.float64) - o["rgba"])[ok]
+        print(f"{storage}/{mode}: scalar max {es.max():.3e} rms {np.sqrt((es ** 2).mean()):.3e} "
+              f"(range {scale:.3g}); rgba max {er.max():.3e} rms {np.sqrt((er ** 2).mean()):.3e}")
+        if mode != "ratio":
+            steady = ok & (o["fragile"] == 0)
+            assert np.abs(flat(g["scalar"]).astype(np.float64) - o["scalar"])[steady].max() <= TOL_REDUCED * scale
