@@ -236,11 +236,14 @@ shw_status shw_pack_bricks(const float *in, int32_t nx, int32_t ny, int32_t nz, 
 
 /* Render one image.  vol2: the second cube for SHW_RATIO / SHW_RATIO_MIP (same dims and
  * storage), else NULL; NULL also when vol holds both cubes as SHW_F32_PAIR.  Outputs (device, any may be NULL except out_rgba):
- *   out_rgba   [H][W][4] float32: MIP/AVG/RATIO: colourMap(v_hat(result));
+ *   out_rgba   [H][W][4] float32: MIP/AVG/RATIO/RATIO_MIP: colourMap(v_hat(result));
  *              SPECTRAL: (colourMap_rgb(t_z), v_hat(max)), t_z = (z_max + 1/2)/nz;
- *              COMPOSITE: premultiplied (C_r, C_g, C_b, 1 - T).
- *   out_scalar [H][W] float32: the maximum / mean / ratio maximum / 1 - T.
- *   out_index  [H][W] int32: channel round(z) of the maximum (MIP, SPECTRAL, RATIO); -1 otherwise.
+ *              MOMENT1, MIP_RGB: as described with their modes;
+ *              COMPOSITE and its coloured forms: premultiplied (C_r, C_g, C_b, 1 - T).
+ *   out_scalar [H][W] float32: the maximum / mean / ratio maximum / 1 - T / first moment /
+ *              max2 / max1 (RATIO_MIP; DATAMIN where max1 fails the floor).
+ *   out_index  [H][W] int32: channel round(z) of the maximum (MIP, SPECTRAL, RATIO, MIP_RGB) or of
+ *              the first moment (MOMENT1, -1 with no weight); -1 otherwise.
  *   out_nsamples [H][W] int32: samples the ray processed.
  * A ray that misses the box (or has N = 0) writes zeros and index -1.
  * ckpt: COMPOSITE only, device buffer of ckpt_bytes >= shw_ckpt_bytes(...), or NULL:
