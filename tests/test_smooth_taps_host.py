@@ -1,6 +1,7 @@
-"""The binding's tap helpers for in-ray smoothing (host logic, no GPU): the linear-sampling
-fold reproduces the offsets and coefficients Algorithm 9 prints, and the N-tap binomial
-filters cost Section 6's 3(N-1)/2 + 1 fetches per step."""
+"""The library's tap tables for in-ray smoothing, called through the C ABI on the host (no
+GPU): the linear-sampling fold reproduces the offsets and coefficients Algorithm 9 prints,
+and the N-tap binomial filters cost Section 6's 3(N-1)/2 + 1 fetches per step."""
+import ctypes as C
 import json
 import math
 import os
@@ -8,6 +9,12 @@ import os
 import pytest
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built_library():
+    from paper_1707_00442_gb300 import build
+    build.build()
 
 
 def test_algorithm9_constants():
@@ -45,3 +52,23 @@ def test_fold_at_integer_points_is_the_kernel():
     i = 20
     folded = c0 * g[i] + sum(wj * (np.interp(i + o, x, g) + np.interp(i - o, x, g)) for o, wj in zip(off, wt))
     assert folded == pytest.approx(float(np.dot(w, g[i - 5:i + 6])), abs=1e-12)
+
+
+def test_tap_tables_through_the_abi():
+    """The raw C calls: Algorithm 9's printed kernel, and the errors the header states."""
+    from paper_1707_00442_gb300 import _lib
+    L = _lib.lib()
+    c0, nf = C.c_double(), C.c_int32()
+    offs, wts = (C.c_double * 4)(), (C.c_double * 4)()
+    assert L.shw_binomial_taps(9, 2, C.byref(c0), offs, wts, 4, C.byref(nf)) == _lib.SHW_OK
+    g = json.load(open(os.path.join(GOLD, "alg9_ninetap.json")))
+    tol = 0.6 * 10.0 ** -g["printed_decimals"]
+    assert nf.value == 2 and abs(c0.value - g["coeff_0"]) <= tol
+    assert abs(offs[0] - g["offset_1"]) <= tol and abs(offs[1] - g["offset_2"]) <= tol
+    assert abs(wts[0] - g["coeff_1"]) <= tol and abs(wts[1] - g["coeff_2"]) <= tol
+    # too few output slots, an even tap count, an asymmetric kernel, a row beyond 62
+    assert L.shw_binomial_taps(13, 0, C.byref(c0), offs, wts, 2, C.byref(nf)) == _lib.SHW_ENOMEM
+    assert L.shw_binomial_taps(8, 0, C.byref(c0), offs, wts, 4, C.byref(nf)) == _lib.SHW_EINVAL
+    w = (C.c_double * 3)(0.2, 0.5, 0.3)
+    assert L.shw_linear_sampling_taps(w, 1, C.byref(c0), offs, wts, 4, C.byref(nf)) == _lib.SHW_EINVAL
+    assert L.shw_binomial_taps(63, 1, C.byref(c0), offs, wts, 4, C.byref(nf)) == _lib.SHW_EUNSUPPORTED
