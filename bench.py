@@ -374,7 +374,7 @@ def kernel_roofline(name, t_ms, nvox, samples_per, peaks, sm_mhz, image_bytes=0)
 
 SMS = 152
 FP32_LANES_PER_SM = 128
-# FP32 flops the method needs per trilinear sample (see the design notes): 3 fraction weights,
+# FP32 flops the method needs per trilinear sample: 3 fraction weights,
 # 7 lerps (sub + FMA = 3 flops), plus the transfer function's own arithmetic.
 _TRI = 3 + 7 * 3
 ALG_FLOPS_PER_SAMPLE = {"mip": _TRI + 1, "spectral": _TRI + 1, "avg": _TRI + 4,

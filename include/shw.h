@@ -48,7 +48,7 @@
 extern "C" {
 #endif
 
-#define SHW_ABI_VERSION 3
+#define SHW_ABI_VERSION 4
 #define SHW_LUT_SIZE 256
 #define SHW_MAX_SMOOTH_RADIUS 16
 #define SHW_MAX_SMOOTH_ARM 16   /* in-ray box smoothing: neighbours on each side */
@@ -163,7 +163,7 @@ typedef enum {
                            2 arm + 1 fetches per sample.  With a step of exactly 1/2 voxel and a
                            single cube the neighbours are the ray's own samples, and the box runs
                            as running sums (about 2 fetches per sample; equal to the direct sums to
-                           FP32 rounding); the environment variable SHW_BOX_DIRECT selects the
+                           FP32 rounding); SHW_DEBUG_BOX_DIRECT (shw_set_debug_flags) selects the
                            direct fetches */
     SHW_SMOOTH_TAPS = 2 /* Algorithm 9 once per data axis e = x, then y, then z, each pass starting from
                            the previous pass's value (the raw sample for x):
@@ -216,6 +216,28 @@ shw_status shw_smooth_weights(const float *in, float *out, int32_t nx, int32_t n
 shw_status shw_smooth_zip(const float *in, const float *first, float *out_pair, int32_t nx, int32_t ny,
                           int32_t nz, float sigma, int32_t radius, void *stream);
 
+/* ---- fetch tables of in-ray tap smoothing (Section 4.2, Algorithm 9) ------ */
+
+/* Fold a symmetric 1-D kernel into the fetches of SHW_SMOOTH_TAPS by linear sampling
+ * (Section 4.2, the trick behind Algorithm 9's 9-tap kernel): the centre keeps w[r]; taps
+ * a and a+1 (a = 1, 3, 5, ...) become one interpolated fetch of weight w[r+a] + w[r+a+1]
+ * at offset (a w[r+a] + (a+1) w[r+a+1]) / (w[r+a] + w[r+a+1]) (a lone last tap keeps its
+ * own offset and weight).  w_host: host, 2*radius+1 finite values, w[r+k] == w[r-k];
+ * 0 <= radius <= 64.  Outputs (host): *c0, offsets[j], weights[j] for j < *nfetch =
+ * ceil(radius/2); capacity = slots in offsets and weights (SHW_ENOMEM if too few).
+ * Computed in double precision on the host; no GPU is needed. */
+shw_status shw_linear_sampling_taps(const double *w_host, int32_t radius, double *c0, double *offsets,
+                                    double *weights, int32_t capacity, int32_t *nfetch);
+
+/* The N-tap binomial filter of Section 4.2 folded as above: b_n = [1, 1] convolved with
+ * itself n = ntaps - 1 + 2*drop times (Pascal's row n), without its `drop` outer taps on
+ * each side, renormalised to sum 1.  ntaps odd >= 1, drop >= 0, n <= 62
+ * (SHW_EUNSUPPORTED beyond).  ntaps = 5, 9, 13 with drop = 0 are b_4, b_8, b_12;
+ * ntaps = 9, drop = 2 gives the offsets 1.3846153846, 3.2307692308 and coefficients
+ * 0.2270270270, 0.3162162162, 0.0702702703 that Algorithm 9 prints.  Host only. */
+shw_status shw_binomial_taps(int32_t ntaps, int32_t drop, double *c0, double *offsets, double *weights,
+                             int32_t capacity, int32_t *nfetch);
+
 /* ---- reduced-precision brick storage -------------------------------------- */
 
 /* Bytes of the brick buffer for a cube of these dims: ceil(n/32) bricks per axis,
@@ -247,7 +269,13 @@ shw_status shw_pack_bricks(const float *in, int32_t nx, int32_t ny, int32_t nz, 
  *   out_nsamples [H][W] int32: samples the ray processed.
  * A ray that misses the box (or has N = 0) writes zeros and index -1.
  * ckpt: COMPOSITE only, device buffer of ckpt_bytes >= shw_ckpt_bytes(...), or NULL:
- * the transmittance every ckpt_interval samples, read by shw_render_backward. */
+ * the transmittance every ckpt_interval samples, read by shw_render_backward.
+ * Scheduling state: views that are not spectral-axis sweeps run as persistent CTAs that
+ * take tiles from a device work counter, one of 1024 per device handed out in turn and
+ * zeroed on `stream` at each call.  So at most 1024 renders may be enqueued and not yet
+ * finished at once across all streams of a device, and a call made while `stream` is being
+ * captured into a CUDA graph is refused with SHW_EUNSUPPORTED (a replayed capture would
+ * keep its counter while later calls reuse it); batch plans are the graph-launched form. */
 shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_camera *cam,
                       const shw_render_params *p, float *out_rgba, float *out_scalar,
                       int32_t *out_index, int32_t *out_nsamples, void *ckpt, size_t ckpt_bytes,
@@ -272,6 +300,24 @@ size_t shw_ckpt_bytes(const shw_volume *vol, const shw_camera *cam, const shw_re
 shw_status shw_render_backward(const shw_volume *vol, const shw_camera *cam, const shw_render_params *p,
                                const float *grad_rgba, const void *ckpt, size_t ckpt_bytes, float *grad_vol,
                                float *grad_lut, float *grad_scale, void *stream);
+
+/* ---- test and diagnosis switches (no paper counterpart) -------------------- */
+
+/* Process-wide switches for tests that compare two paths of the library or exercise its
+ * failure handling; all off by default, and no caller needs them for normal use.  Each
+ * call replaces every flag and returns the previous set.  The switches change which
+ * kernel serves a request, never what it computes (the fault switches excepted). */
+#define SHW_DEBUG_NO_AXIS_SWEEP 0x1u  /* orthographic spectral-axis views take the general marcher */
+#define SHW_DEBUG_SMOOTH_PLAIN  0x2u  /* smoothing takes its kernel without tensor copies */
+#define SHW_DEBUG_BOX_DIRECT    0x4u  /* in-ray box smoothing by direct fetches, never the lattice sums */
+#define SHW_DEBUG_NO_STAGING    0x8u  /* general views take the gather marcher, not the staged one */
+#define SHW_DEBUG_FAULT_ALLOC   0x10u /* batch-plan device allocations fail (SHW_ENOMEM) */
+#define SHW_DEBUG_FAULT_GRAPH   0x20u /* batch-plan graph capture fails (SHW_ECUDA) */
+#define SHW_DEBUG_FAULT_TIMEOUT 0x40u /* tensor-copy kernels launched while set leave one stage's copy
+                                         unissued and wait for it about 1 ms: every CTA that needs the
+                                         stage gives up, returns, and shw_sync_status reports
+                                         SHW_ETIMEOUT; the output is left incomplete */
+uint32_t shw_set_debug_flags(uint32_t flags);
 
 /* ---- batched rendering of many sub-cubes ----------------------------------- */
 
@@ -311,8 +357,8 @@ typedef struct {
  * keeps the fastest; later plans of the same signature reuse the choice.
  * The plan keeps the item pointers (cubes, outputs, colour map) until destroyed.
  * Errors: SHW_EINVAL, SHW_EUNSUPPORTED, SHW_ENOMEM (allocation), SHW_ECUDA (capture),
- * SHW_EDEVICE.  With the environment variable SHW_FAULT containing "alloc" or
- * "graph", the allocation or the capture is made to fail (host-side fault injection). */
+ * SHW_EDEVICE.  SHW_DEBUG_FAULT_ALLOC / SHW_DEBUG_FAULT_GRAPH make the allocation or the
+ * capture fail (host-side fault injection, see shw_set_debug_flags). */
 shw_status shw_batch_plan_create(shw_batch_plan **plan, const shw_batch_item *items, int32_t n,
                                  const shw_render_params *p, int32_t flags, void *stream);
 
@@ -340,7 +386,12 @@ shw_status shw_batch_plan_destroy(shw_batch_plan *plan);
  *  - Capacity: 256 + 128 * n + 8 * (total 16 x 16 tiles of all images) bytes must fit
  *    in SHW_NOALLOC_SCRATCH_BYTES, else SHW_EUNSUPPORTED and nothing is enqueued.
  *  - The first call on a device looks up the array's device address (with that
- *    device current) and caches it; make that first call before any stream capture.
+ *    device current) and caches it.  A call made while `stream` is being captured into
+ *    a CUDA graph is refused with SHW_EUNSUPPORTED: the call copies the item table and
+ *    the work list from host memory it owns only while it runs.
+ *  - That copy is from ordinary (pageable) host memory, so the call returns only after
+ *    the work already enqueued on `stream` has finished and the table has been handed
+ *    to the copy engine: the host waits for the stream, though no allocator is touched.
  *  - Every call reuses the one array per device and overwrites the previous call's
  *    contents (the counter is cleared on `stream` first).  Calls whose work can
  *    overlap on the GPU -- on different streams without ordering -- race with each

@@ -23,8 +23,9 @@
  *                               binomial b_n = [1,1]^{*n} and Algorithm 9
  *   adjoint of compositing .... reverse mode over a stored per-sample tape
  *
- * Readings where the paper is silent (each one is listed with its reason in the
- * design notes): voxel (i,j,k) sits at the point (i,j,k) and the box is
+ * Readings where the paper is silent, ambiguous or garbled (the paper fixes none of
+ * these; each is the plainest reading of the passage cited beside the function that
+ * takes it): voxel (i,j,k) sits at the point (i,j,k) and the box is
  * [-0.5, n-0.5]^3; samples lie at the mid-points t0 + (k + 1/2) h of a ray
  * clipped to the box, N = floor((t1 - t0) / h); indices clamp to the edge; a NaN
  * sample is replaced by DATAMIN, which is the colour map's domain low `lo`;

@@ -9,6 +9,7 @@ from .api import (  # noqa: F401
     binomial_taps,
     bricked_bytes,
     ckpt_bytes,
+    debug_flags,
     launch_count,
     linear_sampling_taps,
     pack_bricks,

@@ -15,8 +15,9 @@ import torch
 from . import _lib
 from ._lib import INTERP, MODES, STORAGE, ShwError, check, lib
 
-__all__ = ["BatchPlan", "BrickVolume", "ShwError", "bricked_bytes", "ckpt_bytes", "launch_count", "pack_bricks", "render",
-           "render_backward", "smooth", "smooth_weights", "sync_status"]
+__all__ = ["BatchPlan", "BrickVolume", "ShwError", "binomial_taps", "bricked_bytes", "ckpt_bytes", "debug_flags",
+           "launch_count", "linear_sampling_taps", "pack_bricks", "render", "render_backward", "smooth",
+           "smooth_weights", "smooth_zip", "sync_status"]
 
 
 def _stream() -> int:
@@ -103,39 +104,50 @@ def params_struct(mode, lut, *, interp="trilinear", step=0.5, lo=-3.0, hi=8.0, o
     return p
 
 
+def _taps_out(call, what):
+    c0, nf = C.c_double(), C.c_int32()
+    offs, wts = (C.c_double * 64)(), (C.c_double * 64)()
+    check(call(C.byref(c0), offs, wts, 64, C.byref(nf)), what)
+    n = nf.value
+    return c0.value, list(offs[:n]), list(wts[:n])
+
+
 def linear_sampling_taps(w):
-    """Fold a symmetric 1-D kernel w[-r..r] into the fetches of SHW_SMOOTH_TAPS (Section 4.2's
-    linear-sampling trick behind Algorithm 9): the centre keeps w_0; taps a and a+1 (a = 1, 3,
-    ...) become one fetch of weight w_a + w_{a+1} at the offset where linear interpolation
-    between them gives their weighted sum.  Returns (c0, offsets, weights)."""
-    w = [float(x) for x in w]
-    if len(w) % 2 != 1:
+    """Fold a symmetric 1-D kernel w[-r..r] into the fetches of SHW_SMOOTH_TAPS by linear
+    sampling (Section 4.2, Algorithm 9), computed by the library (shw_linear_sampling_taps).
+    Returns (c0, offsets, weights)."""
+    wl = [float(x) for x in w]
+    if len(wl) % 2 != 1:
         raise ValueError("the kernel must have odd length 2r+1")
-    r = (len(w) - 1) // 2
-    offs, wts = [], []
-    for a in range(1, r + 1, 2):
-        wa = w[r + a]
-        wb = w[r + a + 1] if a + 1 <= r else 0.0
-        tot = wa + wb
-        offs.append((a * wa + (a + 1) * wb) / tot if tot != 0.0 else float(a))
-        wts.append(tot)
-    return w[r], offs, wts
+    arr = (C.c_double * len(wl))(*wl)
+    return _taps_out(lambda *o: lib().shw_linear_sampling_taps(arr, (len(wl) - 1) // 2, *o),
+                     "shw_linear_sampling_taps")
 
 
 def binomial_taps(ntaps: int, drop: int = 0):
-    """The N-tap binomial filter of Section 4.2 folded for SHW_SMOOTH_TAPS: b_{N-1+2 drop}
-    = [1, 1]^{*(N-1+2 drop)} without its `drop` outer taps on each side, renormalised.
-    ntaps = 5, 9, 13 with drop = 0 are b_4, b_8, b_12; ntaps = 9, drop = 2 is the kernel
-    whose folded constants Algorithm 9 prints."""
-    if ntaps < 1 or ntaps % 2 != 1 or drop < 0:
-        raise ValueError("ntaps must be odd and positive, drop >= 0")
-    n = ntaps - 1 + 2 * drop
-    row = [1]
-    for _ in range(n):
-        row = [a + b for a, b in zip([0] + row, row + [0])]
-    core = row[drop:len(row) - drop]
-    tot = float(sum(core))
-    return linear_sampling_taps([c / tot for c in core])
+    """The N-tap binomial filter of Section 4.2 folded for SHW_SMOOTH_TAPS, computed by the
+    library (shw_binomial_taps): b_{N-1+2 drop} without its `drop` outer taps on each side,
+    renormalised.  ntaps = 5, 9, 13 with drop = 0 are b_4, b_8, b_12; ntaps = 9, drop = 2 is
+    the kernel whose folded constants Algorithm 9 prints."""
+    return _taps_out(lambda *o: lib().shw_binomial_taps(int(ntaps), int(drop), *o), "shw_binomial_taps")
+
+
+class debug_flags:
+    """Context manager setting the library's test and diagnosis switches (shw_set_debug_flags)
+    by name, e.g. ``with debug_flags("no_axis_sweep"): ...``; the previous set is restored."""
+
+    def __init__(self, *names):
+        self.mask = 0
+        for n in names:
+            self.mask |= _lib.DEBUG[n]
+
+    def __enter__(self):
+        self.prev = int(lib().shw_set_debug_flags(self.mask))
+        return self
+
+    def __exit__(self, *exc):
+        lib().shw_set_debug_flags(self.prev)
+        return False
 
 
 def smooth(cube: torch.Tensor, sigma: float, radius: int, out: torch.Tensor | None = None) -> torch.Tensor:

@@ -19,6 +19,9 @@ namespace shw {
 static std::atomic<uint64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+static std::atomic<uint32_t> g_debug_flags{0};
+uint32_t debug_flags() { return g_debug_flags.load(std::memory_order_relaxed); }
+
 // The device error word: kernels OR in a bit when a bounded wait gives up.
 static __device__ unsigned g_device_error;
 static std::mutex g_err_mu;
@@ -220,6 +223,8 @@ size_t shw_struct_size(int32_t which)
 
 uint64_t shw_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+uint32_t shw_set_debug_flags(uint32_t flags) { return g_debug_flags.exchange(flags, std::memory_order_relaxed); }
+
 shw_status shw_sync_status(void *stream)
 {
     int n = 0;
@@ -299,7 +304,7 @@ shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_c
         a.smooth_c0 = (float)(1.0 / (2.0 * p->smooth_arm + 1.0));
         // a step of exactly 1/2 voxel puts the box's neighbours on the ray's own samples
         const bool single = p->mode != SHW_RATIO && p->mode != SHW_RATIO_MIP;
-        if (p->smooth_arm > 0 && p->step == 0.5f && single && !getenv("SHW_BOX_DIRECT")) a.box_lattice = 2;
+        if (p->smooth_arm > 0 && p->step == 0.5f && single && !debug(SHW_DEBUG_BOX_DIRECT)) a.box_lattice = 2;
     } else if (p->smooth == SHW_SMOOTH_TAPS) {
         a.smooth_n = p->smooth_ntaps;
         a.smooth_c0 = p->smooth_c0;
@@ -321,6 +326,8 @@ shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_c
     }
     const shw_volume *v2 = (!pair && (p->mode == SHW_RATIO || p->mode == SHW_RATIO_MIP)) ? vol2 : nullptr;
     cudaStream_t st = as_stream(stream);
+    // a captured launch would keep the work counter it was given while later calls reuse it
+    if (capturing(st)) return SHW_EUNSUPPORTED;
     if (pair) return render_pair(p->mode, p->interp, *vol, *cam, a, st);
     if (a.box_lattice == 2)
         return vol->storage == SHW_F32 ? render_smooth_lat_f32(p->mode, p->interp, *vol, *cam, a, st)

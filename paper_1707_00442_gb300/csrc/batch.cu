@@ -155,11 +155,8 @@ static void plan_free(shw_batch_plan *pl)
     delete pl;
 }
 
-static bool fault(const char *what)
-{
-    const char *f = std::getenv("SHW_FAULT");
-    return f && std::strstr(f, what) != nullptr;
-}
+// host-side fault injection (shw_set_debug_flags)
+static bool fault(uint32_t flag) { return debug(flag); }
 
 // (re)build the work list for a tile size: tiles of the biggest items first
 static shw_status build_work(shw_batch_plan *pl, int tile)
@@ -176,7 +173,7 @@ static shw_status build_work(shw_batch_plan *pl, int tile)
     pl->sh.nwork = pl->nwork;
     if (pl->d_work) cudaFree(pl->d_work);
     pl->d_work = nullptr;
-    if (fault("alloc") || cudaMalloc(&pl->d_work, work.size() * sizeof(int2)) != cudaSuccess) {
+    if (fault(SHW_DEBUG_FAULT_ALLOC) || cudaMalloc(&pl->d_work, work.size() * sizeof(int2)) != cudaSuccess) {
         cudaGetLastError();
         pl->d_work = nullptr;
         return SHW_ENOMEM;
@@ -205,7 +202,7 @@ static shw_status capture(shw_batch_plan *pl)
     if (pl->graph) cudaGraphDestroy(pl->graph);
     pl->exec = nullptr;
     pl->graph = nullptr;
-    if (fault("graph")) return SHW_ECUDA;
+    if (fault(SHW_DEBUG_FAULT_GRAPH)) return SHW_ECUDA;
     if (cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SHW_ECUDA;
     cudaMemsetAsync(pl->d_counter, 0, sizeof(int), pl->cap);
     pl->grid = pl->sms * pl->ctas_per_sm;
@@ -347,7 +344,7 @@ shw_status shw_batch_plan_create(shw_batch_plan **out, const shw_batch_item *ite
     for (int i = 0; i < n; ++i) pl->order[i] = i;
     std::stable_sort(pl->order.begin(), pl->order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
 
-    if (fault("alloc") || cudaMalloc(&pl->d_items, sizeof(BatchItemDev) * n) != cudaSuccess ||
+    if (fault(SHW_DEBUG_FAULT_ALLOC) || cudaMalloc(&pl->d_items, sizeof(BatchItemDev) * n) != cudaSuccess ||
         cudaMalloc(&pl->d_counter, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         plan_free(pl);
@@ -485,6 +482,9 @@ extern "C" shw_status shw_render_batch_noalloc(const shw_batch_item *items, int3
     const size_t bytes = work_off + sizeof(int2) * (size_t)nwork;
     if (nwork > 0x7fffffffLL || bytes > SHW_NOALLOC_SCRATCH_BYTES) return SHW_EUNSUPPORTED;  // beyond the fixed scratch
 
+    // the table below is copied from host memory this call owns only while it runs, so a
+    // capture (whose replays would read it after the call returned) is refused
+    if (capturing(as_stream(stream))) return SHW_EUNSUPPORTED;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
@@ -565,6 +565,3 @@ extern "C" shw_status shw_render_batch_noalloc(const shw_batch_item *items, int3
     return after_launch();
 }
 
-extern "C" {
-
-}  // extern "C"

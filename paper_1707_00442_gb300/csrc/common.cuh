@@ -11,6 +11,21 @@ namespace shw {
 // Counts every kernel launch made by this library (reported by shw_launch_count).
 void note_launch();
 
+// The test and diagnosis switches of shw_set_debug_flags (SHW_DEBUG_*).
+uint32_t debug_flags();
+inline bool debug(uint32_t flag) { return (debug_flags() & flag) != 0u; }
+
+// True if `st` is being captured into a CUDA graph (or its state cannot be read).
+inline bool capturing(cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
 inline shw_status cuda_status(cudaError_t e) { return e == cudaSuccess ? SHW_OK : SHW_ECUDA; }
 
 // Status after a launch: a launch-configuration error is reported now.

@@ -13,7 +13,7 @@ namespace shw {
 // plane spanned by x and y, for single-cube modes.
 static bool axis_eligible(const shw_volume &v, const shw_camera &c, int mode)
 {
-    if (std::getenv("SHW_NO_AXIS_SWEEP")) return false;
+    if (debug(SHW_DEBUG_NO_AXIS_SWEEP)) return false;
     return v.storage == SHW_F32 && mode != SHW_RATIO && mode <= SHW_MOMENT1 && c.ortho && c.fwd[0] == 0.0f && c.fwd[1] == 0.0f &&
            c.fwd[2] != 0.0f && c.right[2] == 0.0f && c.up[2] == 0.0f && v.nx % 4 == 0 && aligned(v.data, 16) &&
            (long long)v.nx * v.ny < (1ll << 29);  // byte offsets in a plane fit an int

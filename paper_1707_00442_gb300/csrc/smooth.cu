@@ -420,7 +420,7 @@ static shw_status smooth_dispatch(const float *in, float *out, int nx, int ny, i
 {
     // TMA pipeline where its alignment rules hold, the staged kernel otherwise
     const bool zip_ok = !ZIP || (aligned(first, 8) && aligned(out, 16));
-    if (r >= 1 && r <= 8 && nx % 4 == 0 && aligned(in, 16) && zip_ok && !std::getenv("SHW_SMOOTH_NO_TMA")) {
+    if (r >= 1 && r <= 8 && nx % 4 == 0 && aligned(in, 16) && zip_ok && !debug(SHW_DEBUG_SMOOTH_PLAIN)) {
         bool ok = false;
         switch (r) {
 #define SHW_T(n) \

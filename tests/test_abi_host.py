@@ -50,7 +50,7 @@ def test_struct_layout(L):
     assert L.shw_struct_size(3) == C.sizeof(_lib.BatchItem) == 112
     assert L.shw_struct_size(4) == C.sizeof(_lib.BatchInfo)
     assert L.shw_struct_size(9) == 0
-    assert L.shw_abi_version() == 3
+    assert L.shw_abi_version() == 4
 
 
 def test_status_strings(L):

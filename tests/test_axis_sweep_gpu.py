@@ -18,13 +18,20 @@ def m():
     return shw()
 
 
-def _cam_z(dims, W, H, *, down=False, angle_deg=0.0, spacing=1.0):
+# Nearest sampling: the eye moves off the half-voxel grid in the image plane so that no pixel
+# centre lies on a voxel-rounding tie (with the centred eye, whole images of the ragged and
+# two-voxel cases would be ties, which the oracle flags and the comparison must skip).
+NEAREST_SHIFT = (0.137, 0.071)
+
+
+def _cam_z(dims, W, H, *, down=False, angle_deg=0.0, spacing=1.0, shift=(0.0, 0.0)):
     nx, ny, nz = dims
     c = math.cos(math.radians(angle_deg)); s = math.sin(math.radians(angle_deg))
     right = np.array([c, s, 0.0]); up = np.array([-s, c, 0.0]); fwd = np.array([0.0, 0.0, 1.0])
     eye = np.array([(nx - 1) / 2, (ny - 1) / 2, -8.0])
     if down:
         fwd = -fwd; right = -right; eye[2] = nz + 8.0
+    eye = eye + shift[0] * right + shift[1] * up
     half_h = spacing * H / 2
     cam = scene.Camera(eye.astype(np.float32), right.astype(np.float32), up.astype(np.float32),
                        fwd.astype(np.float32), 0.0, float(half_h), True, W, H)
@@ -47,10 +54,9 @@ CASES = [
 def _both(m, monkeypatch, cube_t, cam, mode, lut_t, **kw):
     a = m.render(cube_t, cam, mode, lut=lut_t, **kw)
     torch.cuda.synchronize()
-    monkeypatch.setenv("SHW_NO_AXIS_SWEEP", "1")
-    b = m.render(cube_t, cam, mode, lut=lut_t, **kw)
-    torch.cuda.synchronize()
-    monkeypatch.delenv("SHW_NO_AXIS_SWEEP")
+    with m.debug_flags("no_axis_sweep"):
+        b = m.render(cube_t, cam, mode, lut=lut_t, **kw)
+        torch.cuda.synchronize()
     m.sync_status()
     return a, b
 
@@ -64,7 +70,7 @@ def test_sweep_equals_general_marcher(m, monkeypatch, case, mode, interp):
     cube = scene.tiny_cube(config_id=50 + case, dims=dims, n_sources=2)
     cube[3, 5, 7] = np.nan
     cam = _cam_z(dims, c["W"], c["H"], down=c.get("down", False), angle_deg=c.get("angle_deg", 0.0),
-                 spacing=c.get("spacing", 1.0))
+                 spacing=c.get("spacing", 1.0), shift=NEAREST_SHIFT if interp == "nearest" else (0.0, 0.0))
     lut = to_dev(scene.linear_lut())
     kw = dict(interp=interp, opacity_scale=0.05, step=c.get("step", 0.5))
     if mode == "composite":
@@ -92,7 +98,7 @@ def test_sweep_equals_general_marcher(m, monkeypatch, case, mode, interp):
                           step=float(np.float32(c.get("step", 0.5))), eps_pos=1e-6, eps_val=1e-4)
         g = {k: v.cpu().numpy() for k, v in a.items()}
         compare(g, o, mode, scale=float(dims[2]) if mode == "moment1" else float(np.nanmax(cube) - np.nanmin(cube)),
-                max_fragile=0.15 if interp == "trilinear" else 1.0,
+                max_fragile=0.15 if interp == "trilinear" else 0.01,
                 what=f"sweep/{mode}/{interp}/{case}")
 
 
@@ -117,7 +123,7 @@ def test_sweep_mip_without_index(m, monkeypatch, case, interp):
     cube[5, 9, 11] = np.nan
     cube[2, 3, 4] = 0.0
     cam = _cam_z(dims, c["W"], c["H"], down=c.get("down", False), angle_deg=c.get("angle_deg", 0.0),
-                 spacing=c.get("spacing", 1.0))
+                 spacing=c.get("spacing", 1.0), shift=NEAREST_SHIFT if interp == "nearest" else (0.0, 0.0))
     lut = to_dev(scene.linear_lut())
     a, b = _both(m, monkeypatch, to_dev(cube), cam, "mip", lut, interp=interp, step=c.get("step", 0.5),
                  index=False)

@@ -88,20 +88,17 @@ def test_batch_relaunch_and_cache(m):
         p.close()
 
 
-def test_batch_fault_injection(m, monkeypatch):
+def test_batch_fault_injection(m):
     """Host-side faults: allocation and graph capture failures are reported, nothing leaks a plan."""
     items = _batch(n=4, storage_cycle=("f32",))
     lut = to_dev(scene.linear_lut())
     dev = _dev_items(m, items)
-    monkeypatch.setenv("SHW_FAULT", "alloc")
-    with pytest.raises(m.ShwError) as e:
+    with m.debug_flags("fault_alloc"), pytest.raises(m.ShwError) as e:
         m.BatchPlan(dev, lut=lut, tune=False)
     assert e.value.status == 4  # SHW_ENOMEM
-    monkeypatch.setenv("SHW_FAULT", "graph")
-    with pytest.raises(m.ShwError) as e:
+    with m.debug_flags("fault_graph"), pytest.raises(m.ShwError) as e:
         m.BatchPlan(dev, lut=lut, tune=False)
     assert e.value.status == 3  # SHW_ECUDA
-    monkeypatch.delenv("SHW_FAULT")
     p = m.BatchPlan(dev, lut=lut, tune=False)
     p.render()
     m.sync_status()

@@ -231,3 +231,23 @@ def test_alpha_threshold_parity(m, ragged, mode):
     compare(g, o, mode, scale=_scale(cube, mode, o), max_fragile=0.05, what=f"{mode}/alpha-threshold")
     a = g["rgba"][..., 3]
     assert set(np.unique(a)) <= {0.0, 1.0} and (a == 1.0).any() and (a == 0.0).any()
+
+
+def test_render_refuses_a_capturing_stream(m):
+    """A render's persistent CTAs take tiles from a work counter handed out at call time, so a
+    call made while the stream is captured into a CUDA graph is refused (SHW_EUNSUPPORTED)
+    before anything is enqueued; batch plans are the graph-launched form."""
+    cube = to_dev(scene.tiny_cube())
+    lut = to_dev(scene.linear_lut())
+    cam = scene.orbit_camera((64, 64, 64), 30, 20, 32, 24)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    status = []
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=s):
+        try:
+            m.render(cube, cam, "mip", lut=lut)
+        except m.ShwError as e:
+            status.append(e.status)
+    assert status == [2]
+    m.sync_status()

@@ -66,9 +66,9 @@ def test_smooth_nan_propagates_locally(m):
     assert np.abs(g[ok] - o[ok]).max() <= TOL_F32 * float(np.nanmax(cube) - np.nanmin(cube))
 
 
-def test_smooth_tma_and_staged_paths_agree(m, monkeypatch):
+def test_smooth_tma_and_staged_paths_agree(m):
     cube = scene.tiny_cube(config_id=24, dims=(68, 52, 75), n_sources=2)
     a = _gpu_smooth(m, cube, 2.0, 6)
-    monkeypatch.setenv("SHW_SMOOTH_NO_TMA", "1")
-    b = _gpu_smooth(m, cube, 2.0, 6)
+    with m.debug_flags("smooth_plain"):
+        b = _gpu_smooth(m, cube, 2.0, 6)
     assert np.abs(a - b).max() <= 1e-6 * float(cube.max() - cube.min())

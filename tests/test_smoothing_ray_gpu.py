@@ -165,9 +165,9 @@ def test_smoothing_rejected_where_unsupported(m, ragged):
 
 @pytest.mark.parametrize("step", [0.5, 1.0])
 @pytest.mark.parametrize("mode", ["mip", "avg", "composite", "moment1"])
-def test_box_lattice_matches_direct(m, ragged, step, mode, monkeypatch):
+def test_box_lattice_matches_direct(m, ragged, step, mode):
     """With a step of 1/2 voxel the box runs as running sums over the ray's own samples; it
-    agrees with the direct per-sample sums (SHW_BOX_DIRECT) to FP32 rounding.  (A step of 1
+    agrees with the direct per-sample sums (SHW_DEBUG_BOX_DIRECT) to FP32 rounding.  (A step of 1
     takes the direct sums either way.)"""
     cube, c2 = ragged
     cube = cube.copy()
@@ -176,8 +176,8 @@ def test_box_lattice_matches_direct(m, ragged, step, mode, monkeypatch):
     lut = to_dev(scene.linear_lut())
     kw = dict(_kw(mode), step=step, smooth="box", smooth_arm=4)
     lat = gpu_render(m, to_dev(cube), cam, mode, lut, **kw)
-    monkeypatch.setenv("SHW_BOX_DIRECT", "1")
-    dct = gpu_render(m, to_dev(cube), cam, mode, lut, **kw)
+    with m.debug_flags("box_direct"):
+        dct = gpu_render(m, to_dev(cube), cam, mode, lut, **kw)
     scale = 1.0 if mode == "composite" else (float(cube.shape[0]) if mode == "moment1" else
                                               float(np.nanmax(cube) - np.nanmin(cube)))
     if mode != "composite":  # (compositing's exit sample is a rounding decision: oracle check only)
