@@ -3,7 +3,8 @@
 Tolerances (each against the FP64 oracle):
   * FP32 path: max |err| <= 1e-5 x data range for scalar outputs (range = max - min of
     the input cube; of the oracle's ratio image for RATIO) and <= 1e-5 for RGBA;
-  * BF16 / FP16 bricks: <= 2e-3 on the same scales;
+  * BF16 / FP16 bricks: <= 2e-3 on the same scales (the line ratio from bfloat16 storage:
+    BF16_RATIO_TOL of the ratio image's range, declared outside that bound);
   * nearest-sample maximum and its channel on axis-aligned parallel views: bit-exact.
 Where floating point decides a discrete outcome (which sample is the maximum, a
 nearest-voxel rounding, a ratio threshold, the early-exit sample, the sample count),
@@ -20,6 +21,11 @@ import oracle
 
 TOL_F32 = 1e-5
 TOL_REDUCED = 2e-3
+# The line ratio from bfloat16 storage: a quotient of two values each rounded to 8 significant
+# bits errs by up to about 2 x 2^-8 of the ratio, more than 2e-3 of the ratio image's range;
+# this path is declared outside the reduced-precision bound and held to this fraction of the
+# range instead (binary16 storage meets TOL_REDUCED).
+BF16_RATIO_TOL = 2e-2
 F_COUNT, F_ROUND, F_RATIO, F_EXIT, F_TIE = (oracle.FRAG_COUNT, oracle.FRAG_ROUND, oracle.FRAG_RATIO,
                                            oracle.FRAG_EXIT, oracle.FRAG_TIE)
 

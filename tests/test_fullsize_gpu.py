@@ -120,8 +120,12 @@ def test_survey_bricks_error_vs_fp64(m, survey, pixels, storage):
     """The reduced-precision path at full size: every mode rendered from 16-bit bricks of the
     smoothed survey cubes (the ratio from pair bricks), against the FP64 oracle on the float32
     smoothed cubes at sampled pixels.  Prints max-abs and RMS error per mode; the scalar of the
-    single-cube modes within 2e-3 of the data range (near-ties at that margin skipped)."""
-    from parity import TOL_REDUCED
+    single-cube modes within 2e-3 of the data range (near-ties at that margin skipped).  The line
+    ratio, a quotient of two rounded values, is held to 2e-3 of the ratio image's range with
+    binary16 storage and to the wider declared bound BF16_RATIO_TOL of that range with bfloat16
+    (8 significant bits: the quotient's relative error reaches about 2 x 2^-8), on rays whose
+    threshold and maximum decisions lie outside the storage's rounding margin."""
+    from parity import BF16_RATIO_TOL, TOL_REDUCED
     cube, c2 = survey[0], survey[1]
     sig, r = W.SURVEY["sigma"], W.SURVEY["radius"]
     s1 = m.smooth(to_dev(cube), sig, r)
@@ -140,14 +144,25 @@ def test_survey_bricks_error_vs_fp64(m, survey, pixels, storage):
         m.sync_status()
         g = {k: v.cpu().numpy() for k, v in out.items()}
         scale = 1.0 if mode == "composite" else rng_
+        # decisions within the storage's rounding of the largest magnitude are near-ties
+        eps = (2.0 ** -8 if storage == "bf16" else 2.0 ** -11) * float(np.abs(s1h).max()) if mode == "ratio" \
+            else TOL_REDUCED * scale
         o = oracle.render(s1h, cam, mode, lut=lut, cube2=s2h if mode == "ratio" else None, pixels=pixels,
-                          step=W.SURVEY["step"], eps_pos=1e-6, eps_val=TOL_REDUCED * scale, **kw)
+                          step=W.SURVEY["step"], eps_pos=1e-6, eps_val=eps, **kw)
         flat = lambda a: a.reshape(-1, *a.shape[2:])[pixels]  # noqa: E731
         ok = o["nsamples"] > 0
         es = np.abs(flat(g["scalar"]).astype(np.float64) - o["scalar"])[ok]
         er = np.abs(flat(g["rgba"]).astype(np.float64) - o["rgba"])[ok]
         print(f"{storage}/{mode}: scalar max {es.max():.3e} rms {np.sqrt((es ** 2).mean()):.3e} "
               f"(range {scale:.3g}); rgba max {er.max():.3e} rms {np.sqrt((er ** 2).mean()):.3e}")
+        steady = ok & (o["fragile"] == 0)
+        err = np.abs(flat(g["scalar"]).astype(np.float64) - o["scalar"])[steady]
         if mode != "ratio":
-            steady = ok & (o["fragile"] == 0)
-            assert np.abs(flat(g["scalar"]).astype(np.float64) - o["scalar"])[steady].max() <= TOL_REDUCED * scale
+            assert err.max() <= TOL_REDUCED * scale
+        else:
+            rr = float(o["scalar"].max() - o["scalar"].min())  # the ratio image's range
+            bound = (BF16_RATIO_TOL if storage == "bf16" else TOL_REDUCED) * rr
+            print(f"{storage}/ratio steady rays {steady.mean():.3f}: max {err.max():.3e} = "
+                  f"{err.max() / rr:.2e} of the ratio range {rr:.3g}, rms {np.sqrt((err ** 2).mean()):.3e}")
+            assert steady.mean() >= 0.9
+            assert err.max() <= bound, (storage, err.max(), bound)

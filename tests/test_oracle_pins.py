@@ -279,6 +279,68 @@ def test_perspective_rays_geometry(O):
     assert np.linalg.norm(d - f / np.linalg.norm(f)) < 1e-7
 
 
+def _line_distance(p, a, d):
+    """Distance of point p from the line through a with unit direction d."""
+    v = p - a
+    return float(np.linalg.norm(v - np.dot(v, d) * d))
+
+
+def test_perspective_projection_pin(O):
+    """Appendix A perspective, pinned by the forward pinhole projection (not the oracle's own
+    pixel -> ray formula): a point Q is taken to camera coordinates (x, y, z) = ((Q - eye).right,
+    (Q - eye).up, (Q - eye).fwd) and divided by depth; it lands in pixel
+    u = W/2 (1 + x / (z tan(fov/2) W/H)), v = H/2 (1 - y / (z tan(fov/2))) (row 0 at the top).
+    The oracle's ray of that pixel must pass closer to Q than the rays of its 8 neighbours,
+    within one pixel's footprint at Q's depth.  A wrong aspect axis, a flipped row direction or
+    a wrong field-of-view scale each moves the nearest ray to another pixel."""
+    dims = (40, 30, 50)
+    cube = scene.tiny_cube(dims=dims, n_sources=1)
+    W, H = 64, 36  # not square: the aspect ratio matters
+    cam = scene.orbit_camera(dims, 37, -23, W, H)
+    eye = cam.eye.astype(np.float64)
+    R, U, F = (np.asarray(v, np.float64) for v in (cam.right, cam.up, cam.fwd))
+    th = float(cam.tan_half_fovy)
+    rng = np.random.default_rng(17)
+    checked = 0
+
+    def ray(px, py):
+        pos, _ = O.ray_trace(cube, cam, px, py)
+        if len(pos) < 2:
+            return None
+        return pos[0], (pos[1] - pos[0]) / np.linalg.norm(pos[1] - pos[0])
+
+    for _ in range(60):
+        Q = np.array([rng.uniform(3, n - 4) for n in dims])
+        q = Q - eye
+        x, y, z = np.dot(q, R), np.dot(q, U), np.dot(q, F)
+        u = W / 2 * (1 + x / (z * th * W / H))
+        v = H / 2 * (1 - y / (z * th))
+        fu, fv = u - math.floor(u), v - math.floor(v)
+        if min(fu, 1 - fu, fv, 1 - fv) < 0.05 or not (1 <= u < W - 1 and 1 <= v < H - 1):
+            continue  # near a pixel border, or at the image edge
+        px, py = int(math.floor(u)), int(math.floor(v))
+        centre = ray(px, py)
+        assert centre is not None
+        d0 = _line_distance(Q, *centre)
+        assert d0 <= 2 * z * th / H, (Q, d0)  # within one pixel's footprint at depth z
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                if dx == dy == 0:
+                    continue
+                nb = ray(px + dx, py + dy)
+                if nb is not None:
+                    assert _line_distance(Q, *nb) > d0, (Q, px, py, dx, dy)
+        checked += 1
+    assert checked >= 30
+    # the row direction: a point above the cube centre lands in a smaller row than one below
+    c = np.array([(n - 1) / 2 for n in dims])
+    rows = []
+    for k in (-6.0, 6.0):
+        q = c + k * U - eye
+        rows.append(H / 2 * (1 - np.dot(q, U) / (np.dot(q, F) * th)))
+    assert rows[1] < rows[0]
+
+
 def test_ortho_sample_count_is_depth(O):
     cam = scene.ortho_axis_camera((64, 64, 64), 128, 128)
     tot, per = O.count_samples((64, 64, 64), cam)
