@@ -160,6 +160,11 @@ def test_survey_bricks_error_vs_fp64(m, survey, pixels, storage):
         if mode != "ratio":
             assert err.max() <= TOL_REDUCED * scale
         else:
+            # the maximum's value is unique even where its position is a near-tie: only the
+            # count, rounding, exit and ratio-threshold decisions exclude a ray
+            from parity import F_COUNT, F_EXIT, F_RATIO, F_ROUND
+            steady = ok & ((o["fragile"] & (F_COUNT | F_EXIT | F_RATIO | F_ROUND)) == 0)
+            err = np.abs(flat(g["scalar"]).astype(np.float64) - o["scalar"])[steady]
             rr = float(o["scalar"].max() - o["scalar"].min())  # the ratio image's range
             bound = (BF16_RATIO_TOL if storage == "bf16" else TOL_REDUCED) * rr
             print(f"{storage}/ratio steady rays {steady.mean():.3f}: max {err.max():.3e} = "
