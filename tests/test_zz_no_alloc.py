@@ -108,8 +108,8 @@ def test_noalloc_smaller_second_call_uses_only_its_own_table():
         assert bool((o == -7.0).all())
     # the float32 items against the FP64 oracle (the batch-plan tolerance)
     for (vol, cam, mode), cube, o in zip(small, small_cubes, outs):
-        if vol.dtype != torch.float32:
-            continue
+        if not isinstance(vol, torch.Tensor):
+            continue  # the bfloat16 bricks: compared with the batch plan above
         orc = oracle.render(cube, cam, mode, lut=scene.linear_lut(), opacity_scale=0.05, eps_pos=1e-6,
                             eps_val=1e-4)
         ok = orc["fragile"] == 0
