@@ -102,11 +102,22 @@ typedef enum {
     SHW_BF16_PAIR_BRICK = 4, /* the pair storage as bricks: 32-bit elements, the low half the first
                                 cube's bfloat16, the high half the second's; written by
                                 shw_pack_bricks from an SHW_F32_PAIR buffer; the line ratios only */
-    SHW_F16_PAIR_BRICK = 5   /* the same with IEEE binary16 halves */
+    SHW_F16_PAIR_BRICK = 5,  /* the same with IEEE binary16 halves */
+    SHW_BF16 = 6,       /* linear bfloat16 [nz][ny][nx] (raw 16-bit values, rounded to nearest even),
+                           written by shw_pack_bricks.  Only the staged marcher renders the linear
+                           16-bit storages: trilinear sampling, no in-ray smoothing, data 16-byte
+                           aligned, nx * element bytes a multiple of 16, fewer than 2^31 voxels;
+                           other requests SHW_EUNSUPPORTED */
+    SHW_F16 = 7,        /* the same with IEEE binary16 */
+    SHW_BF16_PAIR = 8,  /* the line ratios' two cubes as linear 16-bit pairs: 32-bit elements
+                           [nz][ny][nx], the low half the first cube's bfloat16, the high half the
+                           second's; written by shw_pack_bricks from an SHW_F32_PAIR buffer;
+                           SHW_RATIO and SHW_RATIO_MIP only, with the limits of SHW_BF16 */
+    SHW_F16_PAIR = 9    /* the same with IEEE binary16 halves */
 } shw_storage;
 
 /* A cube.  data: device.  For SHW_F32 it is the linear float32 array; for the
- * brick storages it is the buffer filled by shw_pack_bricks for the same dims. */
+ * brick and 16-bit storages it is the buffer filled by shw_pack_bricks for the same dims. */
 typedef struct {
     const void *data;
     int32_t nx, ny, nz;
@@ -238,19 +249,21 @@ shw_status shw_linear_sampling_taps(const double *w_host, int32_t radius, double
 shw_status shw_binomial_taps(int32_t ntaps, int32_t drop, double *c0, double *offsets, double *weights,
                              int32_t capacity, int32_t *nfetch);
 
-/* ---- reduced-precision brick storage -------------------------------------- */
+/* ---- reduced-precision storage (bricks and linear 16-bit cubes) ------------ */
 
-/* Bytes of the brick buffer for a cube of these dims: ceil(n/32) bricks per axis,
- * each (32+2)^3 elements of 2 bytes (a 1-voxel apron on every face); 4-byte elements
- * for the pair storages.  Returns 0 for invalid arguments. */
+/* Bytes of the buffer of a reduced-precision storage for a cube of these dims.  Bricks:
+ * ceil(n/32) bricks per axis, each (32+2)^3 elements of 2 bytes (a 1-voxel apron on every
+ * face), 4-byte elements for the pair bricks.  Linear 16-bit storages: nx*ny*nz elements of
+ * 2 bytes (4 for SHW_BF16_PAIR / SHW_F16_PAIR).  Returns 0 for invalid arguments. */
 size_t shw_bricked_bytes(int32_t nx, int32_t ny, int32_t nz, int32_t storage);
 
-/* Pack a float32 cube into bricks, rounding to nearest even.  Brick (bx, by, bz)
- * starts at element ((bz*nby + by)*nbx + bx) * 34^3 and stores, at
+/* Round a float32 cube to a reduced-precision storage, to nearest even.  Bricks: brick
+ * (bx, by, bz) starts at element ((bz*nby + by)*nbx + bx) * 34^3 and stores, at
  * ((lz*34 + ly)*34 + lx), the voxel (32 bx + lx - 1, 32 by + ly - 1, 32 bz + lz - 1)
- * clamped to the cube.  in: device float32 [nz][ny][nx], or for the pair storages the
- * SHW_F32_PAIR buffer [nz][ny][nx][2] (8-byte aligned); out: device, 2-byte aligned (4 for
- * pairs), out_bytes >= shw_bricked_bytes. */
+ * clamped to the cube.  Linear 16-bit storages: element v holds voxel v.
+ * in: device float32 [nz][ny][nx], or for the pair storages the SHW_F32_PAIR buffer
+ * [nz][ny][nx][2] (8-byte aligned); out: device, 2-byte aligned (4 for pairs),
+ * out_bytes >= shw_bricked_bytes. */
 shw_status shw_pack_bricks(const float *in, int32_t nx, int32_t ny, int32_t nz, int32_t storage,
                            void *out, size_t out_bytes, void *stream);
 
@@ -313,6 +326,10 @@ shw_status shw_render_backward(const shw_volume *vol, const shw_camera *cam, con
 #define SHW_DEBUG_NO_STAGING    0x8u  /* general views take the gather marcher, not the staged one */
 #define SHW_DEBUG_FAULT_ALLOC   0x10u /* batch-plan device allocations fail (SHW_ENOMEM) */
 #define SHW_DEBUG_FAULT_GRAPH   0x20u /* batch-plan graph capture fails (SHW_ECUDA) */
+#define SHW_DEBUG_REQUIRE_STAGING 0x80u /* a render of a float32 cube or pair storage that neither the
+                                           spectral-axis sweep nor the staged marcher serves is
+                                           refused (SHW_EUNSUPPORTED) instead of taking the gather
+                                           marcher */
 #define SHW_DEBUG_FAULT_TIMEOUT 0x40u /* tensor-copy kernels launched while set leave one stage's copy
                                          unissued and wait for it about 1 ms: every CTA that needs the
                                          stage gives up, returns, and shw_sync_status reports
@@ -367,6 +384,12 @@ shw_status shw_batch_plan_create(shw_batch_plan **plan, const shw_batch_item *it
 shw_status shw_render_batch(shw_batch_plan *plan, void *stream);
 
 shw_status shw_batch_plan_info(const shw_batch_plan *plan, shw_batch_info *info);
+
+/* The same items rendered one launch each, in order, by a loop inside the library: each is
+ * shw_render(&item.vol, NULL, &item.cam, p with mode = item.mode, item.out_rgba, NULL, NULL,
+ * NULL, NULL, 0, stream).  The unbatched path a plan is measured against (no host language
+ * overhead between launches).  Returns the first non-OK status (earlier items stay enqueued). */
+shw_status shw_render_items(const shw_batch_item *items, int32_t n, const shw_render_params *p, void *stream);
 
 /* Waits for the device to finish outstanding work, then frees the plan. */
 shw_status shw_batch_plan_destroy(shw_batch_plan *plan);

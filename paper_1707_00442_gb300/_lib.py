@@ -17,7 +17,8 @@ SHW_OK, SHW_EINVAL, SHW_EUNSUPPORTED, SHW_ECUDA, SHW_ENOMEM, SHW_ETIMEOUT, SHW_E
 MODES = {"mip": 0, "avg": 1, "composite": 2, "spectral": 3, "ratio": 4, "moment1": 5,
          "composite_spectral": 6, "mip_rgb": 7, "composite_rgb": 8, "ratio_mip": 9}
 INTERP = {"nearest": 0, "trilinear": 1}
-STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "pair": 3, "bf16_pair": 4, "f16_pair": 5}
+STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "pair": 3, "bf16_pair": 4, "f16_pair": 5, "bf16_linear": 6,
+           "f16_linear": 7, "bf16_linear_pair": 8, "f16_linear_pair": 9}
 ABI_VERSION = 4
 LUT_SIZE = 256
 MAX_SMOOTH_RADIUS = 16
@@ -97,13 +98,14 @@ SIGNATURES = {
     "shw_batch_plan_destroy": (_i32, [_vp]),
     "shw_render_batch_noalloc": (_i32, [_P(BatchItem), _i32, _P(RenderParams), _vp]),
     "shw_set_debug_flags": (C.c_uint32, [C.c_uint32]),
+    "shw_render_items": (_i32, [_P(BatchItem), _i32, _P(RenderParams), _vp]),
     "shw_linear_sampling_taps": (_i32, [_P(C.c_double), _i32, _P(C.c_double), _P(C.c_double), _P(C.c_double), _i32,
                                         _P(_i32)]),
     "shw_binomial_taps": (_i32, [_i32, _i32, _P(C.c_double), _P(C.c_double), _P(C.c_double), _i32, _P(_i32)]),
 }
 # test and diagnosis switches of shw_set_debug_flags
 DEBUG = {"no_axis_sweep": 0x1, "smooth_plain": 0x2, "box_direct": 0x4, "no_staging": 0x8, "fault_alloc": 0x10,
-         "fault_graph": 0x20, "fault_timeout": 0x40}
+         "fault_graph": 0x20, "fault_timeout": 0x40, "require_staging": 0x80}
 NOALLOC_SCRATCH_BYTES = 8 << 20
 
 

@@ -35,12 +35,13 @@ def _need_cuda(t: torch.Tensor, name: str, dtype=None):
 
 @dataclass
 class BrickVolume:
-    """A cube packed by ``pack_bricks``: raw 16-bit bricks plus the cube's dims."""
+    """A cube packed by ``pack_bricks``: raw 16-bit values (bricks, or a linear 16-bit cube)
+    plus the cube's dims."""
     data: torch.Tensor   # int16, shw_bricked_bytes/2 elements
     nx: int
     ny: int
     nz: int
-    storage: str          # "bf16" | "f16"
+    storage: str          # a key of STORAGE other than "f32" and "pair"
 
     @property
     def shape(self):
@@ -200,9 +201,11 @@ def bricked_bytes(dims, storage="bf16") -> int:
 
 
 def pack_bricks(cube: torch.Tensor, storage: str = "bf16") -> BrickVolume:
-    """Round a float32 cube to bf16/f16 32^3 bricks with a 1-voxel apron (shw_pack_bricks).
-    A [nz, ny, nx, 2] pair buffer (the line ratios' storage) packs into pair bricks, both
-    cubes' 16-bit values in one 32-bit element (storage "bf16_pair" / "f16_pair")."""
+    """Round a float32 cube to a 16-bit storage (shw_pack_bricks): "bf16" / "f16" are 32^3
+    bricks with a 1-voxel apron, "bf16_linear" / "f16_linear" the linear [nz, ny, nx] cube the
+    staged marcher copies boxes from.  A [nz, ny, nx, 2] pair buffer (the line ratios'
+    storage) packs into the pair form of the same storage, both cubes' 16-bit values in one
+    32-bit element ("bf16_pair", "bf16_linear_pair", ...)."""
     _need_cuda(cube, "cube", torch.float32)
     if cube.dim() == 4 and cube.shape[3] == 2:
         nz, ny, nx, _ = cube.shape
@@ -320,6 +323,14 @@ class BatchPlan:
         check(lib().shw_batch_plan_create(C.byref(handle), arr, len(items), C.byref(p), flags, _stream()),
               "shw_batch_plan_create")
         self._plan = handle
+        self._items, self._params = arr, p
+
+    def render_one_by_one(self) -> list:
+        """The same images with one launch per item, looped inside the library
+        (shw_render_items): the unbatched path the plan is measured against."""
+        check(lib().shw_render_items(self._items, len(self._items), C.byref(self._params), _stream()),
+              "shw_render_items")
+        return self.outputs
 
     def render(self) -> list:
         check(lib().shw_render_batch(self._plan, _stream()), "shw_render_batch")

@@ -92,7 +92,7 @@ int sm_count()
     return n;
 }
 
-bool encode_tmap_3d_f32(CUtensorMap *map, const float *base, int nx, int ny, int nz, int bx, int by)
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
@@ -105,6 +105,34 @@ bool encode_tmap_3d_f32(CUtensorMap *map, const float *base, int nx, int ny, int
             fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
         cudaGetLastError();
     });
+    return fn;
+}
+
+bool encode_tmap_3d(CUtensorMap *map, const void *base, int elem_bytes, int nx, int ny, int nz, int bx, int by,
+                    int bz)
+{
+    const auto fn = tmap_encoder();
+    if (!fn) return false;
+    CUtensorMapDataType dt;
+    switch (elem_bytes) {
+    case 2: dt = CU_TENSOR_MAP_DATA_TYPE_UINT16; break;
+    case 4: dt = CU_TENSOR_MAP_DATA_TYPE_UINT32; break;
+    case 8: dt = CU_TENSOR_MAP_DATA_TYPE_UINT64; break;
+    default: return false;
+    }
+    const cuuint64_t eb = (cuuint64_t)elem_bytes;
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * eb, (cuuint64_t)nx * ny * eb};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, dt, 3, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+bool encode_tmap_3d_f32(CUtensorMap *map, const float *base, int nx, int ny, int nz, int bx, int by)
+{
+    const auto fn = tmap_encoder();
     if (!fn) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
     const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
@@ -121,10 +149,13 @@ static bool finite3(const float v[3]) { return std::isfinite(v[0]) && std::isfin
 bool valid_volume(const shw_volume *v)
 {
     if (!v || !v->data || v->nx <= 0 || v->ny <= 0 || v->nz <= 0) return false;
-    if (v->storage < SHW_F32 || v->storage > SHW_F16_PAIR_BRICK) return false;
+    if (v->storage < SHW_F32 || v->storage > SHW_F16_PAIR) return false;
     if (v->storage == SHW_F32 && !aligned(v->data, 4)) return false;
     if (v->storage == SHW_F32_PAIR && !aligned(v->data, 8)) return false;
-    if (v->storage >= SHW_BF16_PAIR_BRICK && !aligned(v->data, 4)) return false;
+    if ((v->storage == SHW_BF16_PAIR_BRICK || v->storage == SHW_F16_PAIR_BRICK || v->storage == SHW_BF16_PAIR ||
+         v->storage == SHW_F16_PAIR) &&
+        !aligned(v->data, 4))
+        return false;
     if (!aligned(v->data, 2)) return false;
     return true;
 }
@@ -264,7 +295,10 @@ shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_c
     if ((out_scalar && !aligned(out_scalar, 4)) || (out_index && !aligned(out_index, 4)) ||
         (out_nsamples && !aligned(out_nsamples, 4)))
         return SHW_EINVAL;
-    const bool pair = vol->storage >= SHW_F32_PAIR;  // both cubes in one volume
+    const int sto = vol->storage;
+    const bool pair = sto == SHW_F32_PAIR || sto == SHW_BF16_PAIR_BRICK || sto == SHW_F16_PAIR_BRICK ||
+                      sto == SHW_BF16_PAIR || sto == SHW_F16_PAIR;  // both cubes in one volume
+    const bool lin16 = sto >= SHW_BF16 && sto <= SHW_F16_PAIR;  // read by the staged marcher only
     if (pair) {
         // both cubes in one volume: the line ratios only, no second volume, no in-ray smoothing
         if (vol2) return SHW_EINVAL;
@@ -327,8 +361,14 @@ shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_c
     const shw_volume *v2 = (!pair && (p->mode == SHW_RATIO || p->mode == SHW_RATIO_MIP)) ? vol2 : nullptr;
     cudaStream_t st = as_stream(stream);
     // a captured launch would keep the work counter it was given while later calls reuse it
-    if (capturing(st)) return SHW_EUNSUPPORTED;
-    if (pair) return render_pair(p->mode, p->interp, *vol, *cam, a, st);
+    const int cs = capture_state(st);
+    if (cs != 0) return cs > 0 ? SHW_EUNSUPPORTED : SHW_ECUDA;
+    if (lin16) return render_slab(p->mode, p->interp, *vol, *cam, a, st);
+    if (pair) {
+        const shw_status ss = render_slab(p->mode, p->interp, *vol, *cam, a, st);
+        if (ss != SHW_EUNSUPPORTED || debug(SHW_DEBUG_REQUIRE_STAGING)) return ss;
+        return render_pair(p->mode, p->interp, *vol, *cam, a, st);
+    }
     if (a.box_lattice == 2)
         return vol->storage == SHW_F32 ? render_smooth_lat_f32(p->mode, p->interp, *vol, *cam, a, st)
                                        : render_smooth_lat_b16(p->mode, p->interp, *vol, *cam, a, st);
@@ -338,6 +378,11 @@ shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_c
     // orthographic views down the spectral axis: the plane sweep, when it applies
     const shw_status sa = render_axis(p->mode, p->interp, *vol, *cam, a, st);
     if (sa != SHW_EUNSUPPORTED) return sa;
+    // other views of a float32 cube: the staged marcher, when it applies
+    if (sto == SHW_F32) {
+        const shw_status ss = render_slab(p->mode, p->interp, *vol, *cam, a, st);
+        if (ss != SHW_EUNSUPPORTED || debug(SHW_DEBUG_REQUIRE_STAGING)) return ss;
+    }
     switch (vol->storage) {
     case SHW_F32: return render_f32(p->mode, p->interp, *vol, v2, *cam, a, st);
     case SHW_BF16_BRICK: return render_bf16(p->mode, p->interp, *vol, v2, *cam, a, st);

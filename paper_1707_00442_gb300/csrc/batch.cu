@@ -409,6 +409,19 @@ shw_status shw_render_batch(shw_batch_plan *plan, void *stream)
     return SHW_OK;
 }
 
+shw_status shw_render_items(const shw_batch_item *items, int32_t n, const shw_render_params *p, void *stream)
+{
+    if (!items || n <= 0 || !p) return SHW_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        shw_render_params q = *p;
+        q.mode = items[i].mode;
+        const shw_status s = shw_render(&items[i].vol, nullptr, &items[i].cam, &q, items[i].out_rgba, nullptr, nullptr,
+                                        nullptr, nullptr, 0, stream);
+        if (s != SHW_OK) return s;
+    }
+    return SHW_OK;
+}
+
 shw_status shw_batch_plan_info(const shw_batch_plan *plan, shw_batch_info *info)
 {
     if (!plan || !info) return SHW_EINVAL;
@@ -484,7 +497,8 @@ extern "C" shw_status shw_render_batch_noalloc(const shw_batch_item *items, int3
 
     // the table below is copied from host memory this call owns only while it runs, so a
     // capture (whose replays would read it after the call returned) is refused
-    if (capturing(as_stream(stream))) return SHW_EUNSUPPORTED;
+    const int cs = capture_state(as_stream(stream));
+    if (cs != 0) return cs > 0 ? SHW_EUNSUPPORTED : SHW_ECUDA;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();

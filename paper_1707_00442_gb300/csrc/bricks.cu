@@ -65,6 +65,37 @@ __global__ void __launch_bounds__(256) pack_pair_kernel(const float2 *__restrict
     }
 }
 
+// Linear 16-bit storages: element v = voxel v, rounded; four voxels per thread and step
+// (16-byte loads, 8-byte stores) where the count allows, then the remainder.
+template <typename T>
+__global__ void __launch_bounds__(256) convert_kernel(const float *__restrict__ in, unsigned short *__restrict__ out,
+                                                      long long n, bool vec)
+{
+    const long long n4 = vec ? n / 4 : 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    for (long long i = i0; i < n4; i += stride) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(in) + i);
+        ushort4 o;
+        o.x = round_store<T>(v.x);
+        o.y = round_store<T>(v.y);
+        o.z = round_store<T>(v.z);
+        o.w = round_store<T>(v.w);
+        reinterpret_cast<ushort4 *>(out)[i] = o;
+    }
+    for (long long i = 4 * n4 + i0; i < n; i += stride) out[i] = round_store<T>(__ldg(in + i));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) convert_pair_kernel(const float2 *__restrict__ in, unsigned *__restrict__ out,
+                                                           long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float2 v = __ldg(in + i);
+        out[i] = (unsigned)round_store<T>(v.x) | ((unsigned)round_store<T>(v.y) << 16);
+    }
+}
+
 }  // namespace shw
 
 using namespace shw;
@@ -74,6 +105,9 @@ extern "C" {
 size_t shw_bricked_bytes(int32_t nx, int32_t ny, int32_t nz, int32_t storage)
 {
     if (nx <= 0 || ny <= 0 || nz <= 0) return 0;
+    const size_t nvox = (size_t)nx * ny * nz;
+    if (storage == SHW_BF16 || storage == SHW_F16) return 2 * nvox;
+    if (storage == SHW_BF16_PAIR || storage == SHW_F16_PAIR) return 4 * nvox;
     const bool pair = storage == SHW_BF16_PAIR_BRICK || storage == SHW_F16_PAIR_BRICK;
     if (storage != SHW_BF16_BRICK && storage != SHW_F16_BRICK && !pair) return 0;
     const size_t nb = (size_t)ceil_div(nx, kBrick) * ceil_div(ny, kBrick) * ceil_div(nz, kBrick);
@@ -84,6 +118,33 @@ shw_status shw_pack_bricks(const float *in, int32_t nx, int32_t ny, int32_t nz, 
                            size_t out_bytes, void *stream)
 {
     if (!in || !out || nx <= 0 || ny <= 0 || nz <= 0 || !aligned(in, 4) || !aligned(out, 2)) return SHW_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    if (storage >= SHW_BF16 && storage <= SHW_F16_PAIR) {
+        // linear 16-bit storages: a plain element-wise rounding
+        const bool lpair = storage >= SHW_BF16_PAIR;
+        if (lpair && (!aligned(in, 8) || !aligned(out, 4))) return SHW_EINVAL;
+        if (out_bytes < shw_bricked_bytes(nx, ny, nz, storage)) return SHW_ENOMEM;
+        const long long n = (long long)nx * ny * nz;
+        const bool vec = !lpair && aligned(in, 16) && aligned(out, 8);
+        long long blocks = ((vec ? n / 4 + 3 : n) + 255) / 256;
+        if (blocks > 152LL * 64) blocks = 152LL * 64;
+        if (blocks < 1) blocks = 1;
+        if (lpair) {
+            const float2 *ip = reinterpret_cast<const float2 *>(in);
+            auto *op = static_cast<unsigned *>(out);
+            if (storage == SHW_BF16_PAIR)
+                convert_pair_kernel<__nv_bfloat16><<<(unsigned)blocks, 256, 0, st>>>(ip, op, n);
+            else
+                convert_pair_kernel<__half><<<(unsigned)blocks, 256, 0, st>>>(ip, op, n);
+        } else {
+            auto *o = static_cast<unsigned short *>(out);
+            if (storage == SHW_BF16)
+                convert_kernel<__nv_bfloat16><<<(unsigned)blocks, 256, 0, st>>>(in, o, n, vec);
+            else
+                convert_kernel<__half><<<(unsigned)blocks, 256, 0, st>>>(in, o, n, vec);
+        }
+        return after_launch();
+    }
     const bool pair = storage == SHW_BF16_PAIR_BRICK || storage == SHW_F16_PAIR_BRICK;
     if (storage != SHW_BF16_BRICK && storage != SHW_F16_BRICK && !pair) return SHW_EINVAL;
     if (pair && (!aligned(in, 8) || !aligned(out, 4))) return SHW_EINVAL;
@@ -93,7 +154,6 @@ shw_status shw_pack_bricks(const float *in, int32_t nx, int32_t ny, int32_t nz, 
     const int nbx = ceil_div(nx, kBrick), nby = ceil_div(ny, kBrick);
     long long blocks = (total + 255) / 256;
     if (blocks > 152LL * 64) blocks = 152LL * 64;  // grid-stride beyond 64 CTAs per SM
-    cudaStream_t st = as_stream(stream);
     if (pair) {
         const float2 *ip = reinterpret_cast<const float2 *>(in);
         auto *op = static_cast<unsigned *>(out);

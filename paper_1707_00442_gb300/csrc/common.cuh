@@ -15,15 +15,15 @@ void note_launch();
 uint32_t debug_flags();
 inline bool debug(uint32_t flag) { return (debug_flags() & flag) != 0u; }
 
-// True if `st` is being captured into a CUDA graph (or its state cannot be read).
-inline bool capturing(cudaStream_t st)
+// Whether `st` is being captured into a CUDA graph: 1 yes, 0 no, -1 the runtime cannot say.
+inline int capture_state(cudaStream_t st)
 {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
         cudaGetLastError();
-        return true;
+        return -1;
     }
-    return cs != cudaStreamCaptureStatusNone;
+    return cs != cudaStreamCaptureStatusNone ? 1 : 0;
 }
 
 inline shw_status cuda_status(cudaError_t e) { return e == cudaSuccess ? SHW_OK : SHW_ECUDA; }

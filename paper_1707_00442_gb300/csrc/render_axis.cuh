@@ -56,19 +56,6 @@ constexpr int kFixStride = (kFixBW * kFixBH + 31) & ~31;  // floats per stage, 1
 constexpr int kAxWaitPolls = 1 << 20;
 constexpr uint32_t kAxSleepNs = 1000;
 
-// MIP when no argmax is wanted: the running maximum alone.  A NaN sample has already
-// been replaced by DATAMIN, so fmaxf sees numbers only and gives the same value as the
-// ordered >= update (the two can differ only in the sign of a zero maximum).
-constexpr int kMipValue = 16;
-struct MaxValState {
-    float m = -INFINITY;
-    int kmax = 0;
-    __device__ __forceinline__ bool update(float v, int)
-    {
-        m = fmaxf(m, v);
-        return false;
-    }
-};
 template <int MODE>
 struct AxisStateOf {
     using type = typename StateOf<MODE>::type;

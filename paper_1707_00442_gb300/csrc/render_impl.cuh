@@ -368,6 +368,20 @@ struct MaxState {
     }
 };
 
+// MIP when no channel (argmax) output is wanted: the running maximum alone.  A NaN sample
+// has already been replaced by DATAMIN, so fmaxf sees numbers only and gives the same value
+// as the ordered >= update (the two can differ only in the sign of a zero maximum).
+constexpr int kMipValue = 16;
+struct MaxValState {
+    float m = -INFINITY;
+    int kmax = 0;
+    __device__ __forceinline__ bool update(float v, int)
+    {
+        m = fmaxf(m, v);
+        return false;
+    }
+};
+
 // Eq. 3 divided by N; compensated (Kahan) summation keeps FP32 accurate
 struct AvgState {
     float sum = 0.0f, comp = 0.0f;
@@ -491,6 +505,10 @@ struct StateOf {
 template <>
 struct StateOf<SHW_MOMENT1> {
     using type = MomentState;
+};
+template <>
+struct StateOf<kMipValue> {
+    using type = MaxValState;
 };
 template <>
 struct StateOf<SHW_AVG> {
@@ -698,7 +716,7 @@ __device__ __forceinline__ void emit_ray(const RenderArgs &a, long long pix, int
     float scalar = 0.0f;
     int index = -1;
     if (N > 0) {
-        if constexpr (MODE == SHW_MIP || MODE == SHW_SPECTRAL || MODE == SHW_RATIO) {
+        if constexpr (MODE == SHW_MIP || MODE == kMipValue || MODE == SHW_SPECTRAL || MODE == SHW_RATIO) {
             const long long Zm = PZ + (long long)st.kmax * DZ;
             index = clampi(fx_round(Zm), 0, a.nz - 1);
             scalar = st.m;
@@ -757,6 +775,45 @@ __device__ __forceinline__ void emit_ray(const RenderArgs &a, long long pix, int
     if (a.nsamples) a.nsamples[pix] = done;
 }
 
+// The transfer-function state of one ray before its first sample (Algorithm 1's "init
+// vars"): the colour map, opacity scale and checkpoint slots of compositing, the first
+// sample's position for the position-coloured modes and the first moment.
+template <int MODE, int INTERP, class St, class S>
+__device__ __forceinline__ void init_ray_state(St &st, const S &s, const RenderArgs &a, const RayFx &r, long long pix,
+                                               const float4 *lut_c)
+{
+    if constexpr (is_composite<MODE>) {
+        st.lut = lut_c;
+        st.lo = a.lo;
+        st.inv_range = a.inv_range;
+        st.s = a.opacity_scale;
+        st.term = a.term_alpha;
+        st.ckpt = a.ckpt_T != nullptr ? a.ckpt_T + pix : nullptr;
+        st.ckpt_stride = (long long)a.width * a.height;
+        st.I = a.ckpt_interval;
+        st.nckpt = a.nckpt;
+        if constexpr (MODE != SHW_COMPOSITE) {
+            st.X = r.P[0];
+            st.Y = r.P[1];
+            st.Z = r.P[2];
+            st.DX = r.D[0];
+            st.DY = r.D[1];
+            st.DZ = r.D[2];
+            st.nx = s.nx;
+            st.ny = s.ny;
+            st.nz = s.nz;
+            st.nearest = INTERP == SHW_NEAREST;
+        }
+    }
+    if constexpr (MODE == SHW_MOMENT1) {
+        st.Z = r.P[2];
+        st.DZ = r.D[2];
+        st.lo = a.lo;
+        st.nz = a.nz;
+        st.nearest = INTERP == SHW_NEAREST;
+    }
+}
+
 // One ray of Algorithm 1 with the transfer function MODE.  lut_c: the colour map in
 // shared memory (read per sample by COMPOSITE); a.lut: the same map in global memory.
 // SMK: 0 no in-ray smoothing; 1 smoothing by direct fetches; 2 the box on the sample lattice
@@ -766,7 +823,6 @@ __device__ __forceinline__ void render_pixel(const S &s, const S &s2, const shw_
                                              const float4 *lut_c, int px, int py)
 {
     const long long pix = (long long)py * a.width + px;
-    const long long npix = (long long)a.width * a.height;
 
     RayFx r;
     const bool hit = !quick_miss(cam, px, py, s.nx, s.ny, s.nz) && setup_ray(cam, px, py, s.nx, s.ny, s.nz, a.step, r);
@@ -779,36 +835,7 @@ __device__ __forceinline__ void render_pixel(const S &s, const S &s2, const shw_
         interior_range(r, s.nx, s.ny, s.nz, N, ka, kb);
         long long X = r.P[0], Y = r.P[1], Z = r.P[2];
         const long long DX = r.D[0], DY = r.D[1], DZ = r.D[2];
-        if constexpr (is_composite<MODE>) {
-            st.lut = lut_c;
-            st.lo = a.lo;
-            st.inv_range = a.inv_range;
-            st.s = a.opacity_scale;
-            st.term = a.term_alpha;
-            st.ckpt = a.ckpt_T != nullptr ? a.ckpt_T + pix : nullptr;
-            st.ckpt_stride = npix;
-            st.I = a.ckpt_interval;
-            st.nckpt = a.nckpt;
-            if constexpr (MODE != SHW_COMPOSITE) {
-                st.X = r.P[0];
-                st.Y = r.P[1];
-                st.Z = r.P[2];
-                st.DX = r.D[0];
-                st.DY = r.D[1];
-                st.DZ = r.D[2];
-                st.nx = s.nx;
-                st.ny = s.ny;
-                st.nz = s.nz;
-                st.nearest = INTERP == SHW_NEAREST;
-            }
-        }
-        if constexpr (MODE == SHW_MOMENT1) {
-            st.Z = r.P[2];
-            st.DZ = r.D[2];
-            st.lo = a.lo;
-            st.nz = a.nz;
-            st.nearest = INTERP == SHW_NEAREST;
-        }
+        init_ray_state<MODE, INTERP>(st, s, a, r, pix, lut_c);
         CacheOf<S> cc, cc2;
         if constexpr (SMK == 2) {
             march_box_lattice<2, MODE, INTERP>(s, a, st, r.P, r.D, N, done);
@@ -1047,6 +1074,9 @@ shw_status render_bf16_big(int mode, int interp, const shw_volume &v, const shw_
                            const RenderArgs &a, cudaStream_t st);
 shw_status render_f16_big(int mode, int interp, const shw_volume &v, const shw_volume *v2, const shw_camera &cam,
                           const RenderArgs &a, cudaStream_t st);
+// the staged marcher (render_slab.cu); SHW_EUNSUPPORTED if it does not apply
+shw_status render_slab(int mode, int interp, const shw_volume &v, const shw_camera &cam, const RenderArgs &a,
+                       cudaStream_t st);
 // the plane sweep for orthographic spectral-axis views (render_axis.cu); SHW_EUNSUPPORTED if it does not apply
 shw_status render_axis(int mode, int interp, const shw_volume &v, const shw_camera &cam, const RenderArgs &a,
                        cudaStream_t st);

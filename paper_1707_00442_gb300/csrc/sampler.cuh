@@ -172,6 +172,78 @@ struct SamplerBrick {
     }
 };
 
+// Linear 16-bit cube [nz][ny][nx] (bfloat16 or binary16 raw values; fewer than 2^31
+// voxels): the layout the staged marcher copies boxes from.  Values widen to FP32 on load.
+template <typename T>
+struct SamplerLin16 {
+    static constexpr bool kLinearF32 = false;
+    static constexpr bool kPair = false;
+    const unsigned short *__restrict__ v;
+    int nx, ny, nz;
+    int sy, sz;  // strides of y and z in elements
+
+    template <bool CLAMP = true>
+    __device__ __forceinline__ float nearest(long long X, long long Y, long long Z) const
+    {
+        int x = fx_round(X), y = fx_round(Y), z = fx_round(Z);
+        if (CLAMP) {
+            x = clampi(x, 0, nx - 1);
+            y = clampi(y, 0, ny - 1);
+            z = clampi(z, 0, nz - 1);
+        }
+        return to_f32<T>(__ldg(v + (z * sz + y * sy + x)));
+    }
+
+    // corners of the cell with base (ix, iy, iz); CLAMP: each index in [-1, n-1]
+    template <bool CLAMP = true>
+    __device__ __forceinline__ void corners(int ix, int iy, int iz, float c[8]) const
+    {
+        int x0 = ix, y0 = iy, z0 = iz, dx = 1, dy = sy, dz = sz;
+        if (CLAMP) {
+            x0 = max(ix, 0);
+            y0 = max(iy, 0);
+            z0 = max(iz, 0);
+            dx = min(ix + 1, nx - 1) - x0;
+            dy = (min(iy + 1, ny - 1) - y0) * sy;
+            dz = (min(iz + 1, nz - 1) - z0) * sz;
+        }
+        const unsigned short *p00 = v + (z0 * sz + y0 * sy + x0);
+        const unsigned short *p01 = p00 + dy, *p10 = p00 + dz, *p11 = p10 + dy;
+        c[0] = to_f32<T>(__ldg(p00));
+        c[1] = to_f32<T>(__ldg(p00 + dx));
+        c[2] = to_f32<T>(__ldg(p01));
+        c[3] = to_f32<T>(__ldg(p01 + dx));
+        c[4] = to_f32<T>(__ldg(p10));
+        c[5] = to_f32<T>(__ldg(p10 + dx));
+        c[6] = to_f32<T>(__ldg(p11));
+        c[7] = to_f32<T>(__ldg(p11 + dx));
+    }
+
+    __device__ __forceinline__ float trilinear(long long X, long long Y, long long Z) const
+    {
+        float c[8];
+        corners<true>(cell_of<true>(X, nx), cell_of<true>(Y, ny), cell_of<true>(Z, nz), c);
+        return trilerp(c, fx_frac(X), fx_frac(Y), fx_frac(Z));
+    }
+};
+
+// The two cubes of a line ratio in one linear 16-bit pair buffer: 32-bit elements
+// [nz][ny][nx], low half the first cube.
+template <typename T>
+struct SamplerLin16Pair {
+    static constexpr bool kLinearF32 = false;
+    static constexpr bool kPair = true;
+    const unsigned *__restrict__ v;
+    int nx, ny, nz;
+    int sy, sz;
+
+    template <bool CLAMP = true>
+    __device__ __forceinline__ float2 nearest2(long long X, long long Y, long long Z) const;  // (not instanced)
+
+    template <bool CLAMP = true>
+    __device__ __forceinline__ void corners2(int ix, int iy, int iz, float2 c[8]) const;
+};
+
 // The two cubes of a line ratio interleaved, float2 [nz][ny][nx]: (first, second) per voxel.
 // One 8-byte load fetches a corner of both cubes; the interpolation runs on the pairs with
 // packed FP32x2 lerps in the single-cube order, so each cube's value is bit-identical to
@@ -242,6 +314,44 @@ __device__ __forceinline__ float2 pair_to_f32<__half>(unsigned w)
 {
     return __half22float2(__halves2half2(__ushort_as_half((unsigned short)(w & 0xffffu)),
                                          __ushort_as_half((unsigned short)(w >> 16))));
+}
+
+template <typename T>
+template <bool CLAMP>
+__device__ __forceinline__ float2 SamplerLin16Pair<T>::nearest2(long long X, long long Y, long long Z) const
+{
+    int x = fx_round(X), y = fx_round(Y), z = fx_round(Z);
+    if (CLAMP) {
+        x = clampi(x, 0, nx - 1);
+        y = clampi(y, 0, ny - 1);
+        z = clampi(z, 0, nz - 1);
+    }
+    return pair_to_f32<T>(__ldg(v + (z * sz + y * sy + x)));
+}
+
+template <typename T>
+template <bool CLAMP>
+__device__ __forceinline__ void SamplerLin16Pair<T>::corners2(int ix, int iy, int iz, float2 c[8]) const
+{
+    int x0 = ix, y0 = iy, z0 = iz, dx = 1, dy = sy, dz = sz;
+    if (CLAMP) {
+        x0 = max(ix, 0);
+        y0 = max(iy, 0);
+        z0 = max(iz, 0);
+        dx = min(ix + 1, nx - 1) - x0;
+        dy = (min(iy + 1, ny - 1) - y0) * sy;
+        dz = (min(iz + 1, nz - 1) - z0) * sz;
+    }
+    const unsigned *p00 = v + (z0 * sz + y0 * sy + x0);
+    const unsigned *p01 = p00 + dy, *p10 = p00 + dz, *p11 = p10 + dy;
+    c[0] = pair_to_f32<T>(__ldg(p00));
+    c[1] = pair_to_f32<T>(__ldg(p00 + dx));
+    c[2] = pair_to_f32<T>(__ldg(p01));
+    c[3] = pair_to_f32<T>(__ldg(p01 + dx));
+    c[4] = pair_to_f32<T>(__ldg(p10));
+    c[5] = pair_to_f32<T>(__ldg(p10 + dx));
+    c[6] = pair_to_f32<T>(__ldg(p11));
+    c[7] = pair_to_f32<T>(__ldg(p11 + dx));
 }
 
 // The pair storage as 32^3 bricks with the 1-voxel apron (layout of SamplerBrick), each

@@ -110,4 +110,10 @@ unsigned *device_error_word();
 // out-of-bounds elements of a box read as zero.  Returns false if the driver refuses.
 bool encode_tmap_3d_f32(CUtensorMap *map, const float *base, int nx, int ny, int nz, int bx, int by);
 
+// host: a 3-D tile map over [nz][ny][nx] elements of elem_bytes (2, 4 or 8; copied as raw
+// bits) with box {bx, by, bz}; out-of-bounds elements of a box read as zero.  nx * elem_bytes
+// must be a multiple of 16 and base 16-byte aligned.  False if the driver refuses.
+bool encode_tmap_3d(CUtensorMap *map, const void *base, int elem_bytes, int nx, int ny, int nz, int bx, int by,
+                    int bz);
+
 }  // namespace shw

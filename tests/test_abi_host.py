@@ -94,7 +94,8 @@ def test_render_rejects_invalid_arguments_on_host(L):
         (None, ok_c, ok_p, out),
         (_vol(data=0), ok_c, ok_p, out),
         (_vol(n=(0, 8, 8)), ok_c, ok_p, out),
-        (_vol(storage=7), ok_c, ok_p, out),
+        (_vol(storage=10), ok_c, ok_p, out),          # no such storage
+        (_vol(data=0x1002, storage=8), ok_c, ok_p, out),  # linear 16-bit pairs need 4-byte alignment
         (_vol(data=0x1001), ok_c, ok_p, out),       # misaligned float32 cube
         (ok_v, _cam(W=0), ok_p, out),
         (ok_v, _cam(H=-3), ok_p, out),
@@ -156,7 +157,12 @@ def test_pair_storage_rules_on_host(L):
     assert L.shw_smooth_zip(0x100000, 0x100000, 0x200000, 8, 8, 8, 1.0, 17, None) == EUNSUP
     # pair bricks: 4-byte elements, an 8-byte aligned float32 pair buffer in, line ratios only
     assert L.shw_bricked_bytes(64, 64, 64, 4) == L.shw_bricked_bytes(64, 64, 64, 5) == 8 * 34 ** 3 * 4
-    assert L.shw_bricked_bytes(64, 64, 64, 6) == 0
+    assert L.shw_bricked_bytes(64, 64, 64, 10) == 0
+    # linear 16-bit storages: 2 bytes per voxel, 4 for the pairs
+    assert L.shw_bricked_bytes(64, 64, 64, 6) == L.shw_bricked_bytes(64, 64, 64, 7) == 2 * 64 ** 3
+    assert L.shw_bricked_bytes(64, 64, 64, 8) == L.shw_bricked_bytes(64, 64, 64, 9) == 4 * 64 ** 3
+    assert L.shw_pack_bricks(0x100004, 64, 64, 64, 8, 0x800000, 1 << 30, None) == EINVAL  # pair input 8-aligned
+    assert L.shw_pack_bricks(0x100000, 64, 64, 64, 6, 0x800000, 1000, None) == 4          # ENOMEM
     assert L.shw_pack_bricks(0x100004, 64, 64, 64, 4, 0x800000, 1 << 30, None) == EINVAL  # pair input 8-aligned
     assert L.shw_pack_bricks(0x100000, 64, 64, 64, 4, 0x800002, 1 << 30, None) == EINVAL  # 4-byte elements
     assert L.shw_pack_bricks(0x100000, 64, 64, 64, 5, 0x800000, 1000, None) == 4          # ENOMEM
@@ -165,8 +171,13 @@ def test_pair_storage_rules_on_host(L):
                             None) == EUNSUP
         assert L.shw_render(b(_vol(storage=st, data=0x1002)), None, b(ok_c), b(_params(mode=4)), out, None, None,
                             None, None, 0, None) == EINVAL
-    assert L.shw_render(b(_vol(storage=6)), None, b(ok_c), b(_params(mode=4)), out, None, None, None, None, 0,
+    assert L.shw_render(b(_vol(storage=10)), None, b(ok_c), b(_params(mode=4)), out, None, None, None, None, 0,
                         None) == EINVAL
+    # linear 16-bit pairs: the line ratios only; linear 16-bit cubes: the staged marcher only
+    # (trilinear, no in-ray smoothing), refused before any launch
+    for st in (8, 9):
+        assert L.shw_render(b(_vol(storage=st)), None, b(ok_c), b(_params(mode=0)), out, None, None, None, None, 0,
+                            None) == EUNSUP
 
 
 def test_smooth_and_pack_reject_invalid_arguments_on_host(L):

@@ -129,3 +129,20 @@ def test_batch_survey_shaped(m):
         single = m.render(vol, cam, mode, lut=lut, opacity_scale=0.02)["rgba"]
         assert torch.equal(outs[j], single)
     plan.close()
+
+
+def test_render_items_equals_plan(m):
+    """One launch per item from the library's own loop (shw_render_items), the path a plan is
+    measured against, gives the plan's images bit for bit."""
+    items = _batch(n=10, storage_cycle=("f32", "bf16"), modes=("mip", "composite"))
+    lut = to_dev(scene.linear_lut())
+    dev = _dev_items(m, items)
+    plan = m.BatchPlan(dev, lut=lut, opacity_scale=0.05, tune=False)
+    a = [o.clone() for o in plan.render()]
+    for o in plan.outputs:
+        o.fill_(-1.0)
+    b = plan.render_one_by_one()
+    m.sync_status()
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    plan.close()

@@ -115,6 +115,27 @@ def test_survey_step_ratio_on_pair_storage(m, survey, pixels):
     print("ratio-pair", st)
 
 
+@pytest.mark.parametrize("mode", W.MODES)
+def test_survey_staged_equals_gather(m, survey, mode):
+    """The benchmark's renders through the staged marcher (the line ratio on the pair storage)
+    equal the gather marcher's over the whole 1920 x 1080 image, bit for bit."""
+    cube, c2 = survey[0], survey[1]
+    cam = W.survey_camera()
+    lut = to_dev(scene.ratio_lut() if mode == "ratio" else scene.linear_lut())
+    vol = torch.stack([to_dev(cube), to_dev(c2)], dim=-1).contiguous() if mode == "ratio" else to_dev(cube)
+    kw = dict(W.MODE_PARAMS[mode], step=W.SURVEY["step"])
+    with m.debug_flags("require_staging"):
+        a = m.render(vol, cam, mode, lut=lut, **kw)
+        torch.cuda.synchronize()
+    with m.debug_flags("no_staging"):
+        b = m.render(vol, cam, mode, lut=lut, **kw)
+        torch.cuda.synchronize()
+    m.sync_status()
+    for k in a:
+        assert torch.equal(a[k], b[k]), (mode, k)
+    del vol
+
+
 @pytest.mark.parametrize("storage", ["bf16", "f16"])
 def test_survey_bricks_error_vs_fp64(m, survey, pixels, storage):
     """The reduced-precision path at full size: every mode rendered from 16-bit bricks of the
