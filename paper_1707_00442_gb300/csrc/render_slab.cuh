@@ -22,6 +22,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "render_impl.cuh"
 #include "tma.cuh"
@@ -50,7 +51,8 @@ struct SlabHdr {
     int ox, oy, oz;     // cell coordinates of the staged box's first element
     int ex1, ey1, ez1;  // a cell c is staged with c + 1 when (unsigned)(c - o) < e1 on every axis
     int sy, sz;         // element strides of y and z in the stage
-    int pad[2];
+    int wide;           // y- and z-major: the box rows are the wide chunk width (else the narrow one)
+    int pad;
 };
 static_assert(sizeof(SlabHdr) == 64, "stage header");
 
@@ -78,20 +80,23 @@ struct ElemHPair {
     __device__ __forceinline__ static float2 cvt(unsigned r) { return pair_to_f32<T>(r); }
 };
 
-// Chunk widths.  A chunk's rows lie one row pitch apart in the stage; a pitch of 40 words
-// (160 bytes; 28 words for 16-bit elements, 20 for the x-major chunks) puts 8 consecutive
-// rows on different shared-memory banks, so the lanes of a warp, whose rays cover a few
-// neighbouring rows, rarely collide.  Widths are 16-byte multiples and 8 rows a 128-byte
-// multiple, as the tensor copies require.
+// Chunk widths.  A chunk's rows lie one row pitch apart in the stage; pitches of 20, 28 and
+// 40 words put 8 consecutive rows on different shared-memory banks, so the lanes of a warp,
+// whose rays cover a few neighbouring rows, rarely collide.  y- and z-major slabs take the
+// narrow width when their footprint fits it, else the wide one (x-major: one width).  Widths
+// are 16-byte multiples and 8 rows a 128-byte multiple, as the tensor copies require.
 template <class EP>
 struct SlabGeom {
     static constexpr int kBytes = (int)sizeof(typename EP::raw);
-    static constexpr int kAlign = 16 / kBytes;                 // elements per 16 bytes (x alignment of a copy)
-    static constexpr int kBX = (kBytes == 2 ? 112 : 160) / kBytes;  // chunk width, y- and z-major
-    static constexpr int kBXx = 80 / kBytes;                   // chunk width, x-major
+    static constexpr int kAlign = 16 / kBytes;  // elements per 16 bytes (x alignment of a copy)
+    static constexpr int kBXn = (kBytes == 2 ? 80 : 112) / kBytes;   // narrow chunk width (elements)
+    static constexpr int kBXw = (kBytes == 2 ? 112 : 160) / kBytes;  // wide chunk width
+    static constexpr int kBXx = 80 / kBytes;                         // x-major chunk width
     static constexpr int kStageElems = kSlabStageBytes / kBytes;
-    static_assert((kBX * kBytes) % 16 == 0 && (kBXx * kBytes) % 16 == 0, "16-byte rows");
-    static_assert((kSlabRows * kBX * kBytes) % 128 == 0 && (kSlabRows * kBXx * kBytes) % 128 == 0,
+    static_assert((kBXn * kBytes) % 16 == 0 && (kBXw * kBytes) % 16 == 0 && (kBXx * kBytes) % 16 == 0,
+                  "16-byte rows");
+    static_assert((kSlabRows * kBXn * kBytes) % 128 == 0 && (kSlabRows * kBXw * kBytes) % 128 == 0 &&
+                      (kSlabRows * kBXx * kBytes) % 128 == 0,
                   "chunks start on 128 bytes");
 };
 
@@ -137,8 +142,10 @@ __device__ __forceinline__ TileRays tile_rays(const shw_camera &c, int px0, int 
     float s[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) s[k] = t.u[0][k] + t.u[1][k] + t.u[2][k] + t.u[3][k];
+    // y or z when either advances at least a quarter as fast as x: x-major boxes hold only a
+    // few x planes per chunk, so their slabs stay thin
     const float ax = fabsf(s[0]), ay = fabsf(s[1]), az = fabsf(s[2]);
-    t.major = (ax >= ay && ax >= az) ? 0 : (ay >= az ? 1 : 2);
+    t.major = ax > 4.0f * fmaxf(ay, az) ? 0 : (ay > az ? 1 : 2);
     const float sm = t.major == 0 ? s[0] : (t.major == 1 ? s[1] : s[2]);
     t.dir = sm > 0.0f ? 1 : -1;
     return t;
@@ -236,36 +243,39 @@ __device__ __forceinline__ SlabPlan plan_slab(const TileLines<M> &t, int dir, in
         h.ez1 = p.np - 1;
         h.sy = G::kBXx;
         h.sz = p.nc * kSlabRows * G::kBXx;
+        h.wide = 0;
     } else {
-        // y- or z-major: planes along the major axis, x within one chunk width, rows on the
-        // remaining axis (z for y-major, y for z-major)
-        constexpr int qmax = G::kStageElems / (kSlabRows * G::kBX);
+        // y- or z-major: planes along the major axis, x within one chunk width (narrow when
+        // the footprint fits it), rows on the remaining axis (z for y-major, y for z-major)
         constexpr int R = (M == 2) ? 1 : 2;
         int xlo, xhi, rlo, rhi;
         lateral_cells<M, 0>(t, m0, m1, nx, xlo, xhi);
         lateral_cells<M, R>(t, m0, m1, R == 1 ? ny : nz, rlo, rhi);
         p.empty = xlo > xhi || rlo > rhi;
         const int x0 = xlo & ~(G::kAlign - 1);
+        h.wide = xhi - x0 + 1 > G::kBXn;
+        const int bx = h.wide ? G::kBXw : G::kBXn;
+        const int qmax = G::kStageElems / (kSlabRows * bx);
         p.nc = (rhi - rlo + kSlabRows) / kSlabRows;
         p.np = c1 + 2 - c0;
         p.fits = p.np * p.nc <= qmax;
         if (!p.fits) p.nc = max(1, qmax / p.np);
         h.ox = x0;
-        h.ex1 = G::kBX - 1;
+        h.ex1 = bx - 1;
         if constexpr (M == 2) {
             h.oy = rlo;
             h.oz = c0;
             h.ey1 = p.nc * kSlabRows - 1;
             h.ez1 = p.np - 1;
-            h.sy = G::kBX;
-            h.sz = p.nc * kSlabRows * G::kBX;
+            h.sy = bx;
+            h.sz = p.nc * kSlabRows * bx;
         } else {
             h.oy = c0;
             h.oz = rlo;
             h.ey1 = p.np - 1;
             h.ez1 = p.nc * kSlabRows - 1;
-            h.sy = p.nc * kSlabRows * G::kBX;
-            h.sz = G::kBX;
+            h.sy = p.nc * kSlabRows * bx;
+            h.sz = bx;
         }
     }
     return p;
@@ -438,8 +448,9 @@ struct SlabRing {
 // its box clipped to a stage, when none fits), and empty runs are skipped.  False if a
 // wait gave up.
 template <class EP, int M>
-__device__ __forceinline__ bool produce_tile(const TileRays &r, bool persp, const CUtensorMap *map, const RenderArgs &a,
-                                             int tile, unsigned char *stages, SlabRing &ring)
+__device__ __forceinline__ bool produce_tile(const TileRays &r, bool persp, const CUtensorMap *map_n,
+                                             const CUtensorMap *map_w, const RenderArgs &a, int tile,
+                                             unsigned char *stages, SlabRing &ring)
 {
     using G = SlabGeom<EP>;
     TileLines<M> L;
@@ -455,7 +466,6 @@ __device__ __forceinline__ bool produce_tile(const TileRays &r, bool persp, cons
         else
             hi_c = min(hi_c, e);
     }
-    constexpr int chunk = kSlabRows * (M == 0 ? G::kBXx : G::kBX) * G::kBytes;  // bytes of one copy
     int cur = dir > 0 ? lo_c : hi_c;
     while (cur >= lo_c && cur <= hi_c) {
         const int len = lane + 1;
@@ -473,6 +483,9 @@ __device__ __forceinline__ bool produce_tile(const TileRays &r, bool persp, cons
         const int np = __shfl_sync(0xffffffffu, p.np, pick), nc = __shfl_sync(0xffffffffu, p.nc, pick);
         const int ox = __shfl_sync(0xffffffffu, p.h.ox, pick), oy = __shfl_sync(0xffffffffu, p.h.oy, pick);
         const int oz = __shfl_sync(0xffffffffu, p.h.oz, pick);
+        const bool wide = __shfl_sync(0xffffffffu, p.h.wide, pick) != 0;
+        const int chunk = kSlabRows * (M == 0 ? G::kBXx : (wide ? G::kBXw : G::kBXn)) * G::kBytes;  // bytes of one copy
+        const CUtensorMap *map = wide ? map_w : map_n;
         const int st = ring.take();
         if (st < 0) return false;
         if (lane == pick) {
@@ -503,9 +516,8 @@ __device__ __forceinline__ bool produce_tile(const TileRays &r, bool persp, cons
 // cross, front to back.  Every stage carries a header: a tile's start, one slab, a tile's
 // end, or the end of the launch.
 template <class EP>
-__device__ void slab_producer(const CUtensorMap *mapx, const CUtensorMap *mapy, const CUtensorMap *mapz,
-                              const shw_camera &cam, const RenderArgs &a, const SlabArgs &sa, unsigned char *stages,
-                              SlabShared &sh)
+__device__ void slab_producer(const CUtensorMap *maps, const shw_camera &cam, const RenderArgs &a, const SlabArgs &sa,
+                              unsigned char *stages, SlabShared &sh)
 {
     const int lane = threadIdx.x & 31;
     SlabRing ring{sh, sa};
@@ -523,12 +535,13 @@ __device__ void slab_producer(const CUtensorMap *mapx, const CUtensorMap *mapy, 
         slab_tile((int)t, a, tx, ty);
         const TileRays r = tile_rays(cam, tx * kSlabTW, ty * kSlabTH);
         const bool persp = !cam.ortho;
+        // maps: x-major; y-major narrow, wide; z-major narrow, wide
         if (r.major == 0)
-            ok = produce_tile<EP, 0>(r, persp, mapx, a, (int)t, stages, ring);
+            ok = produce_tile<EP, 0>(r, persp, &maps[0], &maps[0], a, (int)t, stages, ring);
         else if (r.major == 1)
-            ok = produce_tile<EP, 1>(r, persp, mapy, a, (int)t, stages, ring);
+            ok = produce_tile<EP, 1>(r, persp, &maps[1], &maps[2], a, (int)t, stages, ring);
         else
-            ok = produce_tile<EP, 2>(r, persp, mapz, a, (int)t, stages, ring);
+            ok = produce_tile<EP, 2>(r, persp, &maps[3], &maps[4], a, (int)t, stages, ring);
         if (ok) ok = ring.post_plain(kStageTileEnd, (int)t);
     }
     // the CTA may not exit while a tensor copy into its shared memory is in flight: wait
@@ -639,10 +652,14 @@ __device__ void slab_consumer(const S &s, const shw_camera &cam, const RenderArg
 
 // Persistent CTAs: a producer warp and kSlabWarps consumer warps; the ring of stages,
 // their headers and barriers in dynamic shared memory.
+// The tensor maps of one launch: x-major chunks; y-major narrow and wide; z-major narrow and wide.
+struct SlabMaps {
+    CUtensorMap m[5];
+};
+
 template <int MODE, class EP, class S>
 __global__ void __launch_bounds__(kSlabThreads, kSlabMinBlocks)
-    slab_kernel(const __grid_constant__ CUtensorMap mapx, const __grid_constant__ CUtensorMap mapy,
-                const __grid_constant__ CUtensorMap mapz, S s, shw_camera cam, RenderArgs a, SlabArgs sa)
+    slab_kernel(const __grid_constant__ SlabMaps maps, S s, shw_camera cam, RenderArgs a, SlabArgs sa)
 {
     extern __shared__ __align__(128) unsigned char slab_smem[];
     unsigned char *stages = slab_smem;
@@ -657,7 +674,7 @@ __global__ void __launch_bounds__(kSlabThreads, kSlabMinBlocks)
     }
     __syncthreads();
     if ((threadIdx.x >> 5) == kSlabWarps)
-        slab_producer<EP>(&mapx, &mapy, &mapz, cam, a, sa, stages, sh);
+        slab_producer<EP>(maps.m, cam, a, sa, stages, sh);
     else
         slab_consumer<MODE, EP>(s, cam, a, sa, stages, sh);
 }
@@ -668,7 +685,7 @@ constexpr size_t kSlabSmemBytes = (size_t)kSlabStages * kSlabStageBytes + sizeof
 
 // One mode's launch: persistent CTAs, as many as fit on the device at once (at most one per tile).
 template <int MODE, class EP, class S>
-shw_status slab_launch_one(const CUtensorMap maps[3], const S &s, const shw_camera &cam, const RenderArgs &a,
+shw_status slab_launch_one(const SlabMaps &maps, const S &s, const shw_camera &cam, const RenderArgs &a,
                            const SlabArgs &sa, cudaStream_t st)
 {
     auto kern = slab_kernel<MODE, EP, S>;
@@ -688,22 +705,24 @@ shw_status slab_launch_one(const CUtensorMap maps[3], const S &s, const shw_came
     const int nsm = sm_count();
     if (per_sm <= 0 || nsm <= 0) return SHW_ECUDA;
     const long long grid = std::min<long long>((long long)per_sm * nsm, sa.ntiles);
-    kern<<<(unsigned)std::max<long long>(grid, 1), kSlabThreads, kSlabSmemBytes, st>>>(maps[0], maps[1], maps[2], s,
-                                                                                         cam, a, sa);
+    kern<<<(unsigned)std::max<long long>(grid, 1), kSlabThreads, kSlabSmemBytes, st>>>(maps, s, cam, a, sa);
     return after_launch();
 }
 
-// The launch for one storage: the three tensor maps (x-, y- and z-major chunks), the tile
-// order and counter, then the mode's kernel.  SHW_EUNSUPPORTED if the driver refuses a map.
+// The launch for one storage: the tensor maps (x-major chunks; y- and z-major chunks, narrow
+// and wide), the tile order and counter, then the mode's kernel.  SHW_EUNSUPPORTED if the
+// driver refuses a map.
 template <class EP, class S>
 shw_status slab_launch(int mode, const S &s, const void *base, const shw_camera &cam, const RenderArgs &a0,
                        cudaStream_t st)
 {
     using G = SlabGeom<EP>;
-    CUtensorMap maps[3];
-    if (!encode_tmap_3d(&maps[0], base, G::kBytes, s.nx, s.ny, s.nz, G::kBXx, kSlabRows, 1) ||
-        !encode_tmap_3d(&maps[1], base, G::kBytes, s.nx, s.ny, s.nz, G::kBX, 1, kSlabRows) ||
-        !encode_tmap_3d(&maps[2], base, G::kBytes, s.nx, s.ny, s.nz, G::kBX, kSlabRows, 1))
+    SlabMaps maps;
+    if (!encode_tmap_3d(&maps.m[0], base, G::kBytes, s.nx, s.ny, s.nz, G::kBXx, kSlabRows, 1) ||
+        !encode_tmap_3d(&maps.m[1], base, G::kBytes, s.nx, s.ny, s.nz, G::kBXn, 1, kSlabRows) ||
+        !encode_tmap_3d(&maps.m[2], base, G::kBytes, s.nx, s.ny, s.nz, G::kBXw, 1, kSlabRows) ||
+        !encode_tmap_3d(&maps.m[3], base, G::kBytes, s.nx, s.ny, s.nz, G::kBXn, kSlabRows, 1) ||
+        !encode_tmap_3d(&maps.m[4], base, G::kBytes, s.nx, s.ny, s.nz, G::kBXw, kSlabRows, 1))
         return SHW_EUNSUPPORTED;
     RenderArgs a = a0;
     a.tiles_x = ceil_div(cam.width, kSlabTW);
