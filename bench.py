@@ -339,7 +339,7 @@ class E2EPipeline:
 
 # --------------------------------------------------------------------------- roofline
 
-def kernel_roofline(name, t_ms, nvox, samples_per, peaks, sm_mhz, image_bytes=0):
+def kernel_roofline(name, t_ms, nvox, samples_per, peaks, sm_mhz, image_bytes=0, sms=152):
     """Algorithmic work per launch / measured duration, against the bound of that kernel.
     Renders also report their HBM fraction (cube bytes read once + image written, over the
     time, against the measured copy rate) and, where a capture exists, the ncu DRAM fraction."""
@@ -354,7 +354,7 @@ def kernel_roofline(name, t_ms, nvox, samples_per, peaks, sm_mhz, image_bytes=0)
     mode = name[len("render_"):]
     ns = samples_per[mode]
     flops = ALG_FLOPS_PER_SAMPLE[mode] * ns
-    peak = FP32_LANES_PER_SM * 2 * SMS * float(sm_mhz) * 1e6 / 1e12  # TFLOP/s (FMA = 2)
+    peak = FP32_LANES_PER_SM * 2 * sms * float(sm_mhz) * 1e6 / 1e12  # TFLOP/s (FMA = 2)
     ach = flops / (t_ms * 1e-3) / 1e12
     loaded = peaks.get("clocks_under_load", {}).get("sm_mhz_median")
     cube_bytes = (8 if mode == "ratio" else 4) * nvox  # the ratio reads both cubes
@@ -364,7 +364,7 @@ def kernel_roofline(name, t_ms, nvox, samples_per, peaks, sm_mhz, image_bytes=0)
            "gsamples_per_s": round(ns / (t_ms * 1e-3) / 1e9, 2),
            "hbm_frac": round(alg_bytes / (t_ms * 1e-3) / 1e9 / hbm, 4), "algorithmic_bytes": alg_bytes}
     if loaded:  # the ALU fraction against the loaded median clock recorded with the peaks
-        peak_l = FP32_LANES_PER_SM * 2 * SMS * float(loaded) * 1e6 / 1e12
+        peak_l = FP32_LANES_PER_SM * 2 * sms * float(loaded) * 1e6 / 1e12
         rec["frac_at_loaded_median_clock"] = round(ach / peak_l, 4)
     traffic = TRAFFIC_PER_LAUNCH.get(name)
     if traffic:
@@ -372,13 +372,21 @@ def kernel_roofline(name, t_ms, nvox, samples_per, peaks, sm_mhz, image_bytes=0)
     return rec
 
 
-SMS = 152
 FP32_LANES_PER_SM = 128
 # FP32 flops the method needs per trilinear sample: 3 fraction weights,
 # 7 lerps (sub + FMA = 3 flops), plus the transfer function's own arithmetic.
 _TRI = 3 + 7 * 3
 ALG_FLOPS_PER_SAMPLE = {"mip": _TRI + 1, "spectral": _TRI + 1, "avg": _TRI + 4,
                         "ratio": 2 * _TRI + 2, "composite": _TRI + 2 + 8 + 6 + 3 + 2}
+
+
+def step_config(W, world):
+    """The workload of one step, identical for both arms of the benchmark."""
+    return {"workload": W["name"], "cube": "x".join(map(str, W["dims"])) + " f32 + ratio cube",
+            "image": f"{W['width']}x{W['height']} perspective yaw30 pitch20 fov45", "step_vox": W["step"],
+            "modes": WL.MODES, "smooth": "sigma 2, radius 6, both cubes (the second into the line ratio's pair storage)",
+            "interp": "trilinear", "l2": "inputs larger than L2 (1 GiB cubes vs 129 MB L2)",
+            "parallelism": f"replicas x{world}"}
 
 
 # --------------------------------------------------------------------------- multi-rank timing
@@ -476,7 +484,8 @@ def run_ours(args):
     peaks, peaks_src = load_peaks()
     sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 1485.0
     img_bytes = step.cam.width * step.cam.height * 16  # the RGBA float32 image each render writes
-    roof = {k: kernel_roofline(k, t, nvox, samples_per, peaks, sm_mhz, img_bytes) for k, t in per_kernel.items()}
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof = {k: kernel_roofline(k, t, nvox, samples_per, peaks, sm_mhz, img_bytes, sms) for k, t in per_kernel.items()}
     total_by_kind = {k: per_kernel[k] for k in per_kernel}
     dom = max(total_by_kind, key=total_by_kind.get)
 
@@ -492,11 +501,8 @@ def run_ours(args):
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_total / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": W["name"], "cube": "x".join(map(str, W["dims"])) + " f32 + ratio cube",
-                       "image": f"{W['width']}x{W['height']} perspective yaw30 pitch20 fov45", "step_vox": W["step"],
-                       "modes": WL.MODES, "smooth": "sigma 2, radius 6, both cubes (the second into the line ratio's pair storage)", "interp": "trilinear",
-                       "l2": "inputs larger than L2 (1 GiB cubes vs 129 MB L2)",
-                       "samples_per_step": samples_step, "parallelism": f"replicas x{world}"},
+            "config": step_config(W, world),
+            "samples_per_step": samples_step,
             "fps": {m: round(1000.0 / per_kernel[f"render_{m}"], 1) for m in WL.MODES},
             "steps_per_s": round(1000.0 * args.steps / ms_total, 2),
             "per_kernel_ms": {k: round(v, 4) for k, v in per_kernel.items()},
@@ -509,7 +515,7 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clk,
         }
-        if args.variants:
+        if not args.no_variants:
             res["variants"] = run_variants(shw, torch, step, W, per_kernel, samples_per, peaks)
     if world > 1:
         dist.barrier()
@@ -517,13 +523,10 @@ def run_ours(args):
     return res, samples_per
 
 
-# ncu DRAM bytes (read + write) per launch of each step kernel, from one capture of these
-# kernels on one GB300 at the full size; an entry is removed when its kernel changes
-TRAFFIC_PER_LAUNCH: dict = {
-    "smooth": 1273792768 + 1034413824, "smooth2": 2353712128 + 2102823680,
-    "render_mip": 1522822912 + 23123712, "render_avg": 1588480768 + 22132992,
-    "render_composite": 1364563456 + 24787456, "render_spectral": 1565263104 + 22183936,
-    "render_ratio": 2565604608 + 25061376}
+# ncu DRAM bytes (read + write) per launch of each step kernel of the current build (from one
+# capture of each kernel on the profiling case, scaled to the full launch as recorded under
+# profiles/); empty until such a capture exists -- the JSON line then reports traffic null
+TRAFFIC_PER_LAUNCH: dict = {}
 
 
 # --------------------------------------------------------------------------- variants
@@ -545,17 +548,17 @@ def _timeit(torch, fn, reps=5, warm=2):
     return statistics.median(ts)
 
 
-def run_variants(shw, torch, step, W, per_kernel, samples_per, peaks):
-    """The method's variants on the same GPU (reported beside the headline, not part of it):
-    the moment-map view of the same cube (the HBM-bound sweep), BF16/FP16 bricks against
-    the float32 path, the batched persistent launch against one launch per sub-cube, and
-    the adjoint of the compositing render."""
-    dev = step.s1.device
-    hbm = float(peaks["hbm_gbs"])
-    nvox = step.s1.numel()
-    res = {}
+def _hbm_roof(bytes_, t_ms, hbm):
+    ach = bytes_ / (t_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s", "frac": round(ach / hbm, 4),
+            "algorithmic_bytes": int(bytes_)}
 
-    # moment-map view: orthographic down the spectral axis, one pixel per voxel column
+
+def variant_moment_map(shw, torch, step, W, hbm):
+    """The moment-map view (Section 2.2): orthographic down the spectral axis of the smoothed
+    survey cube, one pixel per voxel column -- the plane sweep, bound by HBM."""
+    dev = step.s1.device
+    nvox = step.s1.numel()
     ocam = WL.survey_ortho_camera()
     mm = {}
     for m in ("mip", "avg", "spectral", "composite", "moment1"):
@@ -565,35 +568,61 @@ def run_variants(shw, torch, step, W, per_kernel, samples_per, peaks):
                  ["nsamples"].sum(dtype=torch.int64).item())
         t = _timeit(torch, lambda: shw.render(step.s1, ocam, m, lut=step.lut, step=W["step"], scalar=False,
                                               index=False, nsamples=False, out=o, **kw))
-        gbs = 4 * nvox / (t * 1e-3) / 1e9
         mm[m] = {"ms": round(t, 4), "gsamples_per_s": round(ns / (t * 1e-3) / 1e9, 2),
-                 "hbm_gbs": round(gbs, 1), "frac_of_measured_hbm": round(gbs / hbm, 4)}
-    res["moment_map"] = {"view": "orthographic down z, 512x512, step 0.5, trilinear; algorithmic bytes = "
-                                 "one read of the float32 cube per render", "modes": mm}
+                 "roofline": _hbm_roof(4 * nvox, t, hbm)}
+    return {"view": "orthographic down z, 512x512, step 0.5, trilinear; algorithmic bytes = one read of the "
+                    "float32 cube per render", "modes": mm}
 
-    # BF16 / FP16 bricks of the same smoothed cubes, same perspective renders (the line ratio
-    # on pair bricks packed from the float32 pair storage, against the float32 pair render)
-    br = {}
-    for storage in ("bf16", "f16"):
-        b1, bp = shw.pack_bricks(step.s1, storage), shw.pack_bricks(step.pair, storage)
+
+def variant_precision(shw, torch, step, W, per_kernel, samples_per):
+    """Reduced-precision storages of the same smoothed cubes, same full-HD renders: linear
+    bfloat16 / binary16 cubes (the staged marcher) and 32^3 bricks (the gather marcher).
+    Speed-up against the float32 path of the step, and the image error against that float32
+    render (max-abs and RMS, the scalar as a fraction of the cube's range; RGBA absolute).
+    The error against the FP64 oracle is asserted by the full-size tests."""
+    rng_cube = float(step.s1.max() - step.s1.min())
+    out = {}
+    ref = {}
+    for m in WL.MODES:
+        kw = dict(WL.MODE_PARAMS[m])
+        lut = step.rlut if m == "ratio" else step.lut
+        ref[m] = shw.render(step.vol_of(m), step.cam, m, lut=lut, step=W["step"], index=False, nsamples=False, **kw)
+    for storage in ("bf16_linear", "f16_linear", "bf16", "f16"):
+        v1, vp = shw.pack_bricks(step.s1, storage), shw.pack_bricks(step.pair, storage)
         per = {}
         for m in WL.MODES:
             kw = dict(WL.MODE_PARAMS[m])
             lut = step.rlut if m == "ratio" else step.lut
-            t = _timeit(torch, lambda: shw.render(bp if m == "ratio" else b1, step.cam, m, lut=lut, step=W["step"],
-                                                  scalar=False, index=False, nsamples=False, out=step.outs[m],
-                                                  **kw), reps=3)
+            vol = vp if m == "ratio" else v1
+            g = shw.render(vol, step.cam, m, lut=lut, step=W["step"], index=False, nsamples=False, **kw)
+            r = ref[m]
+            scale = rng_cube if m != "ratio" else float(r["scalar"].max() - r["scalar"].min()) or 1.0
+            es = (g["scalar"].double() - r["scalar"].double()).abs()
+            er = (g["rgba"].double() - r["rgba"].double()).abs()
+            o = {"rgba": g["rgba"]}
+            t = _timeit(torch, lambda: shw.render(vol, step.cam, m, lut=lut, step=W["step"], scalar=False,
+                                                  index=False, nsamples=False, out=o, **kw), reps=3)
             f32 = per_kernel[f"render_{m}"]
             per[m] = {"ms": round(t, 4), "fp32_ms": round(f32, 4), "speedup_vs_fp32": round(f32 / t, 3),
-                      "gsamples_per_s": round(samples_per[m] / (t * 1e-3) / 1e9, 2)}
-        br[storage] = per
-        del b1, bp
-    res["bricks"] = br
+                      "gsamples_per_s": round(samples_per[m] / (t * 1e-3) / 1e9, 2),
+                      "scalar_err_vs_fp32": {"max": float(es.max() / scale), "rms": float(es.pow(2).mean().sqrt() / scale),
+                                             "p999": float(torch.quantile(es.flatten()[::16].float(), 0.999) / scale),
+                                             "scale": "ratio image range" if m == "ratio" else "cube range"},
+                      "rgba_err_vs_fp32": {"max": float(er.max()), "rms": float(er.pow(2).mean().sqrt())}}
+            del g
+        out[storage] = per
+        del v1, vp
+    del ref
+    return {"storages": out, "note": "linear 16-bit cubes render through the staged marcher, bricks through the "
+                                     "gather marcher; both hold the same rounded values"}
 
-    # batch: sub-cubes with axes log-uniform in [32, 256], alternately float32 and BF16 bricks,
-    # alternately MIP and compositing, 256x256 from random views
+
+def variant_batch(shw, torch, step, B):
+    """2,000 sub-cubes (axes log-uniform in [32, 256]; float32 and BF16 bricks alternating; MIP and
+    compositing alternating; 256x256 random views): one graph-captured persistent launch
+    against one launch per sub-cube issued by the library's own loop."""
     import concurrent.futures as cf
-    B = WL.BATCH
+    dev = step.s1.device
     dims = scene.batch_dims(n=B["n"], lo=B["lo"], hi=B["hi"])
     rng = np.random.default_rng(11)
     views = [(rng.uniform(0, 360), rng.uniform(-60, 60)) for _ in range(len(dims))]
@@ -602,46 +631,143 @@ def run_variants(shw, torch, step, W, per_kernel, samples_per, peaks):
         cubes = list(ex.map(lambda i: scene.batch_subcube(i, tuple(int(x) for x in dims[i])), range(len(dims))))
     log(f"batch sub-cubes generated in {time.time() - t0:.1f}s")
     items = []
+    nvox = 0
     for i, cube in enumerate(cubes):
         d = tuple(int(x) for x in dims[i])
         ct = torch.from_numpy(cube).to(dev)
+        nvox += ct.numel()
         vol = ct if i % 2 == 0 else shw.pack_bricks(ct, "bf16")
         cam = scene.orbit_camera(d, views[i][0], views[i][1], B["width"], B["height"])
         items.append((vol, cam, B["modes"][(i // 2) % 2]))
     del cubes
     plan = shw.BatchPlan(items, lut=step.lut, step=B["step"], opacity_scale=B["opacity_scale"])
     t_plan = _timeit(torch, plan.render, reps=3)
-    outs = plan.outputs
-
-    def one_by_one():
-        for (vol, cam, mode), o in zip(items, outs):
-            shw.render(vol, cam, mode, lut=step.lut, step=B["step"], opacity_scale=B["opacity_scale"],
-                       scalar=False, index=False, nsamples=False, out={"rgba": o})
-    t_loop = _timeit(torch, one_by_one, reps=3, warm=1)
+    t_loop = _timeit(torch, plan.render_one_by_one, reps=3, warm=1)
+    ns = 0
+    for vol, cam, mode in items:
+        ns += int(shw.render(vol, cam, mode, lut=step.lut, step=B["step"], opacity_scale=B["opacity_scale"],
+                             scalar=False, index=False)["nsamples"].sum(dtype=torch.int64).item())
     info = plan.info
-    res["batch"] = {"n": len(items), "persistent_graph_ms": round(t_plan, 3), "one_launch_per_cube_ms": round(t_loop, 3),
-                    "subcubes_per_s": round(len(items) / (t_plan * 1e-3), 1),
-                    "subcubes_per_s_one_launch_per_cube": round(len(items) / (t_loop * 1e-3), 1),
-                    "speedup": round(t_loop / t_plan, 3), "tile": info["tile"], "ctas_per_sm": info["ctas_per_sm"]}
     plan.close()
-    del items, outs
+    del items
+    return {"n": int(len(dims)), "voxels": int(nvox), "samples": ns,
+            "persistent_graph_ms": round(t_plan, 3), "one_launch_per_cube_ms": round(t_loop, 3),
+            "subcubes_per_s": round(len(dims) / (t_plan * 1e-3), 1),
+            "subcubes_per_s_one_launch_per_cube": round(len(dims) / (t_loop * 1e-3), 1),
+            "speedup": round(t_loop / t_plan, 3), "gsamples_per_s": round(ns / (t_plan * 1e-3) / 1e9, 2),
+            "tile": info["tile"], "ctas_per_sm": info["ctas_per_sm"],
+            "baseline": "one shw_render launch per sub-cube from the library's loop (shw_render_items)"}
 
-    # adjoint of the compositing render (256^3 cube, 512x512 image, checkpoints every 64 steps)
+
+def variant_adjoint(shw, torch, step):
+    """Forward with transmittance checkpoints every 64 samples and the adjoint of compositing
+    (256^3 cube, 512x512 perspective)."""
+    dev = step.s1.device
     D = WL.DIFF
     cube = torch.from_numpy(scene.diff_cube(dims=D["dims"])).to(dev)
     cam = scene.orbit_camera(D["dims"], D["yaw"], D["pitch"], D["width"], D["height"])
     kw = dict(lut=step.lut, step=D["step"], opacity_scale=D["opacity_scale"], ckpt_interval=D["ckpt_interval"])
-    fw = shw.render(cube, cam, "composite", scalar=False, index=False, nsamples=False, ckpt=True, **kw)
+    fw = shw.render(cube, cam, "composite", scalar=False, index=False, ckpt=True, **kw)
+    ns = int(fw["nsamples"].sum(dtype=torch.int64).item())
+    fw.pop("nsamples")
     g_rgba = torch.ones_like(fw["rgba"])
     g_vol, g_lut, g_s = torch.zeros_like(cube), torch.zeros_like(step.lut), torch.zeros(1, device=dev)
     t_fw = _timeit(torch, lambda: shw.render(cube, cam, "composite", scalar=False, index=False, nsamples=False,
                                              ckpt=True, out=fw, **kw))
     t_bw = _timeit(torch, lambda: shw.render_backward(cube, cam, g_rgba, fw["ckpt"], grad_vol=g_vol, grad_lut=g_lut,
                                                       grad_scale=g_s, **kw))
-    res["adjoint"] = {"workload": D["name"], "forward_ms": round(t_fw, 4), "backward_ms": round(t_bw, 4)}
     del cube, fw, g_rgba, g_vol
-    res["in_ray_smoothing"] = run_in_ray_smoothing(shw, torch, dev)
-    shw.sync_status()
+    return {"workload": D["name"], "samples": ns, "forward_ms": round(t_fw, 4), "backward_ms": round(t_bw, 4),
+            "forward_gsamples_per_s": round(ns / (t_fw * 1e-3) / 1e9, 2),
+            "backward_gsamples_per_s": round(ns / (t_bw * 1e-3) / 1e9, 2)}
+
+
+def _rotation_ms(shw, torch, vol, dims, mode, lut, width, height, pitch, nviews, kw, reps=3):
+    """Median over `reps` of one full rotation's render time (nviews yaws, CUDA events) and
+    the samples of one rotation."""
+    cams = [scene.orbit_camera(dims, 360.0 * i / nviews, pitch, width, height) for i in range(nviews)]
+    o = {"rgba": torch.empty((height, width, 4), dtype=torch.float32, device=lut.device)}
+    ns = 0
+    for c in cams:
+        ns += int(shw.render(vol, c, mode, lut=lut, scalar=False, index=False, **kw)["nsamples"].sum(
+            dtype=torch.int64).item())
+
+    def rot():
+        for c in cams:
+            shw.render(vol, c, mode, lut=lut, scalar=False, index=False, nsamples=False, out=o, **kw)
+    return _timeit(torch, rot, reps=reps, warm=1), ns
+
+
+def variant_paper_shape(shw, torch, dev):
+    """The paper's benchmark shapes (Section 6, Appendix B): U[0,1] cubes 128^3 .. 1024^3, a full
+    rotation of 36 views, median of 3 rotations; MIP on canvases 500^2 .. 2000^2 (the canvas
+    sweep) and compositing with k = 0.22 and a minimum threshold of 0.9 on 1000^2; and the
+    stand-ins for the paper's three real cubes on 1000^2.  Frame rates here are GB300 ones;
+    the paper's are OpenGL frame rates on 2013-2015 GPUs (context only)."""
+    P = WL.PAPER_SHAPE
+    lut = torch.from_numpy(scene.linear_lut()).to(dev)
+    grid = {}
+    for n in P["cubes"]:
+        cube = torch.from_numpy(scene.paper_uniform_cube(n)).to(dev)
+        row = {}
+        for canvas in P["canvases"]:
+            t, ns = _rotation_ms(shw, torch, cube, (n, n, n), "mip", lut, canvas, canvas, P["pitch"], P["views"],
+                                 dict(lo=0.0, hi=1.0, step=P["step"]))
+            row[f"mip_{canvas}"] = {"fps": round(1e3 * P["views"] / t, 1), "gsamples_per_s": round(ns / (t * 1e-3) / 1e9, 2)}
+        t, ns = _rotation_ms(shw, torch, cube, (n, n, n), "composite", lut, 1000, 1000, P["pitch"], P["views"],
+                             dict(lo=0.0, hi=1.0, step=P["step"], opacity_scale=P["opacity_scale"], filter="clip",
+                                  min_threshold=P["clip"][0], max_threshold=P["clip"][1]))
+        row["composite_1000"] = {"fps": round(1e3 * P["views"] / t, 1), "gsamples_per_s": round(ns / (t * 1e-3) / 1e9, 2)}
+        grid[f"{n}^3"] = row
+        del cube
+    stand = {}
+    for kind in ("ngc2903", "antennae", "gama511867"):
+        c = scene.paper_standin(kind)
+        dims = scene.STANDIN_DIMS[kind]
+        if kind == "gama511867":
+            pair = torch.stack([torch.from_numpy(c[0]), torch.from_numpy(c[1])], dim=-1).contiguous().to(dev)
+            rl = torch.from_numpy(scene.ratio_lut()).to(dev)
+            t, ns = _rotation_ms(shw, torch, pair, dims, "ratio", rl, 1000, 1000, P["pitch"], P["views"],
+                                 dict(lo=0.0, hi=1.0, step=P["step"], ratio_floor=1.0))
+            stand[kind] = {"mode": "ratio (line ratio of the two sub-cubes)", "fps": round(1e3 * P["views"] / t, 1),
+                           "gsamples_per_s": round(ns / (t * 1e-3) / 1e9, 2)}
+            del pair
+            continue
+        ct = torch.from_numpy(c).to(dev)
+        r = {}
+        for m in ("mip", "composite"):
+            kw = dict(lo=-3.0, hi=8.0, step=P["step"])
+            if m == "composite":
+                kw.update(opacity_scale=0.05)
+            t, ns = _rotation_ms(shw, torch, ct, dims, m, lut, 1000, 1000, P["pitch"], P["views"], kw)
+            r[m] = {"fps": round(1e3 * P["views"] / t, 1), "gsamples_per_s": round(ns / (t * 1e-3) / 1e9, 2)}
+        stand[kind] = r
+        del ct
+    return {"workload": P["name"], "rotation": f"{P['views']} views (yaw 0..350, pitch {P['pitch']}), median of 3",
+            "uniform_cubes": grid, "standins_1000x1000": stand,
+            "paper_context": "the paper reports up to 94 fps (MIP, 128^3, 1000^2, GTX TITAN X) and about 2 fps "
+                             "for 1024^3 on a GT 750M / GRID K1 (OpenGL; not measured here)"}
+
+
+def run_variants(shw, torch, step, W, per_kernel, samples_per, peaks):
+    """The method's variants on the same GPU, reported beside the headline step: the moment-map
+    view (the HBM-bound sweep), the reduced-precision storages against float32, the batched
+    persistent launch against one launch per sub-cube, the adjoint, the paper's benchmark
+    shapes and the in-ray smoothing kernels."""
+    dev = step.s1.device
+    hbm = float(peaks["hbm_gbs"])
+    res = {}
+    for name, fn in (("moment_map", lambda: variant_moment_map(shw, torch, step, W, hbm)),
+                     ("precision", lambda: variant_precision(shw, torch, step, W, per_kernel, samples_per)),
+                     ("batch", lambda: variant_batch(shw, torch, step, WL.BATCH)),
+                     ("adjoint", lambda: variant_adjoint(shw, torch, step)),
+                     ("paper_shape", lambda: variant_paper_shape(shw, torch, dev)),
+                     ("in_ray_smoothing", lambda: run_in_ray_smoothing(shw, torch, dev))):
+        t = time.time()
+        res[name] = fn()
+        shw.sync_status()
+        torch.cuda.empty_cache()
+        log(f"variant {name}: {time.time() - t:.1f}s")
     return res
 
 
@@ -761,7 +887,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WL.SURVEY["name"]},
+        "config": step_config(WL.SURVEY, world),
         "cpu_baseline": {"value": round(v, 6), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -814,8 +940,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variants", action="store_true",
-                    help="also time the moment-map view, BF16/FP16 bricks, the batched launch and the adjoint")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the variant legs (moment-map view, 16-bit storages, batch, adjoint, paper shapes, "
+                         "in-ray smoothing)")
     ap.add_argument("--workload", default="survey", choices=sorted(WORKLOADS),
                     help="survey: the headline workload; survey-small: the same step on a smaller cube "
                          "(profiler captures)")

@@ -330,10 +330,12 @@ shw_status shw_render_backward(const shw_volume *vol, const shw_camera *cam, con
                                            spectral-axis sweep nor the staged marcher serves is
                                            refused (SHW_EUNSUPPORTED) instead of taking the gather
                                            marcher */
-#define SHW_DEBUG_FAULT_TIMEOUT 0x40u /* tensor-copy kernels launched while set leave one stage's copy
-                                         unissued and wait for it about 1 ms: every CTA that needs the
-                                         stage gives up, returns, and shw_sync_status reports
-                                         SHW_ETIMEOUT; the output is left incomplete */
+#define SHW_DEBUG_FAULT_TIMEOUT 0x40u /* smoothing launched while set (its tensor-copy form: radius 1..8,
+                                         nx a multiple of 4) leaves the copy of each z chunk's second
+                                         plane unissued and bounds its waits at about 1 ms: every CTA
+                                         gives up at that plane, waits for its other copies and returns;
+                                         shw_sync_status then reports SHW_ETIMEOUT and the output is
+                                         incomplete.  Later calls run normally */
 uint32_t shw_set_debug_flags(uint32_t flags);
 
 /* ---- batched rendering of many sub-cubes ----------------------------------- */

@@ -14,6 +14,7 @@
 // Neighbouring CTAs sweep z in lockstep, so their halo reads hit L2.
 #include <cmath>
 #include <cstdlib>
+#include <type_traits>
 
 #include "common.cuh"
 #include "tma.cuh"
@@ -25,12 +26,6 @@ struct SmoothWeights {
     float2 w2[2 * SHW_MAX_SMOOTH_RADIUS + 1];  // (w_k, w_k): the packed FMAs' weight operand
 };
 
-#ifndef SHW_SMOOTH_ONEBAR
-#define SHW_SMOOTH_ONEBAR 1  // 1: one CTA barrier per plane (after the x pass); 0: also one after the wait
-#endif
-#ifndef SHW_SMOOTH_WPAIR
-#define SHW_SMOOTH_WPAIR 1  // 1: packed FMAs take the weight pair from the parameters; 0: built per use
-#endif
 
 __device__ __forceinline__ int clampi_s(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
@@ -118,11 +113,19 @@ __global__ void __launch_bounds__(32 * (32 / YB)) smooth_kernel(const float *__r
 //           straight to HBM as float2.
 constexpr int kSmTX = 32, kSmTY = 32, kSmXP = 8, kSmBW = kSmTX + 2 * kSmXP, kSmStages = 3, kSmThreads = 256;
 
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 wpair(const SmoothWeights &W, int k)
+// Call f(std::integral_constant<int, v>) for the runtime value v in [0, N): the callee sees
+// v as a compile-time constant (a chain of N compares selects the instance).
+template <int N, int S = 0, class F>
+__device__ __forceinline__ void static_slot(int v, F &&f)
 {
-    return SHW_SMOOTH_WPAIR ? W.w2[k] : f2(W.w[k]);
+    if constexpr (S < N) {
+        if (v == S)
+            f(std::integral_constant<int, S>{});
+        else
+            static_slot<N, S + 1>(v, f);
+    }
 }
+
 
 // Replace the zero-filled out-of-range border of a staged tile by the edge values
 // (clamp-to-edge): first the columns outside [c_lo, c_hi], then whole rows outside
@@ -150,17 +153,14 @@ __device__ __forceinline__ void clamp_tile_edges(float *tile, int c_lo, int c_hi
     }
 }
 
-#ifndef SHW_SMOOTH_ZIP_MINB
-#define SHW_SMOOTH_ZIP_MINB 2  // the zip form holds the first cube's values of a plane in registers too
-#endif
-#ifndef SHW_SMOOTH_MINB
-#define SHW_SMOOTH_MINB 3  // 80 registers, no spills, with the weight pairs in the parameters
-#endif
+constexpr int kSmoothZipMinBlocks = 2;  // the zip form holds the first cube's values of a plane in registers too
+constexpr int kSmoothMinBlocks = 3;     // resident CTAs per SM the plain form is compiled for
 
 template <int R, bool ZIP>
-__global__ void __launch_bounds__(kSmThreads, ZIP ? SHW_SMOOTH_ZIP_MINB : SHW_SMOOTH_MINB)
+__global__ void __launch_bounds__(kSmThreads, ZIP ? kSmoothZipMinBlocks : kSmoothMinBlocks)
     smooth_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict__ out, int nx, int ny, int nz,
-                      int zchunk, SmoothWeights W, unsigned *err, const float *__restrict__ first)
+                      int zchunk, SmoothWeights W, unsigned *err, const float *__restrict__ first, int skip_plane,
+                      int polls)
 {
     constexpr int IH = kSmTY + 2 * R, K = 2 * R + 1;
     constexpr int STAGE_FLOATS = IH * kSmBW;
@@ -188,6 +188,7 @@ __global__ void __launch_bounds__(kSmThreads, ZIP ? SHW_SMOOTH_ZIP_MINB : SHW_SM
     if (s_bad) return;  // reported in the error word; nothing was issued
     if (tid == 0) {
         for (int s = 0; s < kSmStages && s < nplanes; ++s) {
+            if (s == skip_plane) continue;  // fault injection: this plane's copy is never issued
             mbar_arrive_expect_tx(&bars[s], STAGE_BYTES);
             tma_load_3d(s_in + s * STAGE_FLOATS, &tmap, x0 - kSmXP, y0 - R, min(max(zfirst + s, 0), nz - 1),
                         &bars[s]);
@@ -210,89 +211,79 @@ __global__ void __launch_bounds__(kSmThreads, ZIP ? SHW_SMOOTH_ZIP_MINB : SHW_SM
 
     bool failed = false;
     int fail_i = 0;  // the plane whose wait gave up
-    for (int base = 0; base < nplanes && !failed; base += K) {
+    for (int i = 0; i < nplanes; ++i) {
+        const int stage = i % kSmStages;
+        // ZIP: this plane's output pairs take the first cube's values; load them now, so
+        // the latency hides behind the passes (a lane outside the cube loads nothing)
+        float2 fpre[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+        if constexpr (ZIP) {
+            if (i >= 2 * R && gx < nx) {
+                const size_t zrow = (size_t)(zfirst + i - R) * plane;
 #pragma unroll
-        for (int slot = 0; slot < K; ++slot) {
-            const int i = base + slot;
-            if (i >= nplanes) break;
-            const int stage = i % kSmStages;
-            // ZIP: this plane's output pairs take the first cube's values; load them now, so
-            // the latency hides behind the passes (a lane outside the cube loads nothing)
-            float2 fpre[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
-            if constexpr (ZIP) {
-                if (i >= 2 * R && gx < nx) {
-                    const size_t zrow = (size_t)(zfirst + i - R) * plane;
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        const int gy = y0 + 2 * rg + j;
-                        if (gy < ny)
-                            fpre[j] = __ldg(reinterpret_cast<const float2 *>(first + zrow + (size_t)gy * nx + gx));
-                    }
+                for (int j = 0; j < 2; ++j) {
+                    const int gy = y0 + 2 * rg + j;
+                    if (gy < ny) fpre[j] = __ldg(reinterpret_cast<const float2 *>(first + zrow + (size_t)gy * nx + gx));
                 }
             }
-            const bool ok = mbar_wait(&bars[stage], (uint32_t)((i / kSmStages) & 1), err);
-#if !SHW_SMOOTH_ONEBAR
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                fail_i = i;
-                break;
+        }
+        const bool ok = mbar_wait(&bars[stage], (uint32_t)((i / kSmStages) & 1), err, polls);
+        float *tile = s_in + stage * STAGE_FLOATS;
+        if (edge) clamp_tile_edges<IH>(tile, c_lo, c_hi, r_lo, r_hi, tid);
+        float *xp = s_xp + (i & 1) * IH * kSmTX;
+        // x-pass: unit u -> row u/8, outputs 4q .. 4q+3 with q = u%8
+        for (int u = tid; u < IH * 8; u += kSmThreads) {
+            const int r = u >> 3, q = u & 7;
+            const float4 *src = reinterpret_cast<const float4 *>(tile + r * kSmBW + 4 * q);
+            float v[20];
+#pragma unroll
+            for (int t = 0; t < 5; ++t) {
+                const float4 f = src[t];
+                v[4 * t] = f.x;
+                v[4 * t + 1] = f.y;
+                v[4 * t + 2] = f.z;
+                v[4 * t + 3] = f.w;
             }
-#endif
-            float *tile = s_in + stage * STAGE_FLOATS;
-            if (edge) clamp_tile_edges<IH>(tile, c_lo, c_hi, r_lo, r_hi, tid);
-            float *xp = s_xp + (i & 1) * IH * kSmTX;
-            // x-pass: unit u -> row u/8, outputs 4q .. 4q+3 with q = u%8
-            for (int u = tid; u < IH * 8; u += kSmThreads) {
-                const int r = u >> 3, q = u & 7;
-                const float4 *src = reinterpret_cast<const float4 *>(tile + r * kSmBW + 4 * q);
-                float v[20];
+            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
-                for (int t = 0; t < 5; ++t) {
-                    const float4 f = src[t];
-                    v[4 * t] = f.x;
-                    v[4 * t + 1] = f.y;
-                    v[4 * t + 2] = f.z;
-                    v[4 * t + 3] = f.w;
-                }
-                float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            for (int k = 0; k < K; ++k)
 #pragma unroll
-                for (int k = 0; k < K; ++k)
+                for (int j = 0; j < 4; ++j) acc[j] = __fmaf_rn(W.w[k], v[kSmXP - R + j + k], acc[j]);
+            *reinterpret_cast<float4 *>(xp + r * kSmTX + 4 * q) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        }
+        if (edge) fence_proxy_async();  // the edge clamp wrote the stage that a tensor copy refills next
+        // one barrier per plane: it orders the x pass before the refill and the y pass, and
+        // reports a wait that gave up (the x pass then read a stage whose copy may not have
+        // landed; nothing of this plane reaches memory outside the CTA)
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            fail_i = i;
+            break;
+        }
+        // the stage is consumed: refill it with plane i + stages
+        if (tid == 0 && i + kSmStages < nplanes) {
+            mbar_arrive_expect_tx(&bars[stage], STAGE_BYTES);
+            tma_load_3d(tile, &tmap, x0 - kSmXP, y0 - R, min(max(zfirst + i + kSmStages, 0), nz - 1), &bars[stage]);
+        }
+        // y-pass of this plane
+        const float2 *xp2 = reinterpret_cast<const float2 *>(xp);
+        float2 col[2 + 2 * R];
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[j] = __fmaf_rn(W.w[k], v[kSmXP - R + j + k], acc[j]);
-                *reinterpret_cast<float4 *>(xp + r * kSmTX + 4 * q) = make_float4(acc[0], acc[1], acc[2], acc[3]);
-            }
-            if (edge) fence_proxy_async();  // the edge clamp wrote the stage that a tensor copy refills next
-#if SHW_SMOOTH_ONEBAR
-            // one barrier per plane: it orders the x pass before the refill and the y pass, and
-            // reports a wait that gave up (the x pass then read a stage whose copy may not have
-            // landed; nothing of this plane reaches memory outside the CTA)
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                fail_i = i;
-                break;
-            }
-#else
-            __syncthreads();
-#endif
-            // the stage is consumed: refill it with plane i + stages
-            if (tid == 0 && i + kSmStages < nplanes) {
-                mbar_arrive_expect_tx(&bars[stage], STAGE_BYTES);
-                tma_load_3d(tile, &tmap, x0 - kSmXP, y0 - R, min(max(zfirst + i + kSmStages, 0), nz - 1),
-                            &bars[stage]);
-            }
-            // y-pass into the ring slot of this plane
-            const float2 *xp2 = reinterpret_cast<const float2 *>(xp);
-            float2 col[2 + 2 * R];
+        for (int m = 0; m < 2 + 2 * R; ++m) col[m] = xp2[(2 * rg + m) * (kSmTX / 2) + cp];
+        float2 yv[2];
 #pragma unroll
-            for (int m = 0; m < 2 + 2 * R; ++m) col[m] = xp2[(2 * rg + m) * (kSmTX / 2) + cp];
+        for (int j = 0; j < 2; ++j) {
+            float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                float2 acc = make_float2(0.0f, 0.0f);
-#pragma unroll
-                for (int k = 0; k < K; ++k) acc = __ffma2_rn(wpair(W, k), col[j + k], acc);
-                ring[j][slot] = acc;
-            }
-            // z-pass: the ring holds planes i-2R .. i (oldest in slot (slot+1) mod K)
+            for (int k = 0; k < K; ++k) acc = __ffma2_rn(W.w2[k], col[j + k], acc);
+            yv[j] = acc;
+        }
+        // into the register ring at slot i mod K, then the z-pass: the ring holds planes
+        // i-2R .. i (oldest in slot (slot+1) mod K).  Only this part is instanced per slot,
+        // so the ring is indexed at compile time.
+        static_slot<K>(i % K, [&](auto sc) {
+            constexpr int slot = decltype(sc)::value;
+            ring[0][slot] = yv[0];
+            ring[1][slot] = yv[1];
             if (i >= 2 * R) {
                 const int zo = zfirst + i - R;
 #pragma unroll
@@ -300,7 +291,7 @@ __global__ void __launch_bounds__(kSmThreads, ZIP ? SHW_SMOOTH_ZIP_MINB : SHW_SM
                     const int gy = y0 + 2 * rg + j;
                     float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
-                    for (int k = 0; k < K; ++k) acc = __ffma2_rn(wpair(W, k), ring[j][(slot + 1 + k) % K], acc);
+                    for (int k = 0; k < K; ++k) acc = __ffma2_rn(W.w2[k], ring[j][(slot + 1 + k) % K], acc);
                     if (gx < nx && gy < ny) {
                         const size_t o = (size_t)zo * plane + (size_t)gy * nx + gx;
                         if constexpr (ZIP) {
@@ -313,13 +304,14 @@ __global__ void __launch_bounds__(kSmThreads, ZIP ? SHW_SMOOTH_ZIP_MINB : SHW_SM
                     }
                 }
             }
-        }
+        });
     }
     if (failed && tid == 0) {
         // drain: wait (bounded) for this CTA's copies still in flight before leaving --
         // planes fail_i .. fail_i + stages - 1 were issued and not consumed
         for (int j = fail_i; j < min(nplanes, fail_i + kSmStages); ++j)
-            mbar_wait(&bars[j % kSmStages], (uint32_t)((j / kSmStages) & 1), nullptr);
+            mbar_wait(&bars[j % kSmStages], (uint32_t)((j / kSmStages) & 1), nullptr,
+                      j == skip_plane ? polls : kWaitPolls);  // (a copy that was issued lands well within a second)
     }
 }
 
@@ -329,16 +321,11 @@ static size_t smooth_tma_smem()
     return (size_t)(kSmStages * (kSmTY + 2 * R) * kSmBW + 2 * (kSmTY + 2 * R) * kSmTX) * 4;
 }
 
-#ifndef SHW_SMOOTH_WAVES
-#define SHW_SMOOTH_WAVES 1  // 1: the z chunk is chosen against the resident-CTA waves
-#endif
-#ifndef SHW_SMOOTH_ZC
-#define SHW_SMOOTH_ZC 128  // largest z chunk of one CTA (planes)
-#endif
+constexpr int kSmoothMaxChunk = 128;  // largest z chunk of one CTA (planes), without a wave count
 static int smooth_zchunk(int nx, int ny, int nz, int r)
 {
     const long long tiles = (long long)ceil_div(nx, 32) * ceil_div(ny, 32);
-    int zc = nz < SHW_SMOOTH_ZC ? nz : SHW_SMOOTH_ZC;
+    int zc = nz < kSmoothMaxChunk ? nz : kSmoothMaxChunk;
     const int zmin = (4 * r > 16) ? 4 * r : 16;
     while (tiles * ceil_div(nz, zc) < 608 && zc / 2 >= zmin) zc /= 2;
     return zc;
@@ -393,10 +380,13 @@ static bool launch_smooth_tma(const float *in, float *out, int nx, int ny, int n
         cudaGetLastError();
         nsm = 0;
     }
-    const int zc = SHW_SMOOTH_WAVES ? smooth_zchunk_waves(nx, ny, nz, R, (long long)per_sm * nsm)
-                                    : smooth_zchunk(nx, ny, nz, R);
+    const int zc = smooth_zchunk_waves(nx, ny, nz, R, (long long)per_sm * nsm);
     const dim3 grid((unsigned)ceil_div(nx, kSmTX), (unsigned)ceil_div(ny, kSmTY), (unsigned)ceil_div(nz, zc));
-    smooth_tma_kernel<R, ZIP><<<grid, kSmThreads, smem, st>>>(map, out, nx, ny, nz, zc, w, err, first);
+    // SHW_DEBUG_FAULT_TIMEOUT: plane 1 of every chunk is never copied, and waits end after about
+    // a millisecond (instead of a second), so every CTA's wait runs out quickly
+    const bool fault = debug(SHW_DEBUG_FAULT_TIMEOUT);
+    smooth_tma_kernel<R, ZIP><<<grid, kSmThreads, smem, st>>>(map, out, nx, ny, nz, zc, w, err, first, fault ? 1 : -1,
+                                                              fault ? kFaultWaitPolls : kWaitPolls);
     return true;
 }
 

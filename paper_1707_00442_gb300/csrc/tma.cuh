@@ -16,7 +16,9 @@ namespace shw {
 
 constexpr unsigned kErrWaitTimeout = 1u;
 constexpr unsigned kErrTmaAlign = 2u;
-constexpr int kWaitSpins = 1 << 22;  // try_wait already suspends in hardware between polls
+constexpr int kWaitPolls = 1 << 20;       // bounded waits: polls of at most ...
+constexpr uint32_t kWaitSleepNs = 1000;  // ... this many nanoseconds each, about a second in all
+constexpr int kFaultWaitPolls = 1000;    // the bound under SHW_DEBUG_FAULT_TIMEOUT: about a millisecond
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -94,11 +96,12 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t pari
     return ok != 0;
 }
 
-// Wait for phase `parity` of `bar`; false (and the error word set) after kWaitSpins polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned *err)
+// Wait for phase `parity` of `bar`, the thread suspended between polls (so waiting warps
+// leave the issue slots to others); false (and the error word set) after `polls` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned *err, int polls = kWaitPolls)
 {
-    for (int i = 0; i < kWaitSpins; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
+    for (int i = 0; i < polls; ++i)
+        if (mbar_try_wait_sleep(bar, parity, kWaitSleepNs)) return true;
     if (err) atomicOr(err, kErrWaitTimeout);
     return false;
 }

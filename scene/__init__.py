@@ -7,12 +7,14 @@ those live separately in the CUDA library and in the oracle.
 """
 from .cubes import (  # noqa: F401
     SEED_BASE,
+    STANDIN_DIMS,
     Source,
     add_source,
     batch_dims,
     batch_subcube,
     diff_cube,
     draw_sources,
+    paper_standin,
     paper_uniform_cube,
     ratio_cube,
     survey_cube,

@@ -146,3 +146,43 @@ def batch_subcube(i: int, dims, config_id: int = 4) -> np.ndarray:
 def paper_uniform_cube(n: int, config_id: int = 9) -> np.ndarray:
     """The paper's benchmark cubes: every voxel an independent U[0,1] float32 (Appendix B)."""
     return _rng(config_id, stream=n).random((n, n, n), dtype=np.float32)
+
+
+# The paper's three real cubes (Section 5.2), stood in for by shape and by the intensity
+# range its histograms report, in units of each cube's noise sigma: NGC 2903 1024x1024x87
+# (minimum about -7 sigma, maximum about 15 sigma); the Antennae mosaic 750x750x70 (maximum
+# about 68 sigma; NaN outside a tilted polygon, the mosaic's footprint); GAMA-511867 two
+# 50x50x37 sub-cubes, H-alpha (maximum about 8 sigma) and [NII] (about 7.6 sigma).
+STANDIN_DIMS = {"ngc2903": (1024, 1024, 87), "antennae": (750, 750, 70), "gama511867": (50, 50, 37)}
+
+
+def paper_standin(kind: str, config_id: int = 10) -> np.ndarray | tuple:
+    """A stand-in for one of the paper's cubes: N(0,1) noise plus rotating-disc sources whose
+    peaks reach the reported maximum.  ``gama511867`` returns the (H-alpha, [NII]) pair, the
+    second line 0.4 times the first plus its own noise (a line ratio near 0.4)."""
+    dims = STANDIN_DIMS[kind]
+    rng = _rng(config_id, stream={"ngc2903": 1, "antennae": 2, "gama511867": 3}[kind])
+    cube = _noise(rng, dims)
+    nx, ny, nz = dims
+    if kind == "ngc2903":
+        srcs = draw_sources(rng, dims, 1, peak=(15.0, 15.0), sig_major=(nx / 8, nx / 8), sig_z=nz / 8, margin=0.4)
+        srcs += draw_sources(rng, dims, 40, peak=(2.0, 8.0), fwhm_loguniform=(6.0, 40.0), sig_z=3.0)
+    elif kind == "antennae":
+        srcs = draw_sources(rng, dims, 2, peak=(30.0, 40.0), sig_major=(nx / 20, nx / 12), sig_z=nz / 10, margin=0.3)
+        srcs += draw_sources(rng, dims, 30, peak=(2.0, 10.0), fwhm_loguniform=(6.0, 30.0), sig_z=3.0, margin=0.2)
+    else:
+        srcs = draw_sources(rng, dims, 1, peak=(8.0, 8.0), sig_major=(nx / 6, nx / 6), sig_z=nz / 8, margin=0.4)
+    for s in srcs:
+        add_source(cube, s)
+    if kind == "antennae":
+        # the mosaic's footprint: a square tilted by 30 degrees covering the central part
+        y, x = np.mgrid[0:ny, 0:nx]
+        c, s_ = math.cos(math.radians(30.0)), math.sin(math.radians(30.0))
+        u = (x - nx / 2) * c + (y - ny / 2) * s_
+        v = -(x - nx / 2) * s_ + (y - ny / 2) * c
+        outside = (np.abs(u) > 0.36 * nx) | (np.abs(v) > 0.36 * ny)
+        cube[:, outside] = np.nan
+    if kind == "gama511867":
+        second = (cube * np.float32(0.4)).astype(np.float32) + _noise(_rng(config_id, stream=4), dims)
+        return cube, second
+    return cube

@@ -32,6 +32,12 @@ PAPER_SMOOTH = dict(name="paper-smoothing-512^3-U01-persp-1000^2", n=512, width=
                     yaws=(0.0, 120.0, 240.0), pitch=20.0, lo=0.0, hi=1.0, opacity_scale=0.22,
                     clip=(0.9, 1.0), box_arms=(1, 2, 3, 4), gauss_taps=(5, 9, 13))
 
+# the paper's benchmark shapes (Section 6, Appendix B): U[0,1] cubes, a full rotation of views,
+# MIP over a sweep of canvas sizes and compositing with k = 0.22 and a 0.9 minimum threshold
+PAPER_SHAPE = dict(name="paper-shape-U01-128..1024^3-rotation36", cubes=(128, 256, 512, 1024),
+                   canvases=(500, 1000, 1500, 2000), views=36, pitch=20.0, step=0.5, opacity_scale=0.22,
+                   clip=(0.9, 1.0))
+
 DIFF = dict(name="diff-256^3-persp-512^2", dims=(256, 256, 256), yaw=30.0, pitch=20.0, width=512, height=512,
             step=0.5, opacity_scale=0.02, target_scale=1.2, lut_sigma=0.05, ckpt_interval=64)
 

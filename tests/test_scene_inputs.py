@@ -52,3 +52,21 @@ def test_batch_dims_and_paper_cubes():
     assert abs(float(np.median(logs)) - 0.5 * (math.log(32) + math.log(256))) < 0.1
     u = scene.paper_uniform_cube(32)
     assert u.shape == (32, 32, 32) and u.min() >= 0.0 and u.max() < 1.0 and abs(float(u.mean()) - 0.5) < 0.01
+
+
+def test_paper_standins_follow_their_recipe():
+    """The stand-ins for the paper's three cubes: shapes of Section 5.2, noise of unit sigma,
+    maxima near the reported maximum / sigma, NaN outside the Antennae mosaic's footprint."""
+    for kind, (lo_max, hi_max) in (("ngc2903", (12.0, 25.0)), ("antennae", (50.0, 90.0))):
+        c = scene.paper_standin(kind)
+        nx, ny, nz = scene.STANDIN_DIMS[kind]
+        assert c.shape == (nz, ny, nx) and c.dtype == np.float32
+        assert lo_max <= float(np.nanmax(c)) <= hi_max, kind
+        corner = c[:, :20, :20]
+        if kind == "antennae":
+            assert np.isnan(corner).all() and not np.isnan(c[:, ny // 2, nx // 2]).any()
+        else:
+            assert abs(float(corner.std()) - 1.0) < 0.05
+    ha, n2 = scene.paper_standin("gama511867")
+    assert ha.shape == n2.shape == (37, 50, 50)
+    assert 6.0 <= float(ha.max()) <= 12.0

@@ -72,3 +72,21 @@ def test_smooth_tma_and_staged_paths_agree(m):
     with m.debug_flags("smooth_plain"):
         b = _gpu_smooth(m, cube, 2.0, 6)
     assert np.abs(a - b).max() <= 1e-6 * float(cube.max() - cube.min())
+
+
+def test_smooth_wait_timeout_is_reported_and_recovered(m):
+    """Device-side waits are bounded: with SHW_DEBUG_FAULT_TIMEOUT the smoothing leaves one
+    plane's tensor copy unissued, every CTA's bounded wait for it runs out, the CTA waits for its
+    own copies in flight and returns, and shw_sync_status reports SHW_ETIMEOUT.  The next
+    normal call runs clean and correct (no GPU fault is involved)."""
+    cube = scene.tiny_cube(config_id=26, dims=(64, 48, 40), n_sources=2)
+    ct = to_dev(cube)
+    with m.debug_flags("fault_timeout"):
+        m.smooth(ct, 1.0, 3)
+        with pytest.raises(m.ShwError) as e:
+            m.sync_status()
+    assert e.value.status == 5  # SHW_ETIMEOUT
+    m.sync_status()  # the error word was cleared by the report
+    g = _gpu_smooth(m, cube, 1.0, 3)
+    o = oracle.smooth(cube, oracle.gauss_weights(1.0, 3))
+    assert np.abs(g - o).max() <= TOL_F32 * float(cube.max() - cube.min())
