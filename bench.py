@@ -928,9 +928,15 @@ def run_case(args):
             lut = torch.from_numpy(scene.ratio_lut()).cuda()
         fn = lambda: shw.render(vol, cam, args.mode, lut=lut, scalar=False, index=False,  # noqa: E731
                                 nsamples=False, out=o, **kw)
+        units = int(shw.render(vol, cam, args.mode, lut=lut, scalar=False, index=False, **kw)["nsamples"].sum(
+            dtype=torch.int64).item())
     t = _timeit(torch, fn, reps=args.steps, warm=args.warmup)
     shw.sync_status()
-    print(f"{args.case} {args.mode} {args.dims}: {t:.4f} ms", flush=True)
+    if args.case in ("smooth", "smooth-zip"):
+        units = cube.numel()
+    print(json.dumps({"case": args.case, "mode": args.mode, "dims": args.dims, "smooth": args.smooth,
+                      "ms": round(t, 4), "units": units,
+                      "unit": "voxels" if args.case.startswith("smooth") else "samples"}), flush=True)
 
 
 def main():

@@ -104,7 +104,9 @@ __device__ __forceinline__ float to_f32(unsigned short raw);
 template <>
 __device__ __forceinline__ float to_f32<__nv_bfloat16>(unsigned short raw)
 {
-    return __uint_as_float(((unsigned)raw) << 16);
+    // the bfloat16 bits are the float's high half: raw * 2^16 (an integer multiply, on the
+    // FMA pipe, instead of a shift on the busier integer ALU pipe; same bits)
+    return __uint_as_float((unsigned)raw * 65536u);
 }
 template <>
 __device__ __forceinline__ float to_f32<__half>(unsigned short raw)
