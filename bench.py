@@ -341,38 +341,53 @@ class E2EPipeline:
 
 def kernel_roofline(name, t_ms, nvox, samples_per, peaks, sm_mhz, image_bytes=0, sms=152):
     """Algorithmic work per launch / measured duration, against the bound of that kernel.
-    Renders also report their HBM fraction (cube bytes read once + image written, over the
-    time, against the measured copy rate) and, where a capture exists, the ncu DRAM fraction."""
+
+    Smoothing: HBM bytes.  The method moves 8 B per voxel (read the cube, write its smoothed
+    copy); the second smoothing also re-reads the first result and writes both into the line
+    ratio's interleaved pair storage (16 B per voxel moved), reported beside as frac_moved.
+    Renders: instruction issue.  Their loops run out of shared memory and are bound by the
+    schedulers, so the roofline is warp instructions issued per second (the ncu count per
+    sample of this build times the samples, over the time) against SMs x 4 schedulers x SM
+    clock; the HBM fraction of the cube bytes read once and the image written, and the FP32
+    fraction of the method's flops, are reported beside."""
     hbm = float(peaks["hbm_gbs"])
-    if name.startswith("smooth"):
-        # read the cube once, write the result once; the second smoothing also reads the
-        # first smoothed cube and writes both into the line ratio's pair storage
-        bytes_ = (16 if name == "smooth2" else 8) * nvox
-        ach = bytes_ / (t_ms * 1e-3) / 1e9
-        return {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(ach / hbm, 4), "algorithmic_bytes": bytes_}
-    mode = name[len("render_"):]
-    ns = samples_per[mode]
-    flops = ALG_FLOPS_PER_SAMPLE[mode] * ns
-    peak = FP32_LANES_PER_SM * 2 * sms * float(sm_mhz) * 1e6 / 1e12  # TFLOP/s (FMA = 2)
-    ach = flops / (t_ms * 1e-3) / 1e12
-    loaded = peaks.get("clocks_under_load", {}).get("sm_mhz_median")
-    cube_bytes = (8 if mode == "ratio" else 4) * nvox  # the ratio reads both cubes
-    alg_bytes = cube_bytes + image_bytes
-    rec = {"bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-           "frac": round(ach / peak, 4), "samples": ns,
-           "gsamples_per_s": round(ns / (t_ms * 1e-3) / 1e9, 2),
-           "hbm_frac": round(alg_bytes / (t_ms * 1e-3) / 1e9 / hbm, 4), "algorithmic_bytes": alg_bytes}
-    if loaded:  # the ALU fraction against the loaded median clock recorded with the peaks
-        peak_l = FP32_LANES_PER_SM * 2 * sms * float(loaded) * 1e6 / 1e12
-        rec["frac_at_loaded_median_clock"] = round(ach / peak_l, 4)
     traffic = TRAFFIC_PER_LAUNCH.get(name)
+    if name.startswith("smooth"):
+        bytes_ = 8 * nvox
+        ach = bytes_ / (t_ms * 1e-3) / 1e9
+        rec = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+               "frac": round(ach / hbm, 4), "algorithmic_bytes": bytes_}
+        if name == "smooth2":
+            moved = 16 * nvox
+            rec["moved_bytes"] = moved
+            rec["frac_moved"] = round(moved / (t_ms * 1e-3) / 1e9 / hbm, 4)
+    else:
+        mode = name[len("render_"):]
+        ns = samples_per[mode]
+        cube_bytes = (8 if mode == "ratio" else 4) * nvox  # the ratio reads both cubes
+        alg_bytes = cube_bytes + image_bytes
+        flops = ALG_FLOPS_PER_SAMPLE[mode] * ns
+        fp32_peak = FP32_LANES_PER_SM * 2 * sms * float(sm_mhz) * 1e6 / 1e12  # TFLOP/s (FMA = 2)
+        rec = {"samples": ns, "gsamples_per_s": round(ns / (t_ms * 1e-3) / 1e9, 2),
+               "hbm_frac": round(alg_bytes / (t_ms * 1e-3) / 1e9 / hbm, 4), "algorithmic_bytes": alg_bytes,
+               "fp32_frac_alg_flops": round(flops / (t_ms * 1e-3) / 1e12 / fp32_peak, 4)}
+        ips = WARP_INST_PER_SAMPLE.get(mode)
+        if ips:
+            peak = sms * SCHEDULERS_PER_SM * float(sm_mhz) * 1e6 / 1e9  # G warp instructions / s
+            ach = ips * ns / (t_ms * 1e-3) / 1e9
+            rec = {"bound": "alu", "achieved": round(ach, 1), "peak": round(peak, 1), "unit": "Gwarp-inst/s",
+                   "frac": round(ach / peak, 4), "warp_inst_per_sample": ips, **rec}
+        else:  # no instruction count for this build: the FP32 roofline of the method's flops
+            ach = flops / (t_ms * 1e-3) / 1e12
+            rec = {"bound": "alu", "achieved": round(ach, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",
+                   "frac": round(ach / fp32_peak, 4), **rec}
     if traffic:
         rec["dram_frac_ncu_bytes"] = round(traffic / (t_ms * 1e-3) / 1e9 / hbm, 4)
     return rec
 
 
 FP32_LANES_PER_SM = 128
+SCHEDULERS_PER_SM = 4  # each issues at most one warp instruction per cycle
 # FP32 flops the method needs per trilinear sample: 3 fraction weights,
 # 7 lerps (sub + FMA = 3 flops), plus the transfer function's own arithmetic.
 _TRI = 3 + 7 * 3
@@ -495,7 +510,12 @@ def run_ours(args):
     if rank == 0:
         dr = dict(roof[dom])
         dr["kernel"] = dom
-        dr["peak_source"] = f"{peaks_src} ({'MEASURED_PEAKS.json hbm_gbs' if dr['bound'] == 'hbm' else 'SMs x 128 FP32 lanes x 2 x median SM clock under load'})"
+        if dr["bound"] == "hbm":
+            dr["peak_source"] = f"{peaks_src} (MEASURED_PEAKS.json hbm_gbs)"
+        elif dr["unit"] == "Gwarp-inst/s":
+            dr["peak_source"] = "SMs x 4 schedulers x median SM clock under load (one warp instruction per cycle each)"
+        else:
+            dr["peak_source"] = "SMs x 128 FP32 lanes x 2 x median SM clock under load"
         dr["traffic"] = TRAFFIC_PER_LAUNCH.get(dom)
         res = {
             "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -523,10 +543,13 @@ def run_ours(args):
     return res, samples_per
 
 
-# ncu DRAM bytes (read + write) per launch of each step kernel of the current build (from one
-# capture of each kernel on the profiling case, scaled to the full launch as recorded under
-# profiles/); empty until such a capture exists -- the JSON line then reports traffic null
+# ncu counters of the step's kernels in the current build, per launch of the full-size step
+# (one capture each, recorded under profiles/ with its command); an entry is removed when its
+# kernel changes, and the JSON line then reports traffic null (or the flop roofline).
+# DRAM bytes (read + write) per launch:
 TRAFFIC_PER_LAUNCH: dict = {}
+# warp instructions executed per sample of each render:
+WARP_INST_PER_SAMPLE: dict = {}
 
 
 # --------------------------------------------------------------------------- variants

@@ -6,9 +6,10 @@
 //   - one producer thread stages the tile's footprint of each z plane into shared
 //     memory with cp.async.bulk.tensor, through a ring of kAxStages stages with a
 //     "full" and an "empty" mbarrier each (every wait bounded);
-//   - eight consumer warps own four rays per thread, in pairs; each ray turns each
-//     plane into one bilinear value (4 shared loads), in the same order of operations
-//     as the general trilinear interpolation, and each warp releases the stage;
+//   - the consumer warps (8 with four rays per thread for MIP, 16 with two for the
+//     other modes) own their rays in pairs; each ray turns each plane into one bilinear
+//     value (4 shared loads), in the same order of operations as the general trilinear
+//     interpolation, and each warp releases the stage;
 //   - the samples that fall between two planes (the same for every ray) are one
 //     lerp each, fed to the same transfer-function state as the general marcher.
 // When the step is exactly 1/Q voxel every interior cell holds Q samples at the same
@@ -26,25 +27,30 @@
 
 namespace shw {
 
-#ifndef SHW_AX_WARPS
-#define SHW_AX_WARPS 8
-#endif
-#ifndef SHW_AX_RAYS
-#define SHW_AX_RAYS 4
-#endif
 #ifndef SHW_AX_STAGES
 #define SHW_AX_STAGES 8
 #endif
-constexpr int kAxWarps = SHW_AX_WARPS;                  // consumer warps
-constexpr int kAxRays = SHW_AX_RAYS;                    // rays per consumer thread (even: they go in pairs)
-constexpr int kAxPairs = kAxRays / 2;
-constexpr int kAxTX = 64, kAxTY = kAxWarps * kAxPairs;  // pixel tile of one CTA
-constexpr int kAxThreads = 32 * (kAxWarps + 1);         // consumers + one producer warp
-constexpr int kAxStages = SHW_AX_STAGES;                // ring depth (a power of two)
+constexpr int kAxTX = 64, kAxTY = 16;    // pixel tile of one CTA
+constexpr int kAxStages = SHW_AX_STAGES;  // ring depth (a power of two)
 constexpr int kAxSmemLimit = 100 * 1024;
 constexpr int kAxMaxQ = 4;  // periodic stepping: at most this many samples per cell
-static_assert(kAxRays % 2 == 0, "rays go in pairs");
 static_assert((kAxStages & (kAxStages - 1)) == 0, "the ring depth is a power of two");
+
+// W consumer warps share the tile's 16 rows: each thread owns 32 / W rays, in pairs (one row
+// each, the pair's rays 32 columns apart), plus one producer warp.  Eight warps of four rays
+// give MIP the most independent work per warp; sixteen warps of two rays hide more latency
+// for the transfer functions with longer per-sample chains (average, spectral, compositing,
+// first moment).
+template <int W>
+struct AxCfg {
+    static constexpr int warps = W, pairs = kAxTY / W, rays = 2 * pairs, threads = 32 * (W + 1);
+    static_assert(W * pairs == kAxTY, "the warps split the tile's rows evenly");
+};
+template <int MODE>
+constexpr int axis_warps()
+{
+    return (MODE == SHW_MIP || MODE == kMipValue) ? 8 : 16;
+}
 
 // The fixed staged box: enough for a 64 x 16 tile at up to one voxel per pixel,
 // axis-aligned (extent 63 x 15, plus the alignment and rounding margins).
@@ -91,7 +97,11 @@ __device__ __forceinline__ float2 lerp2v(float2 a, float2 b, float2 t) { return 
 
 // ray i of consumer thread (lane, warp): pair i / 2 is one row, its two rays 32 columns apart
 __device__ __forceinline__ int ray_px(int txi, int lane, int i) { return txi * kAxTX + lane + 32 * (i & 1); }
-__device__ __forceinline__ int ray_py(int tyi, int warp, int i) { return tyi * kAxTY + kAxPairs * warp + (i >> 1); }
+template <int P>
+__device__ __forceinline__ int ray_py(int tyi, int warp, int i)
+{
+    return tyi * kAxTY + P * warp + (i >> 1);
+}
 
 template <int MODE, class St>
 __device__ __forceinline__ void axis_emit(const RenderArgs &a, long long pix, bool hit, int N, long long PZ,
@@ -142,13 +152,13 @@ __device__ __forceinline__ void axis_emit(const RenderArgs &a, long long pix, bo
 }
 
 // MODE: a transfer function, or kMipValue.  UP: rays advance towards +z.  FIX: the
-// staged box is kFixBW x kFixBH (else A.bw x A.bh).
-template <int MODE, int INTERP, bool UP, bool FIX>
-__global__ void __launch_bounds__(kAxThreads, MODE == SHW_COMPOSITE ? 1 : 2)
+// staged box is kFixBW x kFixBH (else A.bw x A.bh).  W: consumer warps.
+template <int MODE, int INTERP, bool UP, bool FIX, int W = axis_warps<MODE>()>
+__global__ void __launch_bounds__(AxCfg<W>::threads, MODE == SHW_COMPOSITE ? 1 : 2)
     axis_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ vol, shw_camera cam, RenderArgs a,
                 AxisArgs A)
 {
-    constexpr int R = kAxRays, P = kAxPairs, S = kAxStages;
+    constexpr int R = AxCfg<W>::rays, P = AxCfg<W>::pairs, S = kAxStages;
     extern __shared__ __align__(128) float sm[];  // [stages][bh][bw]
     __shared__ __align__(8) uint64_t full[S], empty[S];
     __shared__ long long s_pz, s_dz;
@@ -156,7 +166,7 @@ __global__ void __launch_bounds__(kAxThreads, MODE == SHW_COMPOSITE ? 1 : 2)
     __shared__ volatile int s_quit;  // 1: every ray has stopped, or a wait gave up
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool consumer = warp < kAxWarps;
+    const bool consumer = warp < W;
     const int tile = blockIdx.x, tyi = tile / A.tiles_x, txi = tile - tyi * A.tiles_x;
     const int bw = FIX ? kFixBW : A.bw, bh = FIX ? kFixBH : A.bh;
     const int stride = FIX ? kFixStride : A.stage_stride;
@@ -180,7 +190,7 @@ __global__ void __launch_bounds__(kAxThreads, MODE == SHW_COMPOSITE ? 1 : 2)
         for (int s = 0; s < S; ++s) s_bad |= !tma_dst_ok(sm + s * stride, A.err);
         for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kAxWarps);
+            mbar_init(&empty[s], W);
         }
         fence_barrier_init();
     }
@@ -191,7 +201,7 @@ __global__ void __launch_bounds__(kAxThreads, MODE == SHW_COMPOSITE ? 1 : 2)
 #pragma unroll
     for (int i = 0; i < R; ++i) {
         X[i] = Y[i] = 0;
-        const int px = ray_px(txi, lane, i), py = ray_py(tyi, warp, i);
+        const int px = ray_px(txi, lane, i), py = ray_py<P>(tyi, warp, i);
         RayFx r;
         if (consumer && px < a.width && py < a.height && setup_ray(cam, px, py, A.nx, A.ny, A.nz, a.step, r) &&
             min(r.N, a.nmax) > 0) {
@@ -215,7 +225,7 @@ __global__ void __launch_bounds__(kAxThreads, MODE == SHW_COMPOSITE ? 1 : 2)
     if (s_any == 0) {   // no ray of this tile meets the cube
         if (consumer)
             for (int i = 0; i < R; ++i) {
-                const int px = ray_px(txi, lane, i), py = ray_py(tyi, warp, i);
+                const int px = ray_px(txi, lane, i), py = ray_py<P>(tyi, warp, i);
                 if (px < a.width && py < a.height)
                     axis_emit<MODE>(a, (long long)py * a.width + px, false, 0, 0, 0, INTERP == SHW_NEAREST,
                                     typename AxisStateOf<MODE>::type{}, 0);
@@ -369,7 +379,7 @@ __global__ void __launch_bounds__(kAxThreads, MODE == SHW_COMPOSITE ? 1 : 2)
     for (int i = 0; i < R; ++i) {
         done[i] = NS;
         if constexpr (MODE == SHW_COMPOSITE) {
-            const long long pix = (long long)ray_py(tyi, warp, i) * a.width + ray_px(txi, lane, i);
+            const long long pix = (long long)ray_py<P>(tyi, warp, i) * a.width + ray_px(txi, lane, i);
             st[i].lut = a.lut;
             st[i].lo = a.lo;
             st[i].inv_range = a.inv_range;
@@ -391,7 +401,7 @@ __global__ void __launch_bounds__(kAxThreads, MODE == SHW_COMPOSITE ? 1 : 2)
     // COMPOSITE: rays still taking samples (a ray that misses counts as stopped)
     int live = hitmask;
     bool idle = __all_sync(0xffffffffu, hitmask == 0);
-    if (idle && lane == 0 && atomicAdd(&s_nidle, 1) + 1 == kAxWarps) s_quit = 1;
+    if (idle && lane == 0 && atomicAdd(&s_nidle, 1) + 1 == W) s_quit = 1;
     // COMPOSITE: every 16 cells a warp whose rays have all stopped turns idle; when the
     // last warp does, the sweep ends
     int ncell = 0;
@@ -401,7 +411,7 @@ __global__ void __launch_bounds__(kAxThreads, MODE == SHW_COMPOSITE ? 1 : 2)
             if (!idle && ncell >= 16) {
                 ncell = 0;
                 idle = __all_sync(0xffffffffu, live == 0);
-                if (idle && lane == 0 && atomicAdd(&s_nidle, 1) + 1 == kAxWarps) s_quit = 1;
+                if (idle && lane == 0 && atomicAdd(&s_nidle, 1) + 1 == W) s_quit = 1;
             }
         }
     };
@@ -606,7 +616,7 @@ __global__ void __launch_bounds__(kAxThreads, MODE == SHW_COMPOSITE ? 1 : 2)
 
 #pragma unroll
     for (int i = 0; i < R; ++i) {
-        const int px = ray_px(txi, lane, i), py = ray_py(tyi, warp, i);
+        const int px = ray_px(txi, lane, i), py = ray_py<P>(tyi, warp, i);
         if (px < a.width && py < a.height)
             axis_emit<MODE>(a, (long long)py * a.width + px, (hitmask >> i) & 1, N, PZ, DZ, INTERP == SHW_NEAREST,
                             st[i], done[i]);
@@ -626,7 +636,7 @@ shw_status launch_axis(int mode, int interp, bool up, const CUtensorMap &map, co
         /* static + dynamic shared memory may pass the 48 KB default: always opt in */                \
         cudaFuncSetAttribute(axis_kernel<M, I, U, FIX>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                              (int)smem);                                                                \
-        axis_kernel<M, I, U, FIX><<<grid, kAxThreads, smem, st>>>(map, data, c, a, A);                 \
+        axis_kernel<M, I, U, FIX><<<grid, AxCfg<axis_warps<M>()>::threads, smem, st>>>(map, data, c, a, A);  \
     } while (0)
 #define SHW_AXI(M, I)           \
     if (up) SHW_AX(M, I, true); \

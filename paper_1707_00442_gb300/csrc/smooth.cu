@@ -100,29 +100,39 @@ __global__ void __launch_bounds__(32 * (32 / YB)) smooth_kernel(const float *__r
 // TMA pipeline (radius 1..8, nx a multiple of 4, 16-byte aligned cube).
 //
 // Per CTA: a 32 x 32 (x, y) output block and a chunk of z planes.  One thread
-// issues cp.async.bulk.tensor loads of the (32+16) x (32+2r) input tile of each
-// plane into a 3-stage shared ring, signalled through mbarriers; the box's
-// x start (x0 - 8) keeps the TMA coordinate 16-byte aligned.  Out-of-range
-// elements arrive as zeros and, in blocks touching the cube's faces, are replaced
-// by the edge values (clamp-to-edge).  Then:
-//   x-pass: each thread makes 4 consecutive outputs of a row from 5 float4 reads;
-//   y-pass: each thread makes 2 rows x 2 adjacent columns with packed FP32x2 FMAs
-//           (__ffma2_rn, rounding identical to two scalar FMAs);
-//   z-pass: from a ring of the last 2r+1 y-pass results held in registers and
-//           indexed at compile time (the z loop is unrolled 2r+1 times), written
-//           straight to HBM as float2.
-constexpr int kSmTX = 32, kSmTY = 32, kSmXP = 8, kSmBW = kSmTX + 2 * kSmXP, kSmStages = 3, kSmThreads = 256;
+// issues cp.async.bulk.tensor loads of the 52 x (32+2r) input box of each plane
+// into a 3-stage shared ring, signalled through mbarriers; the box's x start
+// (x0 - 8) keeps the TMA coordinate 16-byte aligned.  Out-of-range elements arrive
+// as zeros and, in blocks touching the cube's faces, are replaced by the edge values
+// (clamp-to-edge).  Then:
+//   x-pass: 4(32+2r) threads each make 8 consecutive outputs of a row from at most
+//           six float4 reads, as four packed FP32x2 accumulators (__ffma2_rn rounds
+//           each lane exactly as a scalar FMA, in the same tap order);
+//   y-pass: each thread makes 2 rows x 2 adjacent columns with packed FMAs;
+//   z-pass: from a ring of the last 2r+1 y-pass results held in registers, written
+//           straight to HBM as float2.  The ring slot of a plane is picked by one
+//           switch, so every ring index is a compile-time constant.
+// The stage rows are 52 floats apart and the x-pass rows 36: the 16-byte shared
+// accesses of eight consecutive threads (two rows) then fall on distinct banks.
+constexpr int kSmTX = 32, kSmTY = 32, kSmXP = 8, kSmBW = 52, kSmXPitch = 36, kSmStages = 3, kSmThreads = 256;
 
-// Call f(std::integral_constant<int, v>) for the runtime value v in [0, N): the callee sees
-// v as a compile-time constant (a chain of N compares selects the instance).
-template <int N, int S = 0, class F>
+// Call f(std::integral_constant<int, v>) for the runtime value v in [0, N) through one
+// switch: the callee sees v as a compile-time constant.
+template <int N, class F>
 __device__ __forceinline__ void static_slot(int v, F &&f)
 {
-    if constexpr (S < N) {
-        if (v == S)
-            f(std::integral_constant<int, S>{});
-        else
-            static_slot<N, S + 1>(v, f);
+    static_assert(N <= 2 * SHW_MAX_SMOOTH_RADIUS + 1 && N <= 17, "one case per ring slot");
+    switch (v) {
+#define SHW_SLOT(n)                                                  \
+    case n:                                                          \
+        if constexpr (n < N) f(std::integral_constant<int, n>{});    \
+        break;
+        SHW_SLOT(0) SHW_SLOT(1) SHW_SLOT(2) SHW_SLOT(3) SHW_SLOT(4) SHW_SLOT(5) SHW_SLOT(6) SHW_SLOT(7)
+        SHW_SLOT(8) SHW_SLOT(9) SHW_SLOT(10) SHW_SLOT(11) SHW_SLOT(12) SHW_SLOT(13) SHW_SLOT(14)
+        SHW_SLOT(15) SHW_SLOT(16)
+#undef SHW_SLOT
+    default:
+        break;
     }
 }
 
@@ -153,22 +163,65 @@ __device__ __forceinline__ void clamp_tile_edges(float *tile, int c_lo, int c_hi
     }
 }
 
-constexpr int kSmoothZipMinBlocks = 2;  // the zip form holds the first cube's values of a plane in registers too
-constexpr int kSmoothMinBlocks = 3;     // resident CTAs per SM the plain form is compiled for
+// x-pass of eight consecutive outputs: row points at the staged row, (8 q) floats in;
+// output 2p + e takes the taps at row[kSmXP - R + 2p + e + k], k = 0..2R, accumulated in
+// tap order from +0 (the scalar pass's rounding, two outputs per packed FMA).
+template <int R>
+__device__ __forceinline__ void xpass8(const float *row, float *dst, const SmoothWeights &W)
+{
+    constexpr int F0 = (kSmXP - R) / 4, F1 = (kSmXP + 7 + R) / 4, NF = F1 - F0 + 1;
+    constexpr int B = kSmXP - R - 4 * F0;  // v index of output 0's first tap
+    static_assert(B + 7 + 2 * R < 4 * NF, "the float4 reads cover every tap");
+    float v[4 * NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        const float4 q = reinterpret_cast<const float4 *>(row)[F0 + f];
+        v[4 * f] = q.x;
+        v[4 * f + 1] = q.y;
+        v[4 * f + 2] = q.z;
+        v[4 * f + 3] = q.w;
+    }
+    float2 acc[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) acc[p] = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int k = 0; k < 2 * R + 1; ++k)
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+            acc[p] = __ffma2_rn(W.w2[k], make_float2(v[B + 2 * p + k], v[B + 2 * p + k + 1]), acc[p]);
+    reinterpret_cast<float4 *>(dst)[0] = make_float4(acc[0].x, acc[0].y, acc[1].x, acc[1].y);
+    reinterpret_cast<float4 *>(dst)[1] = make_float4(acc[2].x, acc[2].y, acc[3].x, acc[3].y);
+}
+
+// resident CTAs per SM each form is compiled for (register budget 65536 / (256 x blocks)):
+// the zip form holds the first cube's values of a plane in registers too, and radii above
+// 6 hold a longer z ring
+template <int R, bool ZIP>
+constexpr int smooth_min_blocks()
+{
+    return (ZIP || R > 6) ? 2 : 3;
+}
+
+// floats from one ring stage to the next: the box, rounded up to 128 bytes (TMA destinations)
+template <int R>
+constexpr int smooth_stage_floats()
+{
+    return ((kSmTY + 2 * R) * kSmBW + 31) & ~31;
+}
 
 template <int R, bool ZIP>
-__global__ void __launch_bounds__(kSmThreads, ZIP ? kSmoothZipMinBlocks : kSmoothMinBlocks)
+__global__ void __launch_bounds__(kSmThreads, smooth_min_blocks<R, ZIP>())
     smooth_tma_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict__ out, int nx, int ny, int nz,
                       int zchunk, SmoothWeights W, unsigned *err, const float *__restrict__ first, int skip_plane,
                       int polls)
 {
     constexpr int IH = kSmTY + 2 * R, K = 2 * R + 1;
-    constexpr int STAGE_FLOATS = IH * kSmBW;
-    static_assert((STAGE_FLOATS * 4) % 128 == 0, "TMA stage buffers must start on 128 bytes");
-    constexpr uint32_t STAGE_BYTES = STAGE_FLOATS * 4;
+    constexpr int STAGE_FLOATS = smooth_stage_floats<R>();
+    constexpr uint32_t STAGE_BYTES = IH * kSmBW * 4;  // what one copy lands
+    static_assert(4 * IH <= kSmThreads, "one x-pass unit per thread");
     extern __shared__ __align__(128) float smem[];
-    float *s_in = smem;                             // [stages][IH][BW]
-    float *s_xp = smem + kSmStages * STAGE_FLOATS;  // [2][IH][TX]
+    float *s_in = smem;                             // [stages][IH][BW] (stage stride STAGE_FLOATS)
+    float *s_xp = smem + kSmStages * STAGE_FLOATS;  // [2][IH][XPitch]
     __shared__ __align__(8) uint64_t bars[kSmStages];
 
     const int tid = threadIdx.x;
@@ -199,10 +252,21 @@ __global__ void __launch_bounds__(kSmThreads, ZIP ? kSmoothZipMinBlocks : kSmoot
     const int r_lo = max(0, R - y0), r_hi = min(IH - 1, ny - 1 - (y0 - R));
     const bool edge = c_lo > 0 || c_hi < kSmBW - 1 || r_lo > 0 || r_hi < IH - 1;
 
+    // x-pass unit of this thread: row xr, outputs 8 xq .. 8 xq + 7
+    const bool xunit = tid < 4 * IH;
+    const int xsrc = (tid >> 2) * kSmBW + 8 * (tid & 3), xdst = (tid >> 2) * kSmXPitch + 8 * (tid & 3);
+
     // y/z passes: each thread owns columns 2cp, 2cp+1 of rows 2rg, 2rg+1, kept as
     // float2 pairs so that packed FP32x2 FMAs need no operand shuffling
     const int lane = tid & 31, cp = lane & 15, rg = (lane >> 4) + 2 * (tid >> 5);
-    const int gx = x0 + 2 * cp;
+    const int gx = x0 + 2 * cp, gy = y0 + 2 * rg;
+    const bool st0 = gx < nx && gy < ny, st1 = gx < nx && gy + 1 < ny;
+    // outputs of plane zb at rows gy, gy + 1 (pair units for the zip form); advanced by a
+    // plane per plane written.  ZIP: the first cube's values of the same voxels.
+    constexpr int OE = ZIP ? 2 : 1;
+    float *op = out + ((size_t)zb * plane + (size_t)gy * nx + gx) * OE;
+    const float *fp = ZIP ? first + (size_t)zb * plane + (size_t)gy * nx + gx : nullptr;
+    const size_t orow = (size_t)nx * OE;
     float2 ring[2][K];
 #pragma unroll
     for (int j = 0; j < 2; ++j)
@@ -211,45 +275,23 @@ __global__ void __launch_bounds__(kSmThreads, ZIP ? kSmoothZipMinBlocks : kSmoot
 
     bool failed = false;
     int fail_i = 0;  // the plane whose wait gave up
+    int stage = 0, slot = 0;
+    uint32_t phase = 0;
     for (int i = 0; i < nplanes; ++i) {
-        const int stage = i % kSmStages;
         // ZIP: this plane's output pairs take the first cube's values; load them now, so
         // the latency hides behind the passes (a lane outside the cube loads nothing)
         float2 fpre[2] = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
         if constexpr (ZIP) {
-            if (i >= 2 * R && gx < nx) {
-                const size_t zrow = (size_t)(zfirst + i - R) * plane;
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int gy = y0 + 2 * rg + j;
-                    if (gy < ny) fpre[j] = __ldg(reinterpret_cast<const float2 *>(first + zrow + (size_t)gy * nx + gx));
-                }
+            if (i >= 2 * R) {
+                if (st0) fpre[0] = __ldg(reinterpret_cast<const float2 *>(fp));
+                if (st1) fpre[1] = __ldg(reinterpret_cast<const float2 *>(fp + nx));
             }
         }
-        const bool ok = mbar_wait(&bars[stage], (uint32_t)((i / kSmStages) & 1), err, polls);
+        const bool ok = mbar_wait(&bars[stage], phase, err, polls);
         float *tile = s_in + stage * STAGE_FLOATS;
         if (edge) clamp_tile_edges<IH>(tile, c_lo, c_hi, r_lo, r_hi, tid);
-        float *xp = s_xp + (i & 1) * IH * kSmTX;
-        // x-pass: unit u -> row u/8, outputs 4q .. 4q+3 with q = u%8
-        for (int u = tid; u < IH * 8; u += kSmThreads) {
-            const int r = u >> 3, q = u & 7;
-            const float4 *src = reinterpret_cast<const float4 *>(tile + r * kSmBW + 4 * q);
-            float v[20];
-#pragma unroll
-            for (int t = 0; t < 5; ++t) {
-                const float4 f = src[t];
-                v[4 * t] = f.x;
-                v[4 * t + 1] = f.y;
-                v[4 * t + 2] = f.z;
-                v[4 * t + 3] = f.w;
-            }
-            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-            for (int k = 0; k < K; ++k)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[j] = __fmaf_rn(W.w[k], v[kSmXP - R + j + k], acc[j]);
-            *reinterpret_cast<float4 *>(xp + r * kSmTX + 4 * q) = make_float4(acc[0], acc[1], acc[2], acc[3]);
-        }
+        float *xp = s_xp + (i & 1) * IH * kSmXPitch;
+        if (xunit) xpass8<R>(tile + xsrc, xp + xdst, W);
         if (edge) fence_proxy_async();  // the edge clamp wrote the stage that a tensor copy refills next
         // one barrier per plane: it orders the x pass before the refill and the y pass, and
         // reports a wait that gave up (the x pass then read a stage whose copy may not have
@@ -264,11 +306,15 @@ __global__ void __launch_bounds__(kSmThreads, ZIP ? kSmoothZipMinBlocks : kSmoot
             mbar_arrive_expect_tx(&bars[stage], STAGE_BYTES);
             tma_load_3d(tile, &tmap, x0 - kSmXP, y0 - R, min(max(zfirst + i + kSmStages, 0), nz - 1), &bars[stage]);
         }
+        if (++stage == kSmStages) {
+            stage = 0;
+            phase ^= 1u;
+        }
         // y-pass of this plane
-        const float2 *xp2 = reinterpret_cast<const float2 *>(xp);
+        const float2 *xp2 = reinterpret_cast<const float2 *>(xp) + rg * kSmXPitch + cp;  // row 2 rg
         float2 col[2 + 2 * R];
 #pragma unroll
-        for (int m = 0; m < 2 + 2 * R; ++m) col[m] = xp2[(2 * rg + m) * (kSmTX / 2) + cp];
+        for (int m = 0; m < 2 + 2 * R; ++m) col[m] = xp2[m * (kSmXPitch / 2)];
         float2 yv[2];
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
@@ -280,31 +326,35 @@ __global__ void __launch_bounds__(kSmThreads, ZIP ? kSmoothZipMinBlocks : kSmoot
         // into the register ring at slot i mod K, then the z-pass: the ring holds planes
         // i-2R .. i (oldest in slot (slot+1) mod K).  Only this part is instanced per slot,
         // so the ring is indexed at compile time.
-        static_slot<K>(i % K, [&](auto sc) {
-            constexpr int slot = decltype(sc)::value;
-            ring[0][slot] = yv[0];
-            ring[1][slot] = yv[1];
-            if (i >= 2 * R) {
-                const int zo = zfirst + i - R;
+        const bool emit = i >= 2 * R;
+        static_slot<K>(slot, [&](auto sc) {
+            constexpr int sl = decltype(sc)::value;
+            ring[0][sl] = yv[0];
+            ring[1][sl] = yv[1];
+            if (emit) {
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
-                    const int gy = y0 + 2 * rg + j;
                     float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
-                    for (int k = 0; k < K; ++k) acc = __ffma2_rn(W.w2[k], ring[j][(slot + 1 + k) % K], acc);
-                    if (gx < nx && gy < ny) {
-                        const size_t o = (size_t)zo * plane + (size_t)gy * nx + gx;
+                    for (int k = 0; k < K; ++k) acc = __ffma2_rn(W.w2[k], ring[j][(sl + 1 + k) % K], acc);
+                    if (j == 0 ? st0 : st1) {
+                        float *o = op + j * orow;
                         if constexpr (ZIP) {
                             // (first, smoothed) for the voxels gx and gx + 1: one 16-byte store
                             const float2 f = fpre[j];
-                            *reinterpret_cast<float4 *>(out + 2 * o) = make_float4(f.x, acc.x, f.y, acc.y);
+                            *reinterpret_cast<float4 *>(o) = make_float4(f.x, acc.x, f.y, acc.y);
                         } else {
-                            *reinterpret_cast<float2 *>(out + o) = acc;
+                            *reinterpret_cast<float2 *>(o) = acc;
                         }
                     }
                 }
             }
         });
+        if (++slot == K) slot = 0;
+        if (emit) {
+            op += plane * OE;
+            if constexpr (ZIP) fp += plane;
+        }
     }
     if (failed && tid == 0) {
         // drain: wait (bounded) for this CTA's copies still in flight before leaving --
@@ -318,7 +368,7 @@ __global__ void __launch_bounds__(kSmThreads, ZIP ? kSmoothZipMinBlocks : kSmoot
 template <int R>
 static size_t smooth_tma_smem()
 {
-    return (size_t)(kSmStages * (kSmTY + 2 * R) * kSmBW + 2 * (kSmTY + 2 * R) * kSmTX) * 4;
+    return (size_t)(kSmStages * smooth_stage_floats<R>() + 2 * (kSmTY + 2 * R) * kSmXPitch) * 4;
 }
 
 constexpr int kSmoothMaxChunk = 128;  // largest z chunk of one CTA (planes), without a wave count

@@ -1,6 +1,6 @@
 """bench.py's host-side arithmetic on CPU: the roofline record of each kernel (algorithmic
-bytes or flops over the measured time, against the measured peak), the PCI ids that pick
-the benchmarked GPU's clock samples, and the clock record itself."""
+bytes, or warp instructions issued, over the measured time, against the peak), the PCI ids
+that pick the benchmarked GPU's clock samples, and the clock record itself."""
 import os
 import sys
 
@@ -21,26 +21,41 @@ def test_smooth_roofline_counts_read_and_write():
     assert r["algorithmic_bytes"] == 8 * nvox
     assert r["achieved"] == pytest.approx(8 * nvox / 1e-3 / 1e9, rel=1e-3)
     assert r["frac"] == pytest.approx(r["achieved"] / 6000.0, rel=1e-3)
-    # the zip form also reads the first cube's result and writes the 8-byte pair
+    # the zip form: the method's 8 bytes per voxel, and beside them the 16 it moves (it also
+    # re-reads the first cube's result and writes the 8-byte pair)
     z = bench.kernel_roofline("smooth2", 1.0, nvox, {}, PEAKS, 2000.0)
-    assert z["algorithmic_bytes"] == 16 * nvox
+    assert z["algorithmic_bytes"] == 8 * nvox and z["moved_bytes"] == 16 * nvox
+    assert z["frac_moved"] == pytest.approx(2 * z["frac"], rel=1e-3)
 
 
-def test_render_roofline_is_alu_flops_per_sample():
+def test_render_roofline_is_instruction_issue(monkeypatch):
     samples = {"mip": 10 ** 9, "composite": 10 ** 9, "ratio": 10 ** 9}
+    monkeypatch.setattr(bench, "WARP_INST_PER_SAMPLE", {"mip": 3.5, "composite": 4.5, "ratio": 4.0})
     r = bench.kernel_roofline("render_mip", 2.0, 1, samples, PEAKS, 2000.0)
-    peak = 152 * 128 * 2 * 2000e6 / 1e12
-    assert r["bound"] == "alu" and r["peak"] == pytest.approx(peak, rel=1e-3)
-    assert r["achieved"] == pytest.approx(bench.ALG_FLOPS_PER_SAMPLE["mip"] * 1e9 / 2e-3 / 1e12, rel=1e-3)
+    peak = 152 * 4 * 2000e6 / 1e9  # warp instructions per second, in G
+    assert r["bound"] == "alu" and r["unit"] == "Gwarp-inst/s" and r["peak"] == pytest.approx(peak, rel=1e-3)
+    assert r["achieved"] == pytest.approx(3.5 * 1e9 / 2e-3 / 1e9, rel=1e-3)
+    assert r["frac"] == pytest.approx(r["achieved"] / peak, rel=1e-3)
     assert r["gsamples_per_s"] == pytest.approx(500.0)
-    # the ratio samples two cubes per step, compositing does the most per sample
-    c = bench.kernel_roofline("render_composite", 2.0, 1, samples, PEAKS, 2000.0)
-    q = bench.kernel_roofline("render_ratio", 2.0, 1, samples, PEAKS, 2000.0)
-    assert c["achieved"] > r["achieved"] and q["achieved"] > r["achieved"]
+    # beside it, the FP32 fraction of the method's flops
+    fp32 = 152 * 128 * 2 * 2000e6 / 1e12
+    assert r["fp32_frac_alg_flops"] == pytest.approx(bench.ALG_FLOPS_PER_SAMPLE["mip"] * 1e9 / 2e-3 / 1e12 / fp32,
+                                                    rel=1e-3)
     # HBM fraction: the cube once (both cubes for the ratio) plus the image
     h = bench.kernel_roofline("render_ratio", 2.0, 10 ** 9, samples, PEAKS, 2000.0, image_bytes=160)
     assert h["algorithmic_bytes"] == 8 * 10 ** 9 + 160
     assert h["hbm_frac"] == pytest.approx((8e9 + 160) / 2e-3 / 1e9 / 6000.0, rel=1e-3)
+
+
+def test_render_roofline_without_a_count_falls_back_to_flops(monkeypatch):
+    samples = {"mip": 10 ** 9, "composite": 10 ** 9}
+    monkeypatch.setattr(bench, "WARP_INST_PER_SAMPLE", {})
+    r = bench.kernel_roofline("render_mip", 2.0, 1, samples, PEAKS, 2000.0)
+    peak = 152 * 128 * 2 * 2000e6 / 1e12
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s" and r["peak"] == pytest.approx(peak, rel=1e-3)
+    assert r["achieved"] == pytest.approx(bench.ALG_FLOPS_PER_SAMPLE["mip"] * 1e9 / 2e-3 / 1e12, rel=1e-3)
+    c = bench.kernel_roofline("render_composite", 2.0, 1, samples, PEAKS, 2000.0)
+    assert c["achieved"] > r["achieved"]  # compositing does the most per sample
 
 
 def test_pci_key_ignores_domain_width_and_case():
