@@ -546,10 +546,25 @@ def run_ours(args):
 # ncu counters of the step's kernels in the current build, per launch of the full-size step
 # (one capture each, recorded under profiles/ with its command); an entry is removed when its
 # kernel changes, and the JSON line then reports traffic null (or the flop roofline).
-# DRAM bytes (read + write) per launch:
-TRAFFIC_PER_LAUNCH: dict = {}
-# warp instructions executed per sample of each render:
-WARP_INST_PER_SAMPLE: dict = {}
+# DRAM bytes (read + write) per launch (profiles/survey_step_dram_traffic.md):
+TRAFFIC_PER_LAUNCH: dict = {
+    "smooth": 1386283008 + 1036524288,
+    "smooth2": 2387365376 + 2102186240,
+    "render_mip": 2084857600 + 17495808,
+    "render_avg": 2051461376 + 17522432,
+    "render_composite": 1855587328 + 18014464,
+    "render_spectral": 2120644864 + 17439232,
+    "render_ratio": 4133697280 + 25476608,
+}
+# warp instructions executed per sample of each render (same file: smsp__inst_executed.sum
+# over the render's samples, 371,839,071; compositing 359,686,584):
+WARP_INST_PER_SAMPLE: dict = {
+    "mip": 3.171,
+    "avg": 3.306,
+    "composite": 4.208,
+    "spectral": 3.271,
+    "ratio": 3.883,
+}
 
 
 # --------------------------------------------------------------------------- variants
@@ -917,7 +932,8 @@ def run_reference(args):
 
 
 def run_case(args):
-    """One small case of one kernel family, for profiler captures (prints its time, no JSON line)."""
+    """One small case of one kernel family, for profiler captures: prints one JSON line with its
+    median time and units (samples or voxels), not the benchmark's line."""
     import torch
     import paper_1707_00442_gb300 as shw
     from scene.camera import ortho_axis_camera

@@ -63,7 +63,9 @@ typedef enum {
     SHW_ECUDA = 3,         /* the CUDA runtime reported an error */
     SHW_ENOMEM = 4,        /* a caller buffer is too small, or a plan allocation failed */
     SHW_ETIMEOUT = 5,      /* a kernel's bounded wait for its own asynchronous copy gave up (shw_sync_status) */
-    SHW_EDEVICE = 6        /* no usable CUDA device */
+    SHW_EDEVICE = 6,       /* no usable CUDA device */
+    SHW_EBOUNDS = 7        /* a bounds-checked build (SHW_CHECKED) found an index outside its array
+                              (shw_sync_status; the access was clamped into the array) */
 } shw_status;
 
 typedef enum {
@@ -200,7 +202,12 @@ size_t shw_struct_size(int32_t which);
 uint64_t shw_launch_count(void);
 
 /* Wait for `stream` and report any error the CUDA runtime has latched, then the
- * library's device error word of the current device (SHW_ETIMEOUT; the word is cleared). */
+ * library's device error word of the current device (SHW_ETIMEOUT; the word is cleared).
+ * A library built with -DSHW_CHECKED (paper_1707_00442_gb300.build.build_checked) also
+ * checks every index its kernels take without clamping -- the interior fast paths of the
+ * samplers, the staged marcher's shared-memory reads, the plane sweep's offsets and planes,
+ * the smoothing's output planes -- clamps a violating one into its array and records it:
+ * this call then reports SHW_EBOUNDS (and clears the record). */
 shw_status shw_sync_status(void *stream);
 
 /* ---- smoothing (Section 4.2) ---------------------------------------------- */

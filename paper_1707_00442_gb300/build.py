@@ -68,5 +68,19 @@ def build(force: bool = False, verbose: bool = False, extra_flags=(), out: str |
     return lib_path
 
 
+CHECKED_LIB = os.path.join(PKG, "libshw_checked.so")
+
+
+def build_checked(force: bool = False, verbose: bool = False) -> str:
+    """The bounds-checked library (-DSHW_CHECKED, same ABI): every index a kernel takes
+    without clamping is checked, a violating one clamped into its array and recorded, and
+    shw_sync_status reports SHW_EBOUNDS.  A diagnosis build (slower), beside libshw.so."""
+    return build(force=force, verbose=verbose, extra_flags=("-DSHW_CHECKED",), out=CHECKED_LIB,
+                 obj_dir=os.path.join(PKG, "_obj_checked"))
+
+
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    if "--checked" in sys.argv:
+        print(build_checked(force="--force" in sys.argv, verbose=True))
+    else:
+        print(build(force="--force" in sys.argv, verbose=True))

@@ -185,6 +185,7 @@ extern "C" shw_status shw_render_backward(const shw_volume *vol, const shw_camer
                                           const float *grad_rgba, const void *ckpt, size_t ckpt_bytes,
                                           float *grad_vol, float *grad_lut, float *grad_scale, void *stream)
 {
+    NvtxRange nvtx_range("shw_render_backward");
     if (!valid_volume(vol) || !valid_camera(cam) || !valid_params(p, vol)) return SHW_EINVAL;
     if (p->mode != SHW_COMPOSITE || !grad_rgba || !ckpt || !aligned(grad_rgba, 16) || !aligned(ckpt, 4))
         return SHW_EINVAL;

@@ -9,12 +9,38 @@
 #include <cudaTypedefs.h>
 
 #include <mutex>
+#include <vector>
 
 #include "common.cuh"
 #include "render_impl.cuh"
 #include "tma.cuh"
 
 namespace shw {
+
+// The bounds-checked build's per-unit violation words (see SHW_CHECK): readers registered
+// while the library loads, polled by shw_sync_status.
+static std::mutex &check_mu()
+{
+    static std::mutex m;
+    return m;
+}
+static std::vector<CheckReader> &check_readers()
+{
+    static std::vector<CheckReader> v;
+    return v;
+}
+void register_check_reader(CheckReader r)
+{
+    std::lock_guard<std::mutex> g(check_mu());
+    check_readers().push_back(r);
+}
+unsigned read_check_words()
+{
+    std::lock_guard<std::mutex> g(check_mu());
+    unsigned v = 0;
+    for (CheckReader r : check_readers()) v |= r();
+    return v;
+}
 
 static std::atomic<uint64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -236,6 +262,7 @@ const char *shw_status_string(int32_t s)
     case SHW_ENOMEM: return "buffer too small or out of memory";
     case SHW_ETIMEOUT: return "timed out";
     case SHW_EDEVICE: return "no usable CUDA device";
+    case SHW_EBOUNDS: return "an index outside its array (bounds-checked build)";
     default: return "unknown status";
     }
 }
@@ -267,16 +294,16 @@ shw_status shw_sync_status(void *stream)
     if (e != cudaSuccess) return SHW_ECUDA;
     if (cudaGetLastError() != cudaSuccess) return SHW_ECUDA;
     unsigned *w = device_error_word();
+    unsigned v = 0;
     if (w) {
-        unsigned v = 0;
         if (cudaMemcpy(&v, w, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess) return SHW_ECUDA;
         if (v != 0) {
             const unsigned zero = 0;
             cudaMemcpy(w, &zero, sizeof zero, cudaMemcpyHostToDevice);
-            return SHW_ETIMEOUT;
         }
     }
-    return SHW_OK;
+    if (read_check_words() != 0) return SHW_EBOUNDS;  // (always 0 unless built with SHW_CHECKED)
+    return v != 0 ? SHW_ETIMEOUT : SHW_OK;
 }
 
 size_t shw_ckpt_bytes(const shw_volume *vol, const shw_camera *cam, const shw_render_params *p)
@@ -290,6 +317,7 @@ shw_status shw_render(const shw_volume *vol, const shw_volume *vol2, const shw_c
                       const shw_render_params *p, float *out_rgba, float *out_scalar, int32_t *out_index,
                       int32_t *out_nsamples, void *ckpt, size_t ckpt_bytes, void *stream)
 {
+    NvtxRange nvtx_range("shw_render");
     if (!valid_volume(vol) || !valid_camera(cam) || !valid_params(p, vol)) return SHW_EINVAL;
     if (!out_rgba || !aligned(out_rgba, 16)) return SHW_EINVAL;
     if ((out_scalar && !aligned(out_scalar, 4)) || (out_index && !aligned(out_index, 4)) ||

@@ -285,6 +285,7 @@ extern "C" {
 shw_status shw_batch_plan_create(shw_batch_plan **out, const shw_batch_item *items, int32_t n,
                                  const shw_render_params *p, int32_t flags, void *stream)
 {
+    NvtxRange nvtx_range("shw_batch_plan_create");
     if (!out) return SHW_EINVAL;
     *out = nullptr;
     if (!items || n <= 0 || !p || !p->lut || !aligned(p->lut, 16)) return SHW_EINVAL;
@@ -401,6 +402,7 @@ shw_status shw_batch_plan_create(shw_batch_plan **out, const shw_batch_item *ite
 
 shw_status shw_render_batch(shw_batch_plan *plan, void *stream)
 {
+    NvtxRange nvtx_range("shw_render_batch");
     if (!plan || !plan->exec) return SHW_EINVAL;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) return SHW_EINVAL;
@@ -411,6 +413,7 @@ shw_status shw_render_batch(shw_batch_plan *plan, void *stream)
 
 shw_status shw_render_items(const shw_batch_item *items, int32_t n, const shw_render_params *p, void *stream)
 {
+    NvtxRange nvtx_range("shw_render_items");
     if (!items || n <= 0 || !p) return SHW_EINVAL;
     for (int i = 0; i < n; ++i) {
         shw_render_params q = *p;
@@ -468,6 +471,7 @@ static int g_noalloc_sms[kNoallocMaxDevices] = {};
 extern "C" shw_status shw_render_batch_noalloc(const shw_batch_item *items, int32_t n, const shw_render_params *p,
                                                void *stream)
 {
+    NvtxRange nvtx_range("shw_render_batch_noalloc");
     if (!items || n <= 0 || !p || !p->lut || !aligned(p->lut, 16)) return SHW_EINVAL;
     if (p->interp != SHW_NEAREST && p->interp != SHW_TRILINEAR) return SHW_EINVAL;
     if (p->filter != SHW_FILTER_NONE || p->alpha_threshold != 0 || p->smooth != SHW_SMOOTH_NONE)

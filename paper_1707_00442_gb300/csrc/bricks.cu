@@ -117,6 +117,7 @@ size_t shw_bricked_bytes(int32_t nx, int32_t ny, int32_t nz, int32_t storage)
 shw_status shw_pack_bricks(const float *in, int32_t nx, int32_t ny, int32_t nz, int32_t storage, void *out,
                            size_t out_bytes, void *stream)
 {
+    NvtxRange nvtx_range("shw_pack_bricks");
     if (!in || !out || nx <= 0 || ny <= 0 || nz <= 0 || !aligned(in, 4) || !aligned(out, 2)) return SHW_EINVAL;
     cudaStream_t st = as_stream(stream);
     if (storage >= SHW_BF16 && storage <= SHW_F16_PAIR) {

@@ -267,7 +267,9 @@ __global__ void __launch_bounds__(AxCfg<W>::threads, MODE == SHW_COMPOSITE ? 1 :
                 }
             }
             mbar_arrive_expect_tx(&full[s], stage_bytes);
-            tma_load_3d(sm + s * stride, &tmap, x0b, y0b, UP ? p_first + j : p_first - j, &full[s]);
+            int pz = UP ? p_first + j : p_first - j;
+            check_range(pz, 0, nz - 1);
+            tma_load_3d(sm + s * stride, &tmap, x0b, y0b, pz, &full[s]);
             issued = j + 1;
         }
         // every copy issued lands before this CTA may exit
@@ -312,6 +314,17 @@ __global__ void __launch_bounds__(AxCfg<W>::threads, MODE == SHW_COMPOSITE ? 1 :
             o11[i] = 4 * (gy1 * A.nx + gx1);
         }
     }
+    if constexpr (kChecked) {  // every offset inside the staged box, or inside the plane
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const long long lim = ((inbox >> i) & 1) ? 4ll * bw * bh : 4ll * A.nx * A.ny;
+            const int lo = min(min(o00[i], o01[i]), min(o10[i], o11[i]));
+            const int hi = max(max(o00[i], o01[i]), max(o10[i], o11[i]));
+            const bool ok = lo >= 0 && (long long)hi + 4 <= lim;
+            SHW_CHECK(ok);
+            if (!ok) o00[i] = o01[i] = o10[i] = o11[i] = 0;
+        }
+    }
     const bool all_inbox = inbox == (1 << R) - 1;
     const size_t plane_elems = (size_t)A.nx * A.ny;
 
@@ -349,7 +362,9 @@ __global__ void __launch_bounds__(AxCfg<W>::threads, MODE == SHW_COMPOSITE ? 1 :
                 }
             }
         } else {
-            const char *g = reinterpret_cast<const char *>(vol + (size_t)(UP ? p_first + jp : p_first - jp) * plane_elems);
+            int pz = UP ? p_first + jp : p_first - jp;
+            check_range(pz, 0, A.nz - 1);
+            const char *g = reinterpret_cast<const char *>(vol + (size_t)pz * plane_elems);
 #pragma unroll
             for (int i = 0; i < R; ++i) {
                 const char *b = ((inbox >> i) & 1) ? t : g;

@@ -89,8 +89,13 @@ template <class EP>
 struct SlabGeom {
     static constexpr int kBytes = (int)sizeof(typename EP::raw);
     static constexpr int kAlign = 16 / kBytes;  // elements per 16 bytes (x alignment of a copy)
-    static constexpr int kBXn = (kBytes == 2 ? 80 : 112) / kBytes;   // narrow chunk width (elements)
-    static constexpr int kBXw = (kBytes == 2 ? 112 : 160) / kBytes;  // wide chunk width
+    // narrow and wide chunk widths (elements).  The 8-byte elements of the float32 pair
+    // storage take one width of 32 (256-byte rows): a 16-pixel tile's x footprint at the
+    // survey magnification is 21-30 cells, and rows of 14 / 20 made most slabs overflow
+    // their box into global loads (line ratio 2.97 ms; 24 / 32: 2.16; 32: 2.13; wider rows
+    // only thin the slabs)
+    static constexpr int kBXn = kBytes == 8 ? 32 : (kBytes == 2 ? 80 : 112) / kBytes;
+    static constexpr int kBXw = kBytes == 8 ? 32 : (kBytes == 2 ? 112 : 160) / kBytes;
     static constexpr int kBXx = 80 / kBytes;                         // x-major chunk width
     static constexpr int kStageElems = kSlabStageBytes / kBytes;
     static_assert((kBXn * kBytes) % 16 == 0 && (kBXw * kBytes) % 16 == 0 && (kBXx * kBytes) % 16 == 0,
@@ -334,7 +339,13 @@ __device__ __forceinline__ bool slab_march(const S &s, const RenderArgs &a, St &
             const int lx = cx - h.ox, ly = cy - h.oy, lz = cz - h.oz;
             if (in_slab && (unsigned)lx < (unsigned)h.ex1 && (unsigned)ly < (unsigned)h.ey1 &&
                 (unsigned)lz < (unsigned)h.ez1) {
-                const raw *q = stage + (lx + ly * h.sy + lz * h.sz);
+                int off = lx + ly * h.sy + lz * h.sz;
+                if constexpr (kChecked) {  // the cell's far corner lies in the stage
+                    const bool ok = off >= 0 && off + h.sz + h.sy + 1 < SlabGeom<EP>::kStageElems;
+                    SHW_CHECK(ok);
+                    if (!ok) off = 0;
+                }
+                const raw *q = stage + off;
                 const raw *qy = q + h.sy, *qz = q + h.sz, *qyz = qz + h.sy;
                 cc.c[0] = EP::cvt(q[0]);
                 cc.c[1] = EP::cvt(q[1]);

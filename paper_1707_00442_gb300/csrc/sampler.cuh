@@ -44,6 +44,31 @@ __device__ __forceinline__ int cell_of(long long p, int n)
     return CLAMP ? clampi(fx_cell(p), -1, n - 1) : fx_cell(p);
 }
 
+// Bounds-checked builds (SHW_CHECKED): the contract of an unclamped accessor -- the base of a
+// cell with both corners inside the cube ([0, n-2] per axis), a voxel inside it, a brick cell
+// in [-1, n-1] -- is checked; a violating index is recorded and clamped into its range.
+// Normal builds: no code.
+__device__ __forceinline__ void check_range(int &i, int lo, int hi)
+{
+    if constexpr (kChecked) {
+        const bool ok = i >= lo && i <= hi;
+        SHW_CHECK(ok);
+        if (!ok) i = max(min(i, hi), lo);
+    }
+}
+__device__ __forceinline__ void check_cell(int &ix, int &iy, int &iz, int nx, int ny, int nz)
+{
+    check_range(ix, 0, nx - 2);
+    check_range(iy, 0, ny - 2);
+    check_range(iz, 0, nz - 2);
+}
+__device__ __forceinline__ void check_voxel(int &x, int &y, int &z, int nx, int ny, int nz)
+{
+    check_range(x, 0, nx - 1);
+    check_range(y, 0, ny - 1);
+    check_range(z, 0, nz - 1);
+}
+
 // Linear float32 cube [nz][ny][nx].  Idx: int for < 2^31 voxels, long long beyond.
 template <typename Idx>
 struct SamplerF32 {
@@ -61,6 +86,8 @@ struct SamplerF32 {
             x = clampi(x, 0, nx - 1);
             y = clampi(y, 0, ny - 1);
             z = clampi(z, 0, nz - 1);
+        } else {
+            check_voxel(x, y, z, nx, ny, nz);
         }
         return __ldg(v + ((Idx)z * sz + (Idx)y * sy + x));
     }
@@ -69,6 +96,7 @@ struct SamplerF32 {
     template <bool CLAMP = true>
     __device__ __forceinline__ void corners(int ix, int iy, int iz, float c[8]) const
     {
+        if (!CLAMP) check_cell(ix, iy, iz, nx, ny, nz);
         int x0 = ix, y0 = iy, z0 = iz, dx = 1;
         Idx dy = sy, dz = sz;
         if (CLAMP) {
@@ -145,6 +173,8 @@ struct SamplerBrick {
             x = clampi(x, 0, nx - 1);
             y = clampi(y, 0, ny - 1);
             z = clampi(z, 0, nz - 1);
+        } else {
+            check_voxel(x, y, z, nx, ny, nz);
         }
         const int bx = x >> 5, by = y >> 5, bz = z >> 5;
         const Idx brick = ((Idx)bz * nby + by) * nbx + bx;
@@ -155,6 +185,9 @@ struct SamplerBrick {
     template <bool CLAMP = true>
     __device__ __forceinline__ void corners(int ix, int iy, int iz, float c[8]) const
     {
+        check_range(ix, -1, nx - 1);
+        check_range(iy, -1, ny - 1);
+        check_range(iz, -1, nz - 1);
         const unsigned short *p = cell_ptr(ix, iy, iz);
         c[0] = to_f32<T>(__ldg(p));
         c[1] = to_f32<T>(__ldg(p + 1));
@@ -192,6 +225,8 @@ struct SamplerLin16 {
             x = clampi(x, 0, nx - 1);
             y = clampi(y, 0, ny - 1);
             z = clampi(z, 0, nz - 1);
+        } else {
+            check_voxel(x, y, z, nx, ny, nz);
         }
         return to_f32<T>(__ldg(v + (z * sz + y * sy + x)));
     }
@@ -200,6 +235,7 @@ struct SamplerLin16 {
     template <bool CLAMP = true>
     __device__ __forceinline__ void corners(int ix, int iy, int iz, float c[8]) const
     {
+        if (!CLAMP) check_cell(ix, iy, iz, nx, ny, nz);
         int x0 = ix, y0 = iy, z0 = iz, dx = 1, dy = sy, dz = sz;
         if (CLAMP) {
             x0 = max(ix, 0);
@@ -273,6 +309,8 @@ struct SamplerF32Pair {
             x = clampi(x, 0, nx - 1);
             y = clampi(y, 0, ny - 1);
             z = clampi(z, 0, nz - 1);
+        } else {
+            check_voxel(x, y, z, nx, ny, nz);
         }
         return __ldg(v + ((Idx)z * sz + (Idx)y * sy + x));
     }
@@ -280,6 +318,7 @@ struct SamplerF32Pair {
     template <bool CLAMP = true>
     __device__ __forceinline__ void corners2(int ix, int iy, int iz, float2 c[8]) const
     {
+        if (!CLAMP) check_cell(ix, iy, iz, nx, ny, nz);
         int x0 = ix, y0 = iy, z0 = iz, dx = 1;
         Idx dy = sy, dz = sz;
         if (CLAMP) {
@@ -327,6 +366,8 @@ __device__ __forceinline__ float2 SamplerLin16Pair<T>::nearest2(long long X, lon
         x = clampi(x, 0, nx - 1);
         y = clampi(y, 0, ny - 1);
         z = clampi(z, 0, nz - 1);
+    } else {
+        check_voxel(x, y, z, nx, ny, nz);
     }
     return pair_to_f32<T>(__ldg(v + (z * sz + y * sy + x)));
 }
@@ -335,6 +376,7 @@ template <typename T>
 template <bool CLAMP>
 __device__ __forceinline__ void SamplerLin16Pair<T>::corners2(int ix, int iy, int iz, float2 c[8]) const
 {
+    if (!CLAMP) check_cell(ix, iy, iz, nx, ny, nz);
     int x0 = ix, y0 = iy, z0 = iz, dx = 1, dy = sy, dz = sz;
     if (CLAMP) {
         x0 = max(ix, 0);
@@ -376,6 +418,8 @@ struct SamplerBrickPair {
             x = clampi(x, 0, nx - 1);
             y = clampi(y, 0, ny - 1);
             z = clampi(z, 0, nz - 1);
+        } else {
+            check_voxel(x, y, z, nx, ny, nz);
         }
         const int bx = x >> 5, by = y >> 5, bz = z >> 5;
         const Idx brick = ((Idx)bz * nby + by) * nbx + bx;
@@ -386,6 +430,9 @@ struct SamplerBrickPair {
     template <bool CLAMP = true>
     __device__ __forceinline__ void corners2(int ix, int iy, int iz, float2 c[8]) const
     {
+        check_range(ix, -1, nx - 1);
+        check_range(iy, -1, ny - 1);
+        check_range(iz, -1, nz - 1);
         // ix in [-1, n-1]: brick of max(ix, 0), local index ix - 32 b + 1 in [0, 32]
         const int bx = max(ix, 0) >> 5, by = max(iy, 0) >> 5, bz = max(iz, 0) >> 5;
         const int lx = ix - (bx << 5) + 1, ly = iy - (by << 5) + 1, lz = iz - (bz << 5) + 1;

@@ -327,6 +327,8 @@ __global__ void __launch_bounds__(kSmThreads, smooth_min_blocks<R, ZIP>())
         // i-2R .. i (oldest in slot (slot+1) mod K).  Only this part is instanced per slot,
         // so the ring is indexed at compile time.
         const bool emit = i >= 2 * R;
+        if constexpr (kChecked)
+            if (emit) SHW_CHECK(zfirst + i - R >= zb && zfirst + i - R < ze);  // the plane written
         static_slot<K>(slot, [&](auto sc) {
             constexpr int sl = decltype(sc)::value;
             ring[0][sl] = yv[0];
@@ -523,6 +525,7 @@ extern "C" {
 shw_status shw_smooth(const float *in, float *out, int32_t nx, int32_t ny, int32_t nz, float sigma, int32_t radius,
                       void *stream)
 {
+    NvtxRange nvtx_range("shw_smooth");
     shw_status s = smooth_check(in, out, nx, ny, nz, radius);
     if (s != SHW_OK) return s;
     SmoothWeights W{};
@@ -533,6 +536,7 @@ shw_status shw_smooth(const float *in, float *out, int32_t nx, int32_t ny, int32
 shw_status shw_smooth_zip(const float *in, const float *first, float *out_pair, int32_t nx, int32_t ny, int32_t nz,
                           float sigma, int32_t radius, void *stream)
 {
+    NvtxRange nvtx_range("shw_smooth_zip");
     if (!in || !first || !out_pair || nx <= 0 || ny <= 0 || nz <= 0 || radius < 0) return SHW_EINVAL;
     if (!aligned(in, 4) || !aligned(first, 4) || !aligned(out_pair, 8)) return SHW_EINVAL;
     if (radius > SHW_MAX_SMOOTH_RADIUS) return SHW_EUNSUPPORTED;
@@ -546,6 +550,7 @@ shw_status shw_smooth_zip(const float *in, const float *first, float *out_pair, 
 shw_status shw_smooth_weights(const float *in, float *out, int32_t nx, int32_t ny, int32_t nz, const float *w_host,
                               int32_t radius, void *stream)
 {
+    NvtxRange nvtx_range("shw_smooth_weights");
     shw_status s = smooth_check(in, out, nx, ny, nz, radius);
     if (s != SHW_OK) return s;
     if (!w_host) return SHW_EINVAL;

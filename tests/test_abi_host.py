@@ -54,7 +54,7 @@ def test_struct_layout(L):
 
 
 def test_status_strings(L):
-    for s in range(7):
+    for s in range(8):  # SHW_OK .. SHW_EBOUNDS
         assert L.shw_status_string(s)
     assert L.shw_status_string(99) == b"unknown status"
 
