@@ -570,19 +570,30 @@ WARP_INST_PER_SAMPLE: dict = {
 # --------------------------------------------------------------------------- variants
 
 def _timeit(torch, fn, reps=5, warm=2):
-    """Median CUDA-event time (ms) of fn on the current stream."""
+    """Median CUDA-event time (ms) of one call of fn on the current stream.  Each measurement
+    brackets enough back-to-back calls to last about 2 ms and divides by their number: with a
+    single call between the events, the host's own time to enqueue it (argument checks, the
+    tensor-map encoding) would count as GPU time while the device sits idle."""
     for _ in range(warm):
         fn()
     torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    fn()
+    e1.record()
+    torch.cuda.synchronize()
+    inner = max(1, min(20, int(math.ceil(2.0 / max(e0.elapsed_time(e1), 1e-3)))))
     ts = []
     for _ in range(reps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
-        fn()
+        for _ in range(inner):
+            fn()
         e1.record()
         torch.cuda.synchronize()
-        ts.append(e0.elapsed_time(e1))
+        ts.append(e0.elapsed_time(e1) / inner)
     return statistics.median(ts)
 
 

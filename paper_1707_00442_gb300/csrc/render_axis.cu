@@ -47,7 +47,8 @@ shw_status render_axis(int mode, int interp, const shw_volume &v, const shw_came
     }
     if (A.bw > 256 || A.bh > 256) return SHW_EUNSUPPORTED;  // the tensor copy's box limit
     A.stage_stride = fix ? kFixStride : (A.bw * A.bh + 31) & ~31;  // TMA destinations start on 128 bytes
-    const size_t smem = (size_t)kAxStages * A.stage_stride * 4;
+    const int kmode = (mode == SHW_MIP && a.index == nullptr) ? kMipValue : mode;
+    const size_t smem = (size_t)axis_stages(kmode, fix) * A.stage_stride * 4;
     if (smem > (size_t)kAxSmemLimit) return SHW_EUNSUPPORTED;
     A.nx = v.nx;
     A.ny = v.ny;
@@ -65,7 +66,6 @@ shw_status render_axis(int mode, int interp, const shw_volume &v, const shw_came
     CUtensorMap map;
     if (!encode_tmap_3d_f32(&map, data, v.nx, v.ny, v.nz, A.bw, A.bh)) return SHW_EUNSUPPORTED;
     const bool up = c.fwd[2] > 0.0f;  // rays advance towards +z (the sign of every ray's z step)
-    const int kmode = (mode == SHW_MIP && a.index == nullptr) ? kMipValue : mode;
     return fix ? launch_axis<true>(kmode, interp, up, map, data, c, a, A, (unsigned)tiles, smem, st)
                : launch_axis<false>(kmode, interp, up, map, data, c, a, A, (unsigned)tiles, smem, st);
 }

@@ -4,12 +4,11 @@
 // Section 2.2 (Eq. 3 is its zeroth moment).  All its rays take their samples at
 // the same z, so a CTA sweeps the cube plane by plane for a 64 x 16 pixel tile:
 //   - one producer thread stages the tile's footprint of each z plane into shared
-//     memory with cp.async.bulk.tensor, through a ring of kAxStages stages with a
-//     "full" and an "empty" mbarrier each (every wait bounded);
-//   - the consumer warps (8 with four rays per thread for MIP, 16 with two for the
-//     other modes) own their rays in pairs; each ray turns each plane into one bilinear
-//     value (4 shared loads), in the same order of operations as the general trilinear
-//     interpolation, and each warp releases the stage;
+//     memory with cp.async.bulk.tensor, through a ring of stages, a group of planes
+//     (stages) per "full" and "empty" mbarrier phase (AxRing; every wait bounded);
+//   - 16 consumer warps own two rays per thread, as a pair; each ray turns each plane
+//     into one bilinear value (4 shared loads), in the same order of operations as the
+//     general trilinear interpolation, and each warp releases the group's stages;
 //   - the samples that fall between two planes (the same for every ray) are one
 //     lerp each, fed to the same transfer-function state as the general marcher.
 // When the step is exactly 1/Q voxel every interior cell holds Q samples at the same
@@ -27,20 +26,30 @@
 
 namespace shw {
 
-#ifndef SHW_AX_STAGES
-#define SHW_AX_STAGES 8
-#endif
-constexpr int kAxTX = 64, kAxTY = 16;    // pixel tile of one CTA
-constexpr int kAxStages = SHW_AX_STAGES;  // ring depth (a power of two)
+constexpr int kAxTX = 64, kAxTY = 16;  // pixel tile of one CTA
 constexpr int kAxSmemLimit = 100 * 1024;
 constexpr int kAxMaxQ = 4;  // periodic stepping: at most this many samples per cell
-static_assert((kAxStages & (kAxStages - 1)) == 0, "the ring depth is a power of two");
+
+// The ring: `stages` plane buffers, consumed in groups of `group` planes that complete on one
+// barrier phase (each consumer warp waits and releases once per group).  A plane's fixed
+// chain in each warp (wait, loads, dependent lerps, release) bounded the sweep, so the
+// fixed box, whose 16 stages fit the shared-memory budget, takes groups of 8 (MIP of the
+// 1 GiB cube 0.386 ms with one plane per phase, 0.261 ms with eight); the first moment, whose
+// per-sample work is longest, does best with groups of 4 of 8 stages, as do runtime-sized boxes.
+template <int MODE, bool FIX>
+struct AxRing {
+    static constexpr bool kDeep = FIX && MODE != SHW_MOMENT1;
+    static constexpr int stages = kDeep ? 16 : 8, group = kDeep ? 8 : 4;
+    static_assert((stages & (stages - 1)) == 0 && (group & (group - 1)) == 0 && stages % group == 0,
+                  "groups tile a power-of-two ring");
+};
+// host: the stages of the kernel a request takes
+inline int axis_stages(int mode, bool fix) { return (fix && mode != SHW_MOMENT1) ? 16 : 8; }
 
 // W consumer warps share the tile's 16 rows: each thread owns 32 / W rays, in pairs (one row
-// each, the pair's rays 32 columns apart), plus one producer warp.  Eight warps of four rays
-// give MIP the most independent work per warp; sixteen warps of two rays hide more latency
-// for the transfer functions with longer per-sample chains (average, spectral, compositing,
-// first moment).
+// each, the pair's rays 32 columns apart), plus one producer warp.  Sixteen warps of two rays
+// hide more of each warp's per-plane chain (wait, loads, dependent lerps) than eight warps of
+// four, for every mode.
 template <int W>
 struct AxCfg {
     static constexpr int warps = W, pairs = kAxTY / W, rays = 2 * pairs, threads = 32 * (W + 1);
@@ -49,7 +58,7 @@ struct AxCfg {
 template <int MODE>
 constexpr int axis_warps()
 {
-    return (MODE == SHW_MIP || MODE == kMipValue) ? 8 : 16;
+    return 16;
 }
 
 // The fixed staged box: enough for a 64 x 16 tile at up to one voxel per pixel,
@@ -158,7 +167,8 @@ __global__ void __launch_bounds__(AxCfg<W>::threads, MODE == SHW_COMPOSITE ? 1 :
     axis_kernel(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ vol, shw_camera cam, RenderArgs a,
                 AxisArgs A)
 {
-    constexpr int R = AxCfg<W>::rays, P = AxCfg<W>::pairs, S = kAxStages;
+    constexpr int R = AxCfg<W>::rays, P = AxCfg<W>::pairs;
+    constexpr int S = AxRing<MODE, FIX>::stages, G = AxRing<MODE, FIX>::group;
     extern __shared__ __align__(128) float sm[];  // [stages][bh][bw]
     __shared__ __align__(8) uint64_t full[S], empty[S];
     __shared__ long long s_pz, s_dz;
@@ -245,13 +255,15 @@ __global__ void __launch_bounds__(AxCfg<W>::threads, MODE == SHW_COMPOSITE ? 1 :
     const int nplanes = (UP ? p_last - p_first : p_first - p_last) + 1;
 
     if (!consumer) {
-        // producer: one thread keeps the ring full
+        // producer: one thread keeps the ring full, a group of G planes at a time -- planes
+        // j .. j + G - 1 (j a multiple of G) go to stages s .. s + G - 1 and complete on stage
+        // s's barrier, so each consumer warp waits and releases once per group
         if (lane != 0) return;
-        const uint32_t stage_bytes = (uint32_t)(bw * bh * 4);
+        const uint32_t plane_bytes = (uint32_t)(bw * bh * 4);
         int issued = 0;
-        for (int j = 0; j < nplanes; ++j) {
+        for (int j = 0; j < nplanes; j += G) {
             const int s = j & (S - 1);
-            if (j >= S) {  // wait until every consumer warp has released plane j - S
+            if (j >= S) {  // wait until every consumer warp has released the group j - S
                 const uint32_t par = (uint32_t)(((j / S) - 1) & 1);
                 bool ok = false, quit = false;
                 for (int it = 0; it < kAxWaitPolls && !ok && !quit; ++it) {
@@ -266,14 +278,17 @@ __global__ void __launch_bounds__(AxCfg<W>::threads, MODE == SHW_COMPOSITE ? 1 :
                     break;
                 }
             }
-            mbar_arrive_expect_tx(&full[s], stage_bytes);
-            int pz = UP ? p_first + j : p_first - j;
-            check_range(pz, 0, nz - 1);
-            tma_load_3d(sm + s * stride, &tmap, x0b, y0b, pz, &full[s]);
-            issued = j + 1;
+            const int cnt = min(G, nplanes - j);
+            mbar_arrive_expect_tx(&full[s], (uint32_t)cnt * plane_bytes);
+            for (int e = 0; e < cnt; ++e) {
+                int pz = UP ? p_first + j + e : p_first - j - e;
+                check_range(pz, 0, nz - 1);
+                tma_load_3d(sm + (s + e) * stride, &tmap, x0b, y0b, pz, &full[s]);
+            }
+            issued = j + cnt;
         }
-        // every copy issued lands before this CTA may exit
-        for (int j = max(issued - S, 0); j < issued; ++j)
+        // every copy issued lands before this CTA may exit (the groups still in the ring)
+        for (int j = (max(issued - S, 0) + G - 1) & ~(G - 1); j < issued; j += G)
             mbar_wait(&full[j & (S - 1)], (uint32_t)((j / S) & 1), A.err);
         return;
     }
@@ -497,22 +512,24 @@ __global__ void __launch_bounds__(AxCfg<W>::threads, MODE == SHW_COMPOSITE ? 1 :
         }
     };
 
-    int j = 0;     // planes consumed; plane j sits in stage j % S, phase parity (j / S) % 2
+    // planes consumed: plane j sits in stage j % S; the group of G planes from j (a multiple
+    // of G) completes on stage j % S's barrier (phase parity (j / S) % 2), waited for at its
+    // first plane and released after its last
+    int j = 0;
     float2 va[P];  // values of the plane held (the near plane of the current cell)
 #pragma unroll
     for (int q = 0; q < P; ++q) va[q] = make_float2(0.0f, 0.0f);
     bool alive = wait_full(0, 0u);
     if (alive) {
         if (!idle) load_plane(0, 0, va);
-        release(0);
         j = 1;
     }
     // one more plane (the far plane of the current cell) through the ring, any stage
     auto next_plane = [&](float2 vb[P]) -> bool {
         const int s = j & (S - 1);
-        if (!wait_full(s, (uint32_t)((j / S) & 1))) return false;
+        if ((j & (G - 1)) == 0 && !wait_full(s, (uint32_t)((j / S) & 1))) return false;
         if (!idle) load_plane(s, j, vb);
-        release(s);
+        if ((j & (G - 1)) == G - 1) release(s - (G - 1));
         ++j;
         return true;
     };
@@ -543,12 +560,12 @@ __global__ void __launch_bounds__(AxCfg<W>::threads, MODE == SHW_COMPOSITE ? 1 :
 #pragma unroll
                 for (int u = 0; u < S; ++u) {
                     float2 vb[P];
-                    if (!wait_full(u, ph)) {
+                    if ((u & (G - 1)) == 0 && !wait_full(u, ph)) {
                         alive = false;
                         break;
                     }
                     if (!idle) load_plane(u, j + u, vb);
-                    release(u);
+                    if ((u & (G - 1)) == G - 1) release(u - (G - 1));
                     if (!idle) cell_q(va, vb, k + u * QQ, QC, fq2);
 #pragma unroll
                     for (int q = 0; q < P; ++q) va[q] = vb[q];
