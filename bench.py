@@ -356,7 +356,11 @@ def kernel_roofline(name, t_ms, nvox, samples_per, peaks, sm_mhz, image_bytes=0,
         bytes_ = 8 * nvox
         ach = bytes_ / (t_ms * 1e-3) / 1e9
         rec = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-               "frac": round(ach / hbm, 4), "algorithmic_bytes": bytes_}
+               "frac": round(ach / hbm, 4), "algorithmic_bytes": bytes_,
+               # the three 1-D passes as separate sweeps would move 24 B per voxel: the rate
+               # that form would need to match this time
+               "three_pass_bytes": 24 * nvox,
+               "three_pass_equiv_frac": round(24 * nvox / (t_ms * 1e-3) / 1e9 / hbm, 4)}
         if name == "smooth2":
             moved = 16 * nvox
             rec["moved_bytes"] = moved
@@ -372,11 +376,14 @@ def kernel_roofline(name, t_ms, nvox, samples_per, peaks, sm_mhz, image_bytes=0,
                "hbm_frac": round(alg_bytes / (t_ms * 1e-3) / 1e9 / hbm, 4), "algorithmic_bytes": alg_bytes,
                "fp32_frac_alg_flops": round(flops / (t_ms * 1e-3) / 1e12 / fp32_peak, 4)}
         ips = WARP_INST_PER_SAMPLE.get(mode)
+        loaded = peaks.get("clocks_under_load", {}).get("sm_mhz_median")
         if ips:
             peak = sms * SCHEDULERS_PER_SM * float(sm_mhz) * 1e6 / 1e9  # G warp instructions / s
             ach = ips * ns / (t_ms * 1e-3) / 1e9
             rec = {"bound": "alu", "achieved": round(ach, 1), "peak": round(peak, 1), "unit": "Gwarp-inst/s",
                    "frac": round(ach / peak, 4), "warp_inst_per_sample": ips, **rec}
+            if loaded:  # against the loaded median clock recorded with the peaks as well
+                rec["frac_at_peaks_loaded_clock"] = round(ach / (sms * SCHEDULERS_PER_SM * float(loaded) * 1e-3), 4)
         else:  # no instruction count for this build: the FP32 roofline of the method's flops
             ach = flops / (t_ms * 1e-3) / 1e12
             rec = {"bound": "alu", "achieved": round(ach, 3), "peak": round(fp32_peak, 2), "unit": "TFLOP/s",

@@ -332,13 +332,12 @@ __device__ __forceinline__ bool slab_march(const S &s, const RenderArgs &a, St &
     for (; k < kb; ++k) {
         const int cx = fx_cell(X), cy = fx_cell(Y), cz = fx_cell(Z);
         const int cm = M == 0 ? cx : (M == 1 ? cy : cz);
-        const int rel = cm - h.s_lo;
-        const bool in_slab = (unsigned)rel < (unsigned)h.s_len;
-        if (!in_slab && ((h.dir > 0) == (rel >= 0))) return false;  // a later slab holds this sample
+        // a sample outside the slab waits for a later one (one behind every slab -- never seen
+        // on the survey views -- is marched at the tile's end with the interior left over)
+        if ((unsigned)(cm - h.s_lo) >= (unsigned)h.s_len) return false;
         if (((cx ^ cc.ix) | (cy ^ cc.iy) | (cz ^ cc.iz)) != 0) {  // a new cell
             const int lx = cx - h.ox, ly = cy - h.oy, lz = cz - h.oz;
-            if (in_slab && (unsigned)lx < (unsigned)h.ex1 && (unsigned)ly < (unsigned)h.ey1 &&
-                (unsigned)lz < (unsigned)h.ez1) {
+            if ((unsigned)lx < (unsigned)h.ex1 && (unsigned)ly < (unsigned)h.ey1 && (unsigned)lz < (unsigned)h.ez1) {
                 int off = lx + ly * h.sy + lz * h.sz;
                 if constexpr (kChecked) {  // the cell's far corner lies in the stage
                     const bool ok = off >= 0 && off + h.sz + h.sy + 1 < SlabGeom<EP>::kStageElems;

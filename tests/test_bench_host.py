@@ -21,6 +21,8 @@ def test_smooth_roofline_counts_read_and_write():
     assert r["algorithmic_bytes"] == 8 * nvox
     assert r["achieved"] == pytest.approx(8 * nvox / 1e-3 / 1e9, rel=1e-3)
     assert r["frac"] == pytest.approx(r["achieved"] / 6000.0, rel=1e-3)
+    # beside it, what the three 1-D passes as separate sweeps would have to move in that time
+    assert r["three_pass_bytes"] == 24 * nvox and r["three_pass_equiv_frac"] == pytest.approx(3 * r["frac"], rel=1e-3)
     # the zip form: the method's 8 bytes per voxel, and beside them the 16 it moves (it also
     # re-reads the first cube's result and writes the 8-byte pair)
     z = bench.kernel_roofline("smooth2", 1.0, nvox, {}, PEAKS, 2000.0)
