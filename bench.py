@@ -557,20 +557,20 @@ def run_ours(args):
 TRAFFIC_PER_LAUNCH: dict = {
     "smooth": 1386283008 + 1036524288,
     "smooth2": 2387365376 + 2102186240,
-    "render_mip": 2084857600 + 17495808,
-    "render_avg": 2051461376 + 17522432,
-    "render_composite": 1855587328 + 18014464,
-    "render_spectral": 2120644864 + 17439232,
-    "render_ratio": 4133697280 + 25476608,
+    "render_mip": 2051754496 + 20182272,
+    "render_avg": 2031599872 + 17270016,
+    "render_composite": 1835591168 + 17908224,
+    "render_spectral": 2120952064 + 17652224,
+    "render_ratio": 4098699520 + 25379072,
 }
 # warp instructions executed per sample of each render (same file: smsp__inst_executed.sum
 # over the render's samples, 371,839,071; compositing 359,686,584):
 WARP_INST_PER_SAMPLE: dict = {
-    "mip": 3.171,
-    "avg": 3.306,
-    "composite": 4.208,
-    "spectral": 3.271,
-    "ratio": 3.883,
+    "mip": 3.097,
+    "avg": 3.232,
+    "composite": 4.139,
+    "spectral": 3.197,
+    "ratio": 3.707,
 }
 
 
