@@ -68,7 +68,10 @@ __device__ __forceinline__ float4 lut_eval(const float4 *L, float vhat)
     const int i0 = min(__float2int_rd(u), 254);
     const float f = u - (float)i0;
     const float4 a = L[i0], b = L[i0 + 1];
-    return make_float4(lerp(a.x, b.x, f), lerp(a.y, b.y, f), lerp(a.z, b.z, f), lerp(a.w, b.w, f));
+    // four lerps as two packed FP32x2 ones (the same rounding as scalar lerps)
+    const float2 rg = lerp2(make_float2(a.x, a.y), make_float2(b.x, b.y), f);
+    const float2 ba = lerp2(make_float2(a.z, a.w), make_float2(b.z, b.w), f);
+    return make_float4(rg.x, rg.y, ba.x, ba.y);
 }
 
 __device__ __forceinline__ float normalise(float v, float lo, float inv_range)
