@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(SamplerF32<long l
                 Tseg[j] = T;
                 const float vv = isnan(v) ? a.lo : v;
                 const float4 c = lut_eval(lut_s, normalise(vv, a.lo, a.inv_range));
-                const float al = fminf(fmaxf(a.opacity_scale * c.w, 0.0f), 1.0f);
+                const float al = __saturatef(a.opacity_scale * c.w);
                 T = T * (1.0f - al);
             }
             // walk it backwards
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(SamplerF32<long l
                 const bool nan = isnan(v);
                 const float vv = nan ? a.lo : v;
                 const float x = (vv - a.lo) * a.inv_range;
-                const float vh = fminf(fmaxf(x, 0.0f), 1.0f);
+                const float vh = __saturatef(x);
                 const float u = vh * 255.0f;
                 const int i0 = min(__float2int_rd(u), 254);
                 const float f = u - (float)i0;
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kBwdThreads) backward_kernel(SamplerF32<long l
                 const float4 c = make_float4(lerp(L0.x, L1.x, f), lerp(L0.y, L1.y, f), lerp(L0.z, L1.z, f),
                                              lerp(L0.w, L1.w, f));
                 const float alpha = a.opacity_scale * c.w;
-                const float al = fminf(fmaxf(alpha, 0.0f), 1.0f);
+                const float al = __saturatef(alpha);
                 const float Tk = Tseg[j];
                 const float ga = (g.x * c.x + g.y * c.y + g.z * c.z) * Tk - gT * Tk;
                 const float wc = Tk * al;

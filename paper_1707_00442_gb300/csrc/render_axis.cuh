@@ -127,7 +127,7 @@ __device__ __forceinline__ void axis_emit(const RenderArgs &a, long long pix, bo
             const float vh = normalise(st.m, a.lo, a.inv_range);
             if constexpr (MODE == SHW_SPECTRAL) {
                 const float zmax = nearest ? (float)index : __ll2float_rn(Zm) * 2.3283064365386963e-10f;
-                const float tz = fminf(fmaxf((zmax + 0.5f) / (float)a.nz, 0.0f), 1.0f);
+                const float tz = __saturatef((zmax + 0.5f) / (float)a.nz);
                 const float4 c = lut_eval(a.lut, tz);
                 out = make_float4(c.x, c.y, c.z, colour_alpha(st.m, a));
             } else {
@@ -141,7 +141,7 @@ __device__ __forceinline__ void axis_emit(const RenderArgs &a, long long pix, bo
                 const float m1 = __fdiv_rn(st.szw, st.sw);
                 scalar = m1;
                 index = clampi(__float2int_rd(m1 + 0.5f), 0, a.nz - 1);
-                const float tz = fminf(fmaxf((m1 + 0.5f) / (float)a.nz, 0.0f), 1.0f);
+                const float tz = __saturatef((m1 + 0.5f) / (float)a.nz);
                 const float4 c = lut_eval(a.lut, tz);
                 out = make_float4(c.x, c.y, c.z, colour_alpha(__fdiv_rn(st.sv, (float)N), a));
             }

@@ -76,8 +76,9 @@ __device__ __forceinline__ float4 lut_eval(const float4 *L, float vhat)
 
 __device__ __forceinline__ float normalise(float v, float lo, float inv_range)
 {
-    // fmaxf first: a NaN argument yields 0 (never reached: NaN samples become lo)
-    return fminf(fmaxf((v - lo) * inv_range, 0.0f), 1.0f);
+    // clamped to [0, 1] by one saturating operation; a NaN argument yields 0 (never reached:
+    // NaN samples become lo)
+    return __saturatef((v - lo) * inv_range);
 }
 
 // The per-sample filter of Algorithm 1: Algorithm 10 (intensity clipping) replaces a value
@@ -406,7 +407,7 @@ __device__ __forceinline__ float colour_pos(long long P, int n, bool nearest)
 {
     return nearest ? (float)clampi(fx_round(P), 0, n - 1) : __fadd_rn((float)fx_cell(P), fx_frac(P));
 }
-__device__ __forceinline__ float tex_coord(float p, int n) { return fminf(fmaxf((p + 0.5f) / (float)n, 0.0f), 1.0f); }
+__device__ __forceinline__ float tex_coord(float p, int n) { return __saturatef((p + 0.5f) / (float)n); }
 
 constexpr int kColourValue = 0, kColourSpectral = 1, kColourPosition = 2;
 
@@ -445,7 +446,7 @@ struct CompositeStateT {
             Y += DY;
             Z += DZ;
         }
-        const float al = fminf(fmaxf(s * c.w, 0.0f), 1.0f);
+        const float al = __saturatef(s * c.w);
         const float w = T * al;
         cr = __fmaf_rn(w, r, cr);
         cg = __fmaf_rn(w, g, cg);
@@ -728,7 +729,7 @@ __device__ __forceinline__ void emit_ray(const RenderArgs &a, long long pix, int
                 // Algorithm 4: colour from the spectral position, alpha from the value
                 const float zmax =
                     (INTERP == SHW_NEAREST) ? (float)index : __ll2float_rn(Zm) * 2.3283064365386963e-10f;
-                const float tz = fminf(fmaxf((zmax + 0.5f) / (float)a.nz, 0.0f), 1.0f);
+                const float tz = __saturatef((zmax + 0.5f) / (float)a.nz);
                 const float4 c = lut_eval(a.lut, tz);
                 out = make_float4(c.x, c.y, c.z, colour_alpha(st.m, a));
             } else {
@@ -759,7 +760,7 @@ __device__ __forceinline__ void emit_ray(const RenderArgs &a, long long pix, int
                 const float m1 = __fdiv_rn(st.szw, st.sw);
                 scalar = m1;
                 index = clampi(__float2int_rd(m1 + 0.5f), 0, a.nz - 1);
-                const float tz = fminf(fmaxf((m1 + 0.5f) / (float)a.nz, 0.0f), 1.0f);
+                const float tz = __saturatef((m1 + 0.5f) / (float)a.nz);
                 const float4 c = lut_eval(a.lut, tz);
                 out = make_float4(c.x, c.y, c.z, colour_alpha(__fdiv_rn(st.sv, (float)N), a));
             }
