@@ -557,20 +557,20 @@ def run_ours(args):
 TRAFFIC_PER_LAUNCH: dict = {
     "smooth": 1386283008 + 1036524288,
     "smooth2": 2387365376 + 2102186240,
-    "render_mip": 2051754496 + 20182272,
-    "render_avg": 2031599872 + 17270016,
-    "render_composite": 1835591168 + 17908224,
-    "render_spectral": 2120952064 + 17652224,
-    "render_ratio": 4098699520 + 25379072,
+    "render_mip": 1990946560 + 20146944,
+    "render_avg": 1984600576 + 17113856,
+    "render_composite": 1822312192 + 17948416,
+    "render_spectral": 2068386560 + 17522176,
+    "render_ratio": 4033366016 + 25200128,
 }
 # warp instructions executed per sample of each render (same file: smsp__inst_executed.sum
 # over the render's samples, 371,839,071; compositing 359,686,584):
 WARP_INST_PER_SAMPLE: dict = {
-    "mip": 3.097,
-    "avg": 3.232,
-    "composite": 4.139,
-    "spectral": 3.197,
-    "ratio": 3.707,
+    "mip": 2.841,
+    "avg": 2.955,
+    "composite": 3.750,
+    "spectral": 2.923,
+    "ratio": 3.450,
 }
 
 
