@@ -336,11 +336,16 @@ __device__ __forceinline__ bool slab_march(const S &s, const RenderArgs &a, St &
         const int cm = M == 0 ? cx : (M == 1 ? cy : cz);
         // a sample outside the slab waits for a later one (one behind every slab -- never seen
         // on the survey views -- is marched at the tile's end with the interior left over)
-        if ((unsigned)(cm - h.s_lo) >= (unsigned)h.s_len) return false;
+        const int rel = cm - h.s_lo;
+        if ((unsigned)rel >= (unsigned)h.s_len) return false;
         val c[8];
         {
-            const int lx = cx - h.ox, ly = cy - h.oy, lz = cz - h.oz;
-            if ((unsigned)lx < (unsigned)h.ex1 && (unsigned)ly < (unsigned)h.ey1 && (unsigned)lz < (unsigned)h.ez1) {
+            // a y- or z-major box starts at the slab's first cell and holds one plane more than
+            // the slab along its axis: a sample in the slab is inside the box on that axis
+            const int lx = cx - h.ox, ly = M == 1 ? rel : cy - h.oy, lz = M == 2 ? rel : cz - h.oz;
+            const bool inbox = (unsigned)lx < (unsigned)h.ex1 && (M == 1 || (unsigned)ly < (unsigned)h.ey1) &&
+                               (M == 2 || (unsigned)lz < (unsigned)h.ez1);
+            if (inbox) {
                 int off = lx + ly * h.sy + lz * h.sz;
                 if constexpr (kChecked) {  // the cell's far corner lies in the stage
                     const bool ok = off >= 0 && off + h.sz + h.sy + 1 < SlabGeom<EP>::kStageElems;
