@@ -557,20 +557,20 @@ def run_ours(args):
 TRAFFIC_PER_LAUNCH: dict = {
     "smooth": 1386283008 + 1036524288,
     "smooth2": 2387365376 + 2102186240,
-    "render_mip": 1990946560 + 20146944,
-    "render_avg": 1984600576 + 17113856,
-    "render_composite": 1822312192 + 17948416,
-    "render_spectral": 2068386560 + 17522176,
-    "render_ratio": 4033366016 + 25200128,
+    "render_mip": 1996232960 + 20115712,
+    "render_avg": 2019793664 + 17363712,
+    "render_composite": 1794625792 + 17764864,
+    "render_spectral": 2045678848 + 17568256,
+    "render_ratio": 3963496704 + 25422592,
 }
 # warp instructions executed per sample of each render (same file: smsp__inst_executed.sum
 # over the render's samples, 371,839,071; compositing 359,686,584):
 WARP_INST_PER_SAMPLE: dict = {
-    "mip": 2.841,
-    "avg": 2.955,
-    "composite": 3.750,
-    "spectral": 2.923,
-    "ratio": 3.450,
+    "mip": 2.775,
+    "avg": 2.893,
+    "composite": 3.688,
+    "spectral": 2.861,
+    "ratio": 3.356,
 }
 
 
