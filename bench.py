@@ -557,19 +557,19 @@ def run_ours(args):
 TRAFFIC_PER_LAUNCH: dict = {
     "smooth": 1386283008 + 1036524288,
     "smooth2": 2387365376 + 2102186240,
-    "render_mip": 1996232960 + 20115712,
-    "render_avg": 2019793664 + 17363712,
-    "render_composite": 1794625792 + 17764864,
-    "render_spectral": 2045678848 + 17568256,
-    "render_ratio": 3963496704 + 25422592,
+    "render_mip": 1898904064 + 19944192,
+    "render_avg": 1995993856 + 17155072,
+    "render_composite": 1799882240 + 17438464,
+    "render_spectral": 1978369024 + 17194496,
+    "render_ratio": 3965529088 + 25304064,
 }
 # warp instructions executed per sample of each render (same file: smsp__inst_executed.sum
 # over the render's samples, 371,839,071; compositing 359,686,584):
 WARP_INST_PER_SAMPLE: dict = {
-    "mip": 2.775,
-    "avg": 2.893,
-    "composite": 3.688,
-    "spectral": 2.861,
+    "mip": 2.593,
+    "avg": 2.727,
+    "composite": 3.555,
+    "spectral": 2.694,
     "ratio": 3.356,
 }
 

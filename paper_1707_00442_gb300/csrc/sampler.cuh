@@ -29,13 +29,14 @@ __device__ __forceinline__ float2 lerp2(float2 a, float2 b, float t)
 }
 
 // Corners of one cell, c[a + 2b + 4c] with a, b, c the x, y, z offsets.
-// Tensor-product interpolation: x first (packed pairwise), then y, then z.
+// Tensor-product interpolation: x first, then y, then z.  The lerps go in pairs across the
+// two z planes, so each level's packed result is the next level's operand as it stands.
 __device__ __forceinline__ float trilerp(const float c[8], float fx, float fy, float fz)
 {
-    const float2 x0 = lerp2(make_float2(c[0], c[2]), make_float2(c[1], c[3]), fx);  // (c00, c01) of plane z0
-    const float2 x1 = lerp2(make_float2(c[4], c[6]), make_float2(c[5], c[7]), fx);  // (c10, c11) of plane z1
-    const float2 y = lerp2(make_float2(x0.x, x1.x), make_float2(x0.y, x1.y), fy);   // (c0, c1)
-    return lerp(y.x, y.y, fz);
+    const float2 y0 = lerp2(make_float2(c[0], c[4]), make_float2(c[1], c[5]), fx);  // row y0 of planes z0, z1
+    const float2 y1 = lerp2(make_float2(c[2], c[6]), make_float2(c[3], c[7]), fx);  // row y1 of planes z0, z1
+    const float2 z = lerp2(y0, y1, fy);                                              // planes z0, z1
+    return lerp(z.x, z.y, fz);
 }
 
 template <bool CLAMP>
