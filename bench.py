@@ -557,20 +557,20 @@ def run_ours(args):
 TRAFFIC_PER_LAUNCH: dict = {
     "smooth": 1386283008 + 1036524288,
     "smooth2": 2387365376 + 2102186240,
-    "render_mip": 1898904064 + 19944192,
-    "render_avg": 1995993856 + 17155072,
-    "render_composite": 1799882240 + 17438464,
-    "render_spectral": 1978369024 + 17194496,
-    "render_ratio": 3965529088 + 25304064,
+    "render_mip": 1872291840 + 19960832,
+    "render_avg": 1903843840 + 17025792,
+    "render_composite": 1776742912 + 17455616,
+    "render_spectral": 1926076672 + 17346048,
+    "render_ratio": 3963735040 + 25214720,
 }
 # warp instructions executed per sample of each render (same file: smsp__inst_executed.sum
 # over the render's samples, 371,839,071; compositing 359,686,584):
 WARP_INST_PER_SAMPLE: dict = {
-    "mip": 2.593,
-    "avg": 2.727,
-    "composite": 3.555,
-    "spectral": 2.694,
-    "ratio": 3.356,
+    "mip": 2.362,
+    "avg": 2.495,
+    "composite": 3.324,
+    "spectral": 2.463,
+    "ratio": 3.120,
 }
 
 

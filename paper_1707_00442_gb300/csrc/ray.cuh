@@ -209,29 +209,14 @@ __device__ __forceinline__ bool setup_ray(const shw_camera &c, int px, int py, i
 __device__ __forceinline__ int fx_cell(long long p) { return (int)(p >> 32); }
 __device__ __forceinline__ float fx_frac(long long p)
 {
-    // 23 most significant fraction bits as the mantissa of a float in [1, 2): (lo >> 9) is
-    // below 2^23, so OR-ing the exponent equals adding it, and the high half of lo * 2^23 is
-    // lo >> 9 -- one integer multiply-add instead of a shift and a logic operation
-    return __uint_as_float(__umulhi((unsigned)p, 1u << 23) + 0x3f800000u) - 1.0f;
+    // the 23 most significant fraction bits as the mantissa of a float in [1, 2): lo >> 9 is
+    // below 2^23, so OR-ing the exponent in equals adding it
+    return __uint_as_float(((unsigned)p >> 9) | 0x3f800000u) - 1.0f;
 }
-// X + D exactly (64-bit fixed point) on the FMA pipe: a widening integer multiply-add of D's
-// low word by `one` (== 1, passed at run time so the compiler keeps the multiply) adds it
-// with its carry into the high word, and a second multiply-add adds D's high word.  The
-// plain 64-bit addition would take two operations of the integer ALU pipe, which the
-// marchers' per-sample loops already keep the busiest.
-__device__ __forceinline__ long long fx_step(long long X, long long D, unsigned one)
-{
-    long long r;
-    asm("{\n\t.reg .b32 dl, dh, rl, rh;\n\t"
-        "mov.b64 {dl, dh}, %2;\n\t"
-        "mad.wide.u32 %0, dl, %3, %1;\n\t"
-        "mov.b64 {rl, rh}, %0;\n\t"
-        "mad.lo.u32 rh, dh, %3, rh;\n\t"
-        "mov.b64 %0, {rl, rh};\n\t}"
-        : "=l"(r)
-        : "l"(X), "l"(D), "r"(one));
-    return r;
-}
+// The next sample's position: X + D, exactly.  (A plain 64-bit addition: a form built from
+// inline multiply-adds, meant to move the work to the FMA pipe, cost register moves around
+// every use.)
+__device__ __forceinline__ long long fx_step(long long X, long long D) { return X + D; }
 
 // floor(p + 1/2): the nearest voxel (round half up).
 __device__ __forceinline__ int fx_round(long long p) { return (int)((p + 0x80000000LL) >> 32); }

@@ -327,7 +327,7 @@ __device__ __forceinline__ bool take_pair(St &st, const RenderArgs &a, float2 c,
 template <int MODE, class EP, int M, bool FILT, class S, class St>
 __device__ __forceinline__ bool slab_march(const S &s, const RenderArgs &a, St &st, long long &X, long long &Y,
                                            long long &Z, long long DX, long long DY, long long DZ, int &k, int kb,
-                                           const SlabHdr &h, const typename EP::raw *stage, unsigned one)
+                                           const SlabHdr &h, const typename EP::raw *stage)
 {
     using raw = typename EP::raw;
     using val = decltype(EP::cvt(raw{}));
@@ -374,9 +374,9 @@ __device__ __forceinline__ bool slab_march(const S &s, const RenderArgs &a, St &
             stop = take_pair<MODE, FILT>(st, a, trilerp_pair(c, fx, fy, fz), k);
         else
             stop = take_value<MODE, FILT>(st, a, trilerp(c, fx, fy, fz), k);
-        X = fx_step(X, DX, one);
-        Y = fx_step(Y, DY, one);
-        Z = fx_step(Z, DZ, one);
+        X = fx_step(X, DX);
+        Y = fx_step(Y, DY);
+        Z = fx_step(Z, DZ);
         if (stop) {
             ++k;
             return true;
@@ -417,7 +417,6 @@ struct SlabArgs {
     unsigned *err;  // the library's device error word
     int ntiles;
     int polls;      // bound of every wait (sleeping polls)
-    unsigned one;   // 1 (see fx_step)
 };
 
 struct SlabShared {
@@ -628,7 +627,7 @@ __device__ void slab_consumer(const S &s, const shw_camera &cam, const RenderArg
                 const long long DX = r.D[0], DY = r.D[1], DZ = r.D[2];
                 bool stop;
 #define SHW_SLAB_MARCH(MM, FF) \
-    stop = slab_march<MODE, EP, MM, FF>(s, a, st, X, Y, Z, DX, DY, DZ, k, kb, h, stg, sa.one)
+    stop = slab_march<MODE, EP, MM, FF>(s, a, st, X, Y, Z, DX, DY, DZ, k, kb, h, stg)
                 if (a.filter == SHW_FILTER_NONE) {
                     if (h.major == 0) SHW_SLAB_MARCH(0, false);
                     else if (h.major == 1) SHW_SLAB_MARCH(1, false);
@@ -750,7 +749,6 @@ shw_status slab_launch(int mode, const S &s, const void *base, const shw_camera 
     sa.ntiles = a.tiles_x * a.tiles_y;
     sa.err = device_error_word();
     sa.polls = kSlabWaitPolls;
-    sa.one = 1u;
     sa.ctr = work_counter(st);
     if (!sa.ctr) return SHW_ECUDA;
     if constexpr (EP::kPair) {
