@@ -557,20 +557,20 @@ def run_ours(args):
 TRAFFIC_PER_LAUNCH: dict = {
     "smooth": 1386283008 + 1036524288,
     "smooth2": 2387365376 + 2102186240,
-    "render_mip": 1872291840 + 19960832,
-    "render_avg": 1903843840 + 17025792,
-    "render_composite": 1776742912 + 17455616,
-    "render_spectral": 1926076672 + 17346048,
-    "render_ratio": 3963735040 + 25214720,
+    "render_mip": 1850765056 + 19937024,
+    "render_avg": 1862723328 + 16973568,
+    "render_composite": 1763378944 + 17127424,
+    "render_spectral": 1877628928 + 17221376,
+    "render_ratio": 3900478720 + 24024064,
 }
 # warp instructions executed per sample of each render (same file: smsp__inst_executed.sum
 # over the render's samples, 371,839,071; compositing 359,686,584):
 WARP_INST_PER_SAMPLE: dict = {
-    "mip": 2.362,
-    "avg": 2.495,
-    "composite": 3.324,
-    "spectral": 2.463,
-    "ratio": 3.120,
+    "mip": 2.322,
+    "avg": 2.455,
+    "composite": 3.283,
+    "spectral": 2.423,
+    "ratio": 3.079,
 }
 
 

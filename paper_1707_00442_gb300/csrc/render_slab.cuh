@@ -324,13 +324,19 @@ __device__ __forceinline__ bool take_pair(St &st, const RenderArgs &a, float2 c,
 // with half-voxel steps some lane of a warp enters a new cell at nearly every sample, so a
 // per-lane cell cache would only add its checks (survey renders 2-5 % faster without it).
 // True if the transfer function stopped the ray (k is then the count of samples processed).
-template <int MODE, class EP, int M, bool FILT, class S, class St>
+// BX: the chunk width of this slab's box when fixed at compile time (the row pitch of x- and
+// z-major boxes, the plane pitch of y-major ones), so that half of the 8 corner loads take
+// immediate offsets; 0: both pitches from the header.
+template <int MODE, class EP, int M, bool FILT, int BX, class S, class St>
 __device__ __forceinline__ bool slab_march(const S &s, const RenderArgs &a, St &st, long long &X, long long &Y,
                                            long long &Z, long long DX, long long DY, long long DZ, int &k, int kb,
                                            const SlabHdr &h, const typename EP::raw *stage)
 {
     using raw = typename EP::raw;
     using val = decltype(EP::cvt(raw{}));
+    // the box's y and z pitches (elements); one of them the chunk width
+    const int sy = (BX > 0 && M != 1) ? BX : h.sy, sz = (BX > 0 && M == 1) ? BX : h.sz;
+    if constexpr (kChecked) SHW_CHECK(sy == h.sy && sz == h.sz);
     for (; k < kb; ++k) {
         const int cx = fx_cell(X), cy = fx_cell(Y), cz = fx_cell(Z);
         const int cm = M == 0 ? cx : (M == 1 ? cy : cz);
@@ -346,14 +352,14 @@ __device__ __forceinline__ bool slab_march(const S &s, const RenderArgs &a, St &
             const bool inbox = (unsigned)lx < (unsigned)h.ex1 && (M == 1 || (unsigned)ly < (unsigned)h.ey1) &&
                                (M == 2 || (unsigned)lz < (unsigned)h.ez1);
             if (inbox) {
-                int off = lx + ly * h.sy + lz * h.sz;
+                int off = lx + ly * sy + lz * sz;
                 if constexpr (kChecked) {  // the cell's far corner lies in the stage
-                    const bool ok = off >= 0 && off + h.sz + h.sy + 1 < SlabGeom<EP>::kStageElems;
+                    const bool ok = off >= 0 && off + sz + sy + 1 < SlabGeom<EP>::kStageElems;
                     SHW_CHECK(ok);
                     if (!ok) off = 0;
                 }
                 const raw *q = stage + off;
-                const raw *qy = q + h.sy, *qz = q + h.sz, *qyz = qz + h.sy;
+                const raw *qy = q + sy, *qz = q + sz, *qyz = qz + sy;
                 c[0] = EP::cvt(q[0]);
                 c[1] = EP::cvt(q[1]);
                 c[2] = EP::cvt(qy[0]);
@@ -626,16 +632,22 @@ __device__ void slab_consumer(const S &s, const shw_camera &cam, const RenderArg
                 const raw *stg = reinterpret_cast<const raw *>(stages + (size_t)si * kSlabStageBytes);
                 const long long DX = r.D[0], DY = r.D[1], DZ = r.D[2];
                 bool stop;
-#define SHW_SLAB_MARCH(MM, FF) \
-    stop = slab_march<MODE, EP, MM, FF>(s, a, st, X, Y, Z, DX, DY, DZ, k, kb, h, stg)
-                if (a.filter == SHW_FILTER_NONE) {
-                    if (h.major == 0) SHW_SLAB_MARCH(0, false);
-                    else if (h.major == 1) SHW_SLAB_MARCH(1, false);
-                    else SHW_SLAB_MARCH(2, false);
+                using G = SlabGeom<EP>;
+#define SHW_SLAB_MARCH(MM, FF, BB) \
+    stop = slab_march<MODE, EP, MM, FF, BB>(s, a, st, X, Y, Z, DX, DY, DZ, k, kb, h, stg)
+                if (a.filter == SHW_FILTER_NONE) {  // the chunk width as a compile-time pitch
+                    if (h.major == 0) SHW_SLAB_MARCH(0, false, G::kBXx);
+                    else if (h.major == 1) {
+                        if (h.wide) SHW_SLAB_MARCH(1, false, G::kBXw);
+                        else SHW_SLAB_MARCH(1, false, G::kBXn);
+                    } else {
+                        if (h.wide) SHW_SLAB_MARCH(2, false, G::kBXw);
+                        else SHW_SLAB_MARCH(2, false, G::kBXn);
+                    }
                 } else {
-                    if (h.major == 0) SHW_SLAB_MARCH(0, true);
-                    else if (h.major == 1) SHW_SLAB_MARCH(1, true);
-                    else SHW_SLAB_MARCH(2, true);
+                    if (h.major == 0) SHW_SLAB_MARCH(0, true, 0);
+                    else if (h.major == 1) SHW_SLAB_MARCH(1, true, 0);
+                    else SHW_SLAB_MARCH(2, true, 0);
                 }
 #undef SHW_SLAB_MARCH
                 if (stop) {
