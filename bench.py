@@ -676,7 +676,9 @@ def variant_precision(shw, torch, step, W, per_kernel, samples_per):
 def variant_batch(shw, torch, step, B):
     """2,000 sub-cubes (axes log-uniform in [32, 256]; float32 and BF16 bricks alternating; MIP and
     compositing alternating; 256x256 random views): one graph-captured persistent launch
-    against one launch per sub-cube issued by the library's own loop."""
+    against one launch per sub-cube issued by the library's own loop.  Then the same
+    sub-cubes all as float32 in a plan that rounds them into bfloat16 bricks of its own, the
+    autotuner choosing the brick edge (16 or 32) with the tile and CTAs per SM."""
     import concurrent.futures as cf
     dev = step.s1.device
     dims = scene.batch_dims(n=B["n"], lo=B["lo"], hi=B["hi"])
@@ -686,7 +688,7 @@ def variant_batch(shw, torch, step, B):
     with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
         cubes = list(ex.map(lambda i: scene.batch_subcube(i, tuple(int(x) for x in dims[i])), range(len(dims))))
     log(f"batch sub-cubes generated in {time.time() - t0:.1f}s")
-    items = []
+    items, f32_items = [], []
     nvox = 0
     for i, cube in enumerate(cubes):
         d = tuple(int(x) for x in dims[i])
@@ -695,6 +697,7 @@ def variant_batch(shw, torch, step, B):
         vol = ct if i % 2 == 0 else shw.pack_bricks(ct, "bf16")
         cam = scene.orbit_camera(d, views[i][0], views[i][1], B["width"], B["height"])
         items.append((vol, cam, B["modes"][(i // 2) % 2]))
+        f32_items.append((ct, cam, B["modes"][(i // 2) % 2]))
     del cubes
     plan = shw.BatchPlan(items, lut=step.lut, step=B["step"], opacity_scale=B["opacity_scale"])
     t_plan = _timeit(torch, plan.render, reps=3)
@@ -706,13 +709,31 @@ def variant_batch(shw, torch, step, B):
     info = plan.info
     plan.close()
     del items
+    # every sub-cube as float32, rounded by the plan into bfloat16 bricks of the edge it tunes
+    t0 = time.time()
+    own = shw.BatchPlan(f32_items, lut=step.lut, step=B["step"], opacity_scale=B["opacity_scale"], pack="bf16",
+                        retune=True)
+    t_create = time.time() - t0
+    t_own = _timeit(torch, own.render, reps=3)
+    oinf = own.info
+    own.close()
+    del f32_items
+    by_edge = {}
+    for tile, ctas, edge, ms in oinf["candidates"]:
+        if str(edge) not in by_edge or ms < by_edge[str(edge)]["tune_ms"]:
+            by_edge[str(edge)] = {"tile": tile, "ctas_per_sm": ctas, "tune_ms": round(ms, 3)}
+    own_bricks = {"persistent_graph_ms": round(t_own, 3), "subcubes_per_s": round(len(dims) / (t_own * 1e-3), 1),
+                  "brick": oinf["brick"], "tile": oinf["tile"], "ctas_per_sm": oinf["ctas_per_sm"],
+                  "packed_gb": round(oinf["packed_bytes"] / 1e9, 3), "plan_create_s": round(t_create, 2),
+                  "best_by_brick_edge": by_edge}
     return {"n": int(len(dims)), "voxels": int(nvox), "samples": ns,
             "persistent_graph_ms": round(t_plan, 3), "one_launch_per_cube_ms": round(t_loop, 3),
             "subcubes_per_s": round(len(dims) / (t_plan * 1e-3), 1),
             "subcubes_per_s_one_launch_per_cube": round(len(dims) / (t_loop * 1e-3), 1),
             "speedup": round(t_loop / t_plan, 3), "gsamples_per_s": round(ns / (t_plan * 1e-3) / 1e9, 2),
             "tile": info["tile"], "ctas_per_sm": info["ctas_per_sm"],
-            "baseline": "one shw_render launch per sub-cube from the library's loop (shw_render_items)"}
+            "baseline": "one shw_render launch per sub-cube from the library's loop (shw_render_items)",
+            "own_bf16_bricks": own_bricks}
 
 
 def variant_adjoint(shw, torch, step):

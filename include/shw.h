@@ -48,7 +48,7 @@
 extern "C" {
 #endif
 
-#define SHW_ABI_VERSION 4
+#define SHW_ABI_VERSION 5
 #define SHW_LUT_SIZE 256
 #define SHW_MAX_SMOOTH_RADIUS 16
 #define SHW_MAX_SMOOTH_ARM 16   /* in-ray box smoothing: neighbours on each side */
@@ -355,8 +355,16 @@ uint32_t shw_set_debug_flags(uint32_t flags);
 
 typedef struct shw_batch_plan shw_batch_plan; /* opaque */
 
-#define SHW_BATCH_NO_TUNE 1 /* skip the autotuner: 16 x 16 tiles, 4 CTAs per SM */
+#define SHW_BATCH_NO_TUNE 1 /* skip the autotuner: 16 x 16 tiles, 4 CTAs per SM, 32^3 bricks when packing */
 #define SHW_BATCH_RETUNE 2  /* re-run the autotuner even if this batch signature is cached */
+#define SHW_BATCH_PACK_BF16 4 /* the plan rounds every SHW_F32 item into bfloat16 bricks that it
+                                 allocates and owns, with the brick edge (16 or 32 voxels) that the
+                                 autotuner picks; each image is that of shw_render on the item's
+                                 shw_pack_bricks storage (the values and the arithmetic do not
+                                 depend on the edge).  Items of other storages render as given */
+#define SHW_BATCH_PACK_F16 8  /* the same with IEEE binary16 */
+#define SHW_BATCH_BRICK_16 16 /* with a PACK flag: 16^3 bricks, the edge not tuned */
+#define SHW_BATCH_BRICK_32 32 /* with a PACK flag: 32^3 bricks, the edge not tuned */
 
 typedef struct {
     shw_volume vol;  /* the sub-cube: any storage, < 2^31 voxels */
@@ -369,20 +377,28 @@ typedef struct {
     int32_t n_items, n_work;     /* items, work items (tiles) */
     int32_t tile, ctas_per_sm;   /* the chosen tile edge (pixels) and persistent CTAs per SM */
     int32_t grid, tuned;         /* CTAs launched; 1 if the autotuner ran for this plan */
-    int32_t n_candidates;
-    int32_t cand_tile[8], cand_ctas_per_sm[8];
-    float tune_ms[8];            /* measured time of each candidate (-1 when not tuned) */
+    int32_t brick;               /* edge of the plan's own bricks (16 or 32); 0 when it packs none */
+    int32_t n_candidates;        /* configurations the autotuner times: tile x CTAs per SM, and
+                                    x brick edge when the plan packs bricks and the edge is free */
+    int32_t cand_tile[16], cand_ctas_per_sm[16], cand_brick[16];
+    float tune_ms[16];           /* measured time of each candidate (-1 when not tuned) */
+    int64_t packed_bytes;        /* device bytes of the plan's own bricks */
 } shw_batch_info;
 
 /* Build a plan for n items sharing the parameters p (p->mode is ignored: each item
  * has its own; interp, step, lo, hi, lut, opacity_scale, term_alpha are shared).
  * Allocates device memory for the item table, the work list and the counter, and
- * captures the launch into a CUDA graph.  Unless SHW_BATCH_NO_TUNE, the first plan
- * of a batch signature (mean size class, image size, storages, modes) times every
- * candidate configuration on `stream` -- rendering into the items' outputs -- and
- * keeps the fastest; later plans of the same signature reuse the choice.
+ * captures the launch into a CUDA graph.  With SHW_BATCH_PACK_BF16 or _F16 it also
+ * allocates the 16-bit bricks of its float32 items (the layout of shw_pack_bricks with
+ * 32 replaced by the edge E and 34 by E + 2) and fills them on `stream`; the float32
+ * cubes are not read after that.  Unless SHW_BATCH_NO_TUNE, the first plan of a batch
+ * signature (mean size class, image size, storages, modes, packing) times every
+ * candidate configuration on `stream` -- rendering into the items' outputs -- and keeps
+ * the fastest; later plans of the same signature reuse the choice.  Tuning the brick
+ * edge packs the items at both edges, so for a moment the plan holds both copies.
  * The plan keeps the item pointers (cubes, outputs, colour map) until destroyed.
- * Errors: SHW_EINVAL, SHW_EUNSUPPORTED, SHW_ENOMEM (allocation), SHW_ECUDA (capture),
+ * Errors: SHW_EINVAL (also: both PACK flags, both BRICK flags, or a BRICK flag without a
+ * PACK flag), SHW_EUNSUPPORTED, SHW_ENOMEM (allocation), SHW_ECUDA (capture),
  * SHW_EDEVICE.  SHW_DEBUG_FAULT_ALLOC / SHW_DEBUG_FAULT_GRAPH make the allocation or the
  * capture fail (host-side fault injection, see shw_set_debug_flags). */
 shw_status shw_batch_plan_create(shw_batch_plan **plan, const shw_batch_item *items, int32_t n,

@@ -19,7 +19,7 @@ MODES = {"mip": 0, "avg": 1, "composite": 2, "spectral": 3, "ratio": 4, "moment1
 INTERP = {"nearest": 0, "trilinear": 1}
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2, "pair": 3, "bf16_pair": 4, "f16_pair": 5, "bf16_linear": 6,
            "f16_linear": 7, "bf16_linear_pair": 8, "f16_linear_pair": 9}
-ABI_VERSION = 4
+ABI_VERSION = 5
 LUT_SIZE = 256
 MAX_SMOOTH_RADIUS = 16
 BRICK = 32
@@ -57,11 +57,14 @@ class BatchItem(C.Structure):
 
 class BatchInfo(C.Structure):
     _fields_ = [("n_items", C.c_int32), ("n_work", C.c_int32), ("tile", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("grid", C.c_int32), ("tuned", C.c_int32), ("n_candidates", C.c_int32),
-                ("cand_tile", C.c_int32 * 8), ("cand_ctas_per_sm", C.c_int32 * 8), ("tune_ms", C.c_float * 8)]
+                ("grid", C.c_int32), ("tuned", C.c_int32), ("brick", C.c_int32), ("n_candidates", C.c_int32),
+                ("cand_tile", C.c_int32 * 16), ("cand_ctas_per_sm", C.c_int32 * 16), ("cand_brick", C.c_int32 * 16),
+                ("tune_ms", C.c_float * 16), ("packed_bytes", C.c_int64)]
 
 
 BATCH_NO_TUNE, BATCH_RETUNE = 1, 2
+BATCH_PACK = {None: 0, "bf16": 4, "f16": 8}   # the plan rounds float32 items into its own 16-bit bricks
+BATCH_BRICK = {None: 0, 16: 16, 32: 32}       # with a pack storage: fix the brick edge (else tuned)
 
 
 class ShwError(RuntimeError):

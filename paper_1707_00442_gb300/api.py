@@ -298,10 +298,12 @@ class BatchPlan:
 
     items: sequence of (vol, cam, mode) or (vol, cam, mode, out_rgba); vol is a float32 CUDA
     cube or a BrickVolume; mode one of "mip", "avg", "composite", "spectral".  Missing
-    outputs are allocated.  The plan keeps references to every tensor it points at."""
+    outputs are allocated.  The plan keeps references to every tensor it points at.
+    pack: None, "bf16" or "f16" -- the plan rounds the float32 items into 16-bit bricks it
+    owns; brick: None (the autotuner picks 16 or 32 when every item is packed), 16 or 32."""
 
     def __init__(self, items, *, lut: torch.Tensor, interp="trilinear", step=0.5, lo=-3.0, hi=8.0,
-                 opacity_scale=1.0, term_alpha=0.99, tune=True, retune=False):
+                 opacity_scale=1.0, term_alpha=0.99, tune=True, retune=False, pack=None, brick=None):
         self._plan = None
         p = params_struct("mip", lut, interp=interp, step=step, lo=lo, hi=hi, opacity_scale=opacity_scale,
                           term_alpha=term_alpha)
@@ -318,7 +320,8 @@ class BatchPlan:
             arr[i].mode = MODES[mode]
             self.outputs.append(out)
             self._keep.append(vol)
-        flags = (0 if tune else _lib.BATCH_NO_TUNE) | (_lib.BATCH_RETUNE if retune else 0)
+        flags = ((0 if tune else _lib.BATCH_NO_TUNE) | (_lib.BATCH_RETUNE if retune else 0) | _lib.BATCH_PACK[pack]
+                 | _lib.BATCH_BRICK[brick])
         handle = C.c_void_p()
         check(lib().shw_batch_plan_create(C.byref(handle), arr, len(items), C.byref(p), flags, _stream()),
               "shw_batch_plan_create")
@@ -342,8 +345,9 @@ class BatchPlan:
         check(lib().shw_batch_plan_info(self._plan, C.byref(inf)), "shw_batch_plan_info")
         n = inf.n_candidates
         return {"n_items": inf.n_items, "n_work": inf.n_work, "tile": inf.tile, "ctas_per_sm": inf.ctas_per_sm,
-                "grid": inf.grid, "tuned": bool(inf.tuned),
-                "candidates": [(inf.cand_tile[i], inf.cand_ctas_per_sm[i], float(inf.tune_ms[i])) for i in range(n)]}
+                "grid": inf.grid, "tuned": bool(inf.tuned), "brick": inf.brick, "packed_bytes": int(inf.packed_bytes),
+                "candidates": [(inf.cand_tile[i], inf.cand_ctas_per_sm[i], inf.cand_brick[i], float(inf.tune_ms[i]))
+                               for i in range(n)]}
 
     def close(self):
         if self._plan is not None:

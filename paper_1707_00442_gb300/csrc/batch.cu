@@ -9,8 +9,9 @@
 // counter -- no CTA ever waits on another -- and renders each tile with the same
 // per-ray code as shw_render.  The counter reset and the launch are captured once
 // into a CUDA graph, so a batch render is a single graph launch.  An autotuner
-// times the candidate tile shapes and CTAs-per-SM at plan creation and caches the
-// winner per batch signature.
+// times the candidate tile shapes and CTAs-per-SM -- and, for plans that round their
+// float32 items into 16-bit bricks of their own, the brick edge (16 or 32 voxels) -- at
+// plan creation and caches the winner per batch signature.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -22,102 +23,38 @@
 #include <tuple>
 #include <vector>
 
-#include "render_impl.cuh"
+#include "batch_kernel.cuh"
 
 namespace shw {
 
 bool valid_volume(const shw_volume *v);
 bool valid_camera(const shw_camera *c);
 long long max_samples(const shw_volume *v, float step);
+size_t bricked_bytes_edge(int nx, int ny, int nz, int edge);
+shw_status pack_bricks_edge(const float *in, int nx, int ny, int nz, int storage, int edge, void *out,
+                            cudaStream_t st);
 
-struct BatchItemDev {
-    const void *data;
-    float4 *rgba;
-    int nx, ny, nz, storage, mode, tiles_x, nbx, nby, nmax, pad;
-    shw_camera cam;
-};
-
-struct BatchShared {
-    const float4 *lut;
-    float step, lo, inv_range, opacity_scale, term_alpha;
-    int nwork;
-};
-
-template <int INTERP, class S>
-__device__ __forceinline__ void batch_pixel(const S &s, const BatchItemDev &it, const RenderArgs &a,
-                                            const float4 *lut_s, int px, int py)
+BatchKernel batch_kernel_for(int tile, int interp, int brick, bool f32)
 {
-    switch (it.mode) {
-    case SHW_MIP: render_pixel<SHW_MIP, INTERP, S>(s, s, it.cam, a, lut_s, px, py); break;
-    case SHW_AVG: render_pixel<SHW_AVG, INTERP, S>(s, s, it.cam, a, lut_s, px, py); break;
-    case SHW_COMPOSITE: render_pixel<SHW_COMPOSITE, INTERP, S>(s, s, it.cam, a, lut_s, px, py); break;
-    default: render_pixel<SHW_SPECTRAL, INTERP, S>(s, s, it.cam, a, lut_s, px, py); break;
-    }
+    if (brick == 16) return batch_kernel_b16(tile, interp);
+    if (!f32) return batch_kernel_b32(tile, interp);
+    if (tile == 8)
+        return interp == SHW_NEAREST ? batch_kernel<8, SHW_NEAREST, 32, true> : batch_kernel<8, SHW_TRILINEAR, 32, true>;
+    return interp == SHW_NEAREST ? batch_kernel<16, SHW_NEAREST, 32, true>
+                                 : batch_kernel<16, SHW_TRILINEAR, 32, true>;
 }
 
-template <int TILE, int INTERP>
-__global__ void __launch_bounds__(TILE *TILE) batch_kernel(const BatchItemDev *__restrict__ items,
-                                                           const int2 *__restrict__ work, int *counter, BatchShared sh)
-{
-    __shared__ float4 lut_s[kLut];
-    __shared__ int w_s;
-    for (int i = threadIdx.x; i < kLut; i += blockDim.x) lut_s[i] = sh.lut[i];
-    constexpr int WX = TILE / 8;  // warps across a tile row; each warp covers 8 x 4 pixels
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int lx = (warp % WX) * 8 + (lane & 7), ly = (warp / WX) * 4 + (lane >> 3);
-    for (;;) {
-        __syncthreads();  // everyone has read w_s (and the colour map is loaded)
-        if (threadIdx.x == 0) w_s = atomicAdd(counter, 1);
-        __syncthreads();
-        const int w = w_s;
-        if (w >= sh.nwork) break;
-        const int2 wi = work[w];
-        const BatchItemDev it = items[wi.x];
-        const int px = (wi.y % it.tiles_x) * TILE + lx, py = (wi.y / it.tiles_x) * TILE + ly;
-        if (px >= it.cam.width || py >= it.cam.height) continue;
-        RenderArgs a{};
-        a.rgba = it.rgba;
-        a.lut = sh.lut;
-        a.width = it.cam.width;
-        a.height = it.cam.height;
-        a.ckpt_interval = 64;
-        a.nmax = it.nmax;
-        a.step = sh.step;
-        a.lo = sh.lo;
-        a.inv_range = sh.inv_range;
-        a.opacity_scale = sh.opacity_scale;
-        a.term_alpha = sh.term_alpha;
-        a.nx = it.nx;
-        a.ny = it.ny;
-        a.nz = it.nz;
-        if (it.storage == SHW_F32) {
-            const SamplerF32<int> s{static_cast<const float *>(it.data), it.nx, it.ny, it.nz, it.nx, it.nx * it.ny};
-            batch_pixel<INTERP>(s, it, a, lut_s, px, py);
-        } else if (it.storage == SHW_BF16_BRICK) {
-            const SamplerBrick<__nv_bfloat16> s{static_cast<const unsigned short *>(it.data), it.nx, it.ny, it.nz,
-                                                it.nbx, it.nby};
-            batch_pixel<INTERP>(s, it, a, lut_s, px, py);
-        } else {
-            const SamplerBrick<__half> s{static_cast<const unsigned short *>(it.data), it.nx, it.ny, it.nz, it.nbx,
-                                         it.nby};
-            batch_pixel<INTERP>(s, it, a, lut_s, px, py);
-        }
-    }
-}
-
-using BatchKernel = void (*)(const BatchItemDev *, const int2 *, int *, BatchShared);
-
-static BatchKernel pick_kernel(int tile, int interp)
-{
-    if (tile == 8) return interp == SHW_NEAREST ? batch_kernel<8, SHW_NEAREST> : batch_kernel<8, SHW_TRILINEAR>;
-    return interp == SHW_NEAREST ? batch_kernel<16, SHW_NEAREST> : batch_kernel<16, SHW_TRILINEAR>;
-}
-
-struct Candidate {
+struct TileChoice {
     int tile, ctas_per_sm;
 };
-static const Candidate kCandidates[] = {{16, 2}, {16, 4}, {16, 8}, {8, 8}, {8, 16}, {8, 32}};
-constexpr int kNumCandidates = (int)(sizeof(kCandidates) / sizeof(kCandidates[0]));
+static const TileChoice kTileChoices[] = {{16, 2}, {16, 4}, {16, 8}, {8, 8}, {8, 16}, {8, 32}};
+constexpr int kNumTileChoices = (int)(sizeof(kTileChoices) / sizeof(kTileChoices[0]));
+constexpr int kDefaultTileChoice = 1;  // {16, 4}
+
+// one configuration the autotuner times; brick: edge of the plan's own bricks (0: none)
+struct Candidate {
+    int tile, ctas_per_sm, brick;
+};
 
 // process-wide cache of tuned choices, keyed by the batch signature
 static std::mutex g_tune_mu;
@@ -137,6 +74,14 @@ struct shw_batch_plan {
     BatchShared sh{};
     std::vector<BatchItemDev> items;
     std::vector<int> order;  // items sorted by estimated cost, descending
+    std::vector<Candidate> cands;
+    // bricks the plan packs itself (SHW_BATCH_PACK_*): one buffer per edge (16, 32)
+    int brick = 0, pack_storage = 0;
+    bool any_f32 = true;             // an item left as float32: the kernel with the float32 path
+    std::vector<const float *> src;  // each packed item's float32 cube, else nullptr
+    void *d_packed[2] = {nullptr, nullptr};
+    size_t packed_bytes[2] = {0, 0};
+    std::vector<size_t> pack_off[2];
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -152,6 +97,8 @@ static void plan_free(shw_batch_plan *pl)
     if (pl->d_items) cudaFree(pl->d_items);
     if (pl->d_work) cudaFree(pl->d_work);
     if (pl->d_counter) cudaFree(pl->d_counter);
+    for (void *b : pl->d_packed)
+        if (b) cudaFree(b);
     delete pl;
 }
 
@@ -187,12 +134,64 @@ static shw_status build_work(shw_batch_plan *pl, int tile)
     return SHW_OK;
 }
 
+static int edge_slot(int edge) { return edge == 16 ? 0 : 1; }
+
+// The plan's bricks of one edge: allocated and filled on `st` the first time they are asked for.
+static shw_status pack_edge(shw_batch_plan *pl, int edge, cudaStream_t st)
+{
+    const int k = edge_slot(edge);
+    if (pl->d_packed[k]) return SHW_OK;
+    std::vector<size_t> &off = pl->pack_off[k];
+    off.assign(pl->n_items, 0);
+    size_t total = 0;
+    for (int i = 0; i < pl->n_items; ++i) {
+        if (!pl->src[i]) continue;
+        const BatchItemDev &it = pl->items[i];
+        off[i] = total;
+        total += (bricked_bytes_edge(it.nx, it.ny, it.nz, edge) + 255) & ~(size_t)255;
+    }
+    if (fault(SHW_DEBUG_FAULT_ALLOC) || cudaMalloc(&pl->d_packed[k], total) != cudaSuccess) {
+        cudaGetLastError();
+        pl->d_packed[k] = nullptr;
+        return SHW_ENOMEM;
+    }
+    pl->packed_bytes[k] = total;
+    for (int i = 0; i < pl->n_items; ++i) {
+        if (!pl->src[i]) continue;
+        const BatchItemDev &it = pl->items[i];
+        const shw_status s = pack_bricks_edge(pl->src[i], it.nx, it.ny, it.nz, pl->pack_storage, edge,
+                                              static_cast<unsigned char *>(pl->d_packed[k]) + off[i], st);
+        if (s != SHW_OK) return s;
+    }
+    return SHW_OK;
+}
+
+// Point the packed items at their bricks of one edge (build_work copies the table).
+static void use_edge(shw_batch_plan *pl, int edge)
+{
+    const int k = edge_slot(edge);
+    for (int i = 0; i < pl->n_items; ++i) {
+        if (!pl->src[i]) continue;
+        BatchItemDev &it = pl->items[i];
+        it.data = static_cast<unsigned char *>(pl->d_packed[k]) + pl->pack_off[k][i];
+        it.storage = pl->pack_storage;
+        it.brick = edge;
+        it.nbx = ceil_div(it.nx, edge);
+        it.nby = ceil_div(it.ny, edge);
+    }
+    pl->brick = edge;
+}
+
+static BatchKernel plan_kernel(const shw_batch_plan *pl)
+{
+    return batch_kernel_for(pl->tile, pl->interp, pl->brick == 16 ? 16 : 32, pl->any_f32);
+}
+
 static shw_status launch_direct(shw_batch_plan *pl, int ctas_per_sm, cudaStream_t st)
 {
     if (cudaMemsetAsync(pl->d_counter, 0, sizeof(int), st) != cudaSuccess) return SHW_ECUDA;
     const int grid = pl->sms * ctas_per_sm;
-    pick_kernel(pl->tile, pl->interp)<<<grid, pl->tile * pl->tile, 0, st>>>(pl->d_items, pl->d_work, pl->d_counter,
-                                                                             pl->sh);
+    plan_kernel(pl)<<<grid, pl->tile * pl->tile, 0, st>>>(pl->d_items, pl->d_work, pl->d_counter, pl->sh);
     return after_launch();
 }
 
@@ -206,8 +205,7 @@ static shw_status capture(shw_batch_plan *pl)
     if (cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SHW_ECUDA;
     cudaMemsetAsync(pl->d_counter, 0, sizeof(int), pl->cap);
     pl->grid = pl->sms * pl->ctas_per_sm;
-    pick_kernel(pl->tile, pl->interp)<<<pl->grid, pl->tile * pl->tile, 0, pl->cap>>>(pl->d_items, pl->d_work,
-                                                                                     pl->d_counter, pl->sh);
+    plan_kernel(pl)<<<pl->grid, pl->tile * pl->tile, 0, pl->cap>>>(pl->d_items, pl->d_work, pl->d_counter, pl->sh);
     cudaError_t e = cudaStreamEndCapture(pl->cap, &pl->graph);
     if (e != cudaSuccess || !pl->graph) {
         cudaGetLastError();
@@ -222,7 +220,8 @@ static shw_status capture(shw_batch_plan *pl)
 
 static std::string signature(const shw_batch_plan *pl)
 {
-    // size class of the work: log2 of the mean item voxel count and image area, storages, modes
+    // size class of the work: log2 of the mean item voxel count and image area, storages, modes,
+    // the packing storage and the brick edges tried
     double vox = 0.0, pix = 0.0;
     int smask = 0, mmask = 0;
     for (const auto &it : pl->items) {
@@ -232,10 +231,12 @@ static std::string signature(const shw_batch_plan *pl)
         mmask |= 1 << it.mode;
     }
     const int n = std::max(1, pl->n_items);
-    char buf[160];
-    std::snprintf(buf, sizeof buf, "i%d v%d p%d n%d s%d m%d sm%d", pl->interp, (int)std::lround(std::log2(vox / n + 1)),
-                  (int)std::lround(std::log2(pix / n + 1)), (int)std::lround(std::log2((double)n)), smask, mmask,
-                  pl->sms);
+    int emask = 0;
+    for (const Candidate &c : pl->cands) emask |= c.brick;
+    char buf[192];
+    std::snprintf(buf, sizeof buf, "i%d v%d p%d n%d s%d m%d sm%d k%d e%d", pl->interp,
+                  (int)std::lround(std::log2(vox / n + 1)), (int)std::lround(std::log2(pix / n + 1)),
+                  (int)std::lround(std::log2((double)n)), smask, mmask, pl->sms, pl->pack_storage, emask);
     return buf;
 }
 
@@ -245,18 +246,24 @@ static shw_status autotune(shw_batch_plan *pl, cudaStream_t st, int *best_out)
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return SHW_ECUDA;
     int best = -1;
     float best_ms = 1e30f;
-    for (int c = 0; c < kNumCandidates; ++c) {
-        shw_status s = build_work(pl, kCandidates[c].tile);
+    for (int c = 0; c < (int)pl->cands.size(); ++c) {
+        const Candidate &cd = pl->cands[c];
+        shw_status s = SHW_OK;
+        if (cd.brick && cd.brick != pl->brick) {
+            s = pack_edge(pl, cd.brick, st);
+            if (s == SHW_OK) use_edge(pl, cd.brick);
+        }
+        if (s == SHW_OK) s = build_work(pl, cd.tile);
         if (s != SHW_OK) {
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             return s;
         }
-        s = launch_direct(pl, kCandidates[c].ctas_per_sm, st);  // warm-up
+        s = launch_direct(pl, cd.ctas_per_sm, st);  // warm-up
         float ms = 1e30f;
         for (int rep = 0; rep < 2 && s == SHW_OK; ++rep) {
             cudaEventRecord(e0, st);
-            s = launch_direct(pl, kCandidates[c].ctas_per_sm, st);
+            s = launch_direct(pl, cd.ctas_per_sm, st);
             cudaEventRecord(e1, st);
             if (cudaEventSynchronize(e1) != cudaSuccess) s = SHW_ECUDA;
             float t = 0.0f;
@@ -295,6 +302,12 @@ shw_status shw_batch_plan_create(shw_batch_plan **out, const shw_batch_item *ite
     if (!std::isfinite(p->step) || !(p->step > 0.0f) || !(p->hi > p->lo) || !std::isfinite(p->lo) ||
         !std::isfinite(p->hi) || !std::isfinite(p->opacity_scale) || !std::isfinite(p->term_alpha))
         return SHW_EINVAL;
+    const int pack = flags & (SHW_BATCH_PACK_BF16 | SHW_BATCH_PACK_F16);
+    const int fixed = flags & (SHW_BATCH_BRICK_16 | SHW_BATCH_BRICK_32);
+    if (pack == (SHW_BATCH_PACK_BF16 | SHW_BATCH_PACK_F16) || fixed == (SHW_BATCH_BRICK_16 | SHW_BATCH_BRICK_32) ||
+        (fixed && !pack))
+        return SHW_EINVAL;
+    int n_own = 0;  // float32 items the plan packs
     for (int i = 0; i < n; ++i) {
         const shw_batch_item &b = items[i];
         if (!valid_volume(&b.vol) || !valid_camera(&b.cam) || !b.out_rgba || !aligned(b.out_rgba, 16))
@@ -304,6 +317,21 @@ shw_status shw_batch_plan_create(shw_batch_plan **out, const shw_batch_item *ite
         if ((long long)b.vol.nx * b.vol.ny * b.vol.nz >= (1LL << 31)) return SHW_EUNSUPPORTED;
         if (b.vol.storage >= SHW_F32_PAIR) return SHW_EUNSUPPORTED;  // the line ratios' storages
         if (max_samples(&b.vol, p->step) > (1LL << 30)) return SHW_EINVAL;
+        n_own += (pack && b.vol.storage == SHW_F32) ? 1 : 0;
+    }
+    // brick edges to try: 16 needs its own kernel, which reads only the plan's bricks, so
+    // a plan that also holds bricks packed by the caller (edge 32) keeps 32
+    std::vector<int> edges;
+    if (n_own == 0) {
+        edges.push_back(0);
+    } else if (fixed == SHW_BATCH_BRICK_16) {
+        if (n_own != n) return SHW_EUNSUPPORTED;
+        edges.push_back(16);
+    } else if (fixed == SHW_BATCH_BRICK_32 || n_own != n) {
+        edges.push_back(32);
+    } else {
+        edges.push_back(16);
+        edges.push_back(32);
     }
     shw_batch_plan *pl = new (std::nothrow) shw_batch_plan();
     if (!pl) return SHW_ENOMEM;
@@ -321,7 +349,11 @@ shw_status shw_batch_plan_create(shw_batch_plan **out, const shw_batch_item *ite
     pl->sh.inv_range = 1.0f / (p->hi - p->lo);
     pl->sh.opacity_scale = p->opacity_scale;
     pl->sh.term_alpha = p->term_alpha;
+    pl->pack_storage = n_own ? (pack == SHW_BATCH_PACK_BF16 ? SHW_BF16_BRICK : SHW_F16_BRICK) : 0;
+    for (int e : edges)
+        for (const TileChoice &t : kTileChoices) pl->cands.push_back({t.tile, t.ctas_per_sm, e});
     pl->items.resize(n);
+    pl->src.assign(n, nullptr);
     std::vector<double> cost(n);
     for (int i = 0; i < n; ++i) {
         const shw_batch_item &b = items[i];
@@ -336,11 +368,15 @@ shw_status shw_batch_plan_create(shw_batch_plan **out, const shw_batch_item *ite
         d.mode = b.mode;
         d.nbx = ceil_div(b.vol.nx, kBrick);
         d.nby = ceil_div(b.vol.ny, kBrick);
+        d.brick = kBrick;
         d.nmax = (int)max_samples(&b.vol, p->step);
         d.cam = b.cam;
+        if (n_own && b.vol.storage == SHW_F32) pl->src[i] = static_cast<const float *>(b.vol.data);
         // expected work: pixels x mean chord (~ cube size) in samples
         cost[i] = (double)b.cam.width * b.cam.height * std::cbrt((double)b.vol.nx * b.vol.ny * b.vol.nz) / p->step;
     }
+    pl->any_f32 = false;
+    for (int i = 0; i < n; ++i) pl->any_f32 = pl->any_f32 || (items[i].vol.storage == SHW_F32 && !pl->src[i]);
     pl->order.resize(n);
     for (int i = 0; i < n; ++i) pl->order[i] = i;
     std::stable_sort(pl->order.begin(), pl->order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
@@ -357,12 +393,14 @@ shw_status shw_batch_plan_create(shw_batch_plan **out, const shw_batch_item *ite
     }
     cudaStream_t st = as_stream(stream);
     const std::string sig = signature(pl);
-    int choice = 1;  // {16, 4}
+    // untuned: {16, 4} with the last edge tried (32 unless 16 is fixed)
+    const int ncand = (int)pl->cands.size();
+    int choice = ncand - kNumTileChoices + kDefaultTileChoice;
     bool tuned = false;
     if (!(flags & SHW_BATCH_NO_TUNE)) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto itc = g_tune_cache.find(sig);
-        if (itc != g_tune_cache.end() && !(flags & SHW_BATCH_RETUNE)) {
+        if (itc != g_tune_cache.end() && itc->second >= 0 && itc->second < ncand && !(flags & SHW_BATCH_RETUNE)) {
             choice = itc->second;
         } else {
             int best = -1;
@@ -376,9 +414,27 @@ shw_status shw_batch_plan_create(shw_batch_plan **out, const shw_batch_item *ite
             g_tune_cache[sig] = best;
         }
     }
-    pl->ctas_per_sm = kCandidates[choice].ctas_per_sm;
-    shw_status s = build_work(pl, kCandidates[choice].tile);
+    const Candidate &cc = pl->cands[choice];
+    shw_status s = SHW_OK;
+    if (cc.brick) {
+        // the chosen edge's bricks (already there if the autotuner packed them); the other
+        // edge's copy, if any, is released
+        s = pack_edge(pl, cc.brick, st);
+        if (s == SHW_OK) {
+            use_edge(pl, cc.brick);
+            const int other = 1 - edge_slot(cc.brick);
+            if (pl->d_packed[other]) {
+                cudaFree(pl->d_packed[other]);
+                pl->d_packed[other] = nullptr;
+                pl->packed_bytes[other] = 0;
+            }
+        }
+    }
+    pl->ctas_per_sm = cc.ctas_per_sm;
+    if (s == SHW_OK) s = build_work(pl, cc.tile);
     if (s == SHW_OK) s = capture(pl);
+    // the bricks are written on `stream`; the graph may be replayed on any stream
+    if (s == SHW_OK && cc.brick && cudaStreamSynchronize(st) != cudaSuccess) s = SHW_ECUDA;
     if (s != SHW_OK) {
         plan_free(pl);
         return s;
@@ -390,10 +446,13 @@ shw_status shw_batch_plan_create(shw_batch_plan **out, const shw_batch_item *ite
     inf.ctas_per_sm = pl->ctas_per_sm;
     inf.grid = pl->grid;
     inf.tuned = tuned ? 1 : 0;
-    inf.n_candidates = kNumCandidates;
-    for (int c = 0; c < kNumCandidates && c < 8; ++c) {
-        inf.cand_tile[c] = kCandidates[c].tile;
-        inf.cand_ctas_per_sm[c] = kCandidates[c].ctas_per_sm;
+    inf.brick = cc.brick;
+    inf.packed_bytes = cc.brick ? (int64_t)pl->packed_bytes[edge_slot(cc.brick)] : 0;
+    inf.n_candidates = ncand;
+    for (int c = 0; c < ncand && c < 16; ++c) {
+        inf.cand_tile[c] = pl->cands[c].tile;
+        inf.cand_ctas_per_sm[c] = pl->cands[c].ctas_per_sm;
+        inf.cand_brick[c] = pl->cands[c].brick;
         if (!tuned) inf.tune_ms[c] = -1.0f;
     }
     *out = pl;
@@ -552,6 +611,7 @@ extern "C" shw_status shw_render_batch_noalloc(const shw_batch_item *items, int3
         d.mode = b.mode;
         d.nbx = ceil_div(b.vol.nx, kBrick);
         d.nby = ceil_div(b.vol.ny, kBrick);
+        d.brick = kBrick;
         d.nmax = (int)max_samples(&b.vol, p->step);
         d.cam = b.cam;
         d.tiles_x = ceil_div(b.cam.width, tile);
@@ -577,7 +637,9 @@ extern "C" shw_status shw_render_batch_noalloc(const shw_batch_item *items, int3
     if (cudaMemsetAsync(counter, 0, sizeof(int), st) != cudaSuccess) return SHW_ECUDA;
     if (cudaMemcpyAsync(scratch + items_off, host.data(), host.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return SHW_ECUDA;
-    pick_kernel(tile, p->interp)<<<sms * ctas_per_sm, tile * tile, 0, st>>>(
+    bool any_f32 = false;
+    for (int i = 0; i < n; ++i) any_f32 = any_f32 || items[i].vol.storage == SHW_F32;
+    batch_kernel_for(tile, p->interp, kBrick, any_f32)<<<sms * ctas_per_sm, tile * tile, 0, st>>>(
         reinterpret_cast<const BatchItemDev *>(scratch + items_off), reinterpret_cast<const int2 *>(scratch + work_off),
         counter, sh);
     return after_launch();

@@ -1,5 +1,6 @@
 // bricks.cu -- float32 cube -> 32^3 bricks of bfloat16 / binary16 with a 1-voxel
-// replicated apron (34^3 stored per brick), rounding to nearest even.
+// replicated apron (34^3 stored per brick), rounding to nearest even; batch plans that
+// pack their own bricks also take 16^3 bricks (18^3 stored).
 //
 // The apron holds copies of the neighbouring bricks' border voxels (clamped at
 // the cube's faces), so that all 8 corners of any interpolation cell are in one
@@ -25,21 +26,22 @@ __device__ __forceinline__ unsigned short round_store<__half>(float v)
 }
 
 // One thread per stored element; consecutive threads walk lx, so reads of a
-// brick row are contiguous in x and writes are contiguous.
-template <typename T>
+// brick row are contiguous in x and writes are contiguous.  E: the brick edge.
+template <typename T, int E>
 __global__ void __launch_bounds__(256) pack_kernel(const float *__restrict__ in, unsigned short *__restrict__ out,
                                                    int nx, int ny, int nz, int nbx, int nby, long long total)
 {
-    constexpr int S = kBrickStored;
+    constexpr int S = E + 2 * SHW_BRICK_APRON;
+    constexpr int kElems = S * S * S;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
-        const long long brick = i / kBrickElems;
-        const int e = (int)(i - brick * kBrickElems);
+        const long long brick = i / kElems;
+        const int e = (int)(i - brick * kElems);
         const int lz = e / (S * S), ly = (e / S) % S, lx = e % S;
         const int bx = (int)(brick % nbx), by = (int)((brick / nbx) % nby), bz = (int)(brick / ((long long)nbx * nby));
-        const int x = min(max(bx * kBrick + lx - 1, 0), nx - 1);
-        const int y = min(max(by * kBrick + ly - 1, 0), ny - 1);
-        const int z = min(max(bz * kBrick + lz - 1, 0), nz - 1);
+        const int x = min(max(bx * E + lx - 1, 0), nx - 1);
+        const int y = min(max(by * E + ly - 1, 0), ny - 1);
+        const int z = min(max(bz * E + lz - 1, 0), nz - 1);
         out[i] = round_store<T>(__ldg(in + ((size_t)z * ny + y) * nx + x));
     }
 }
@@ -94,6 +96,42 @@ __global__ void __launch_bounds__(256) convert_pair_kernel(const float2 *__restr
         const float2 v = __ldg(in + i);
         out[i] = (unsigned)round_store<T>(v.x) | ((unsigned)round_store<T>(v.y) << 16);
     }
+}
+
+// Bytes of one cube as 16-bit bricks of edge E (16 or 32); 0 for another edge.
+size_t bricked_bytes_edge(int nx, int ny, int nz, int edge)
+{
+    if (nx <= 0 || ny <= 0 || nz <= 0 || (edge != 16 && edge != 32)) return 0;
+    const size_t s = (size_t)edge + 2 * SHW_BRICK_APRON;
+    return (size_t)ceil_div(nx, edge) * ceil_div(ny, edge) * ceil_div(nz, edge) * s * s * s * 2;
+}
+
+// Enqueue the rounding of a float32 cube into 16-bit bricks of edge 16 or 32 (storage
+// SHW_BF16_BRICK or SHW_F16_BRICK; the layout of shw_pack_bricks with 32 replaced by the
+// edge).  out: device, 2-byte aligned, bricked_bytes_edge bytes.  The batch plans' own
+// bricks; arguments are checked by the caller.
+shw_status pack_bricks_edge(const float *in, int nx, int ny, int nz, int storage, int edge, void *out,
+                            cudaStream_t st)
+{
+    const long long total = (long long)(bricked_bytes_edge(nx, ny, nz, edge) / 2);
+    if (total <= 0 || (storage != SHW_BF16_BRICK && storage != SHW_F16_BRICK)) return SHW_EINVAL;
+    const int nbx = ceil_div(nx, edge), nby = ceil_div(ny, edge);
+    long long blocks = (total + 255) / 256;
+    if (blocks > 152LL * 64) blocks = 152LL * 64;  // grid-stride beyond 64 CTAs per SM
+    auto *o = static_cast<unsigned short *>(out);
+    const unsigned g = (unsigned)blocks;
+    if (storage == SHW_BF16_BRICK) {
+        if (edge == 16)
+            pack_kernel<__nv_bfloat16, 16><<<g, 256, 0, st>>>(in, o, nx, ny, nz, nbx, nby, total);
+        else
+            pack_kernel<__nv_bfloat16, 32><<<g, 256, 0, st>>>(in, o, nx, ny, nz, nbx, nby, total);
+    } else {
+        if (edge == 16)
+            pack_kernel<__half, 16><<<g, 256, 0, st>>>(in, o, nx, ny, nz, nbx, nby, total);
+        else
+            pack_kernel<__half, 32><<<g, 256, 0, st>>>(in, o, nx, ny, nz, nbx, nby, total);
+    }
+    return after_launch();
 }
 
 }  // namespace shw
@@ -164,12 +202,7 @@ shw_status shw_pack_bricks(const float *in, int32_t nx, int32_t ny, int32_t nz, 
             pack_pair_kernel<__half><<<(unsigned)blocks, 256, 0, st>>>(ip, op, nx, ny, nz, nbx, nby, total);
         return after_launch();
     }
-    auto *o = static_cast<unsigned short *>(out);
-    if (storage == SHW_BF16_BRICK)
-        pack_kernel<__nv_bfloat16><<<(unsigned)blocks, 256, 0, st>>>(in, o, nx, ny, nz, nbx, nby, total);
-    else
-        pack_kernel<__half><<<(unsigned)blocks, 256, 0, st>>>(in, o, nx, ny, nz, nbx, nby, total);
-    return after_launch();
+    return pack_bricks_edge(in, nx, ny, nz, storage, kBrick, out, st);
 }
 
 }  // extern "C"

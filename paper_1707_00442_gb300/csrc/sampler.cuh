@@ -143,27 +143,31 @@ __device__ __forceinline__ float to_f32<__half>(unsigned short raw)
     return __half2float(__ushort_as_half(raw));
 }
 
-// 32^3 bricks with a 1-voxel replicated apron, stored as 34^3 16-bit values
-// (layout documented with shw_pack_bricks).  The apron makes the 8 corners of
-// every cell live in one brick, at fixed offsets from the cell's base.
+// E^3 bricks (E = 32 for shw_pack_bricks; batch plans that pack their own bricks also
+// use 16) with a 1-voxel replicated apron, stored as (E+2)^3 16-bit values (layout
+// documented with shw_pack_bricks).  The apron makes the 8 corners of every cell live in
+// one brick, at fixed offsets from the cell's base.
 // Idx: int when the brick buffer holds < 2^31 elements (cheaper address arithmetic), else long long.
-template <typename T, typename Idx = long long>
+template <typename T, typename Idx = long long, int E = kBrick>
 struct SamplerBrick {
+    static_assert(E == 16 || E == 32, "brick edge 16 or 32");
     static constexpr bool kLinearF32 = false;
     static constexpr bool kPair = false;
     const unsigned short *__restrict__ v;
     int nx, ny, nz;
     int nbx, nby;
 
-    static constexpr int S = kBrickStored;
+    static constexpr int kShift = E == 16 ? 4 : 5;
+    static constexpr int S = E + 2 * SHW_BRICK_APRON;
+    static constexpr int kElems = S * S * S;
 
     __device__ __forceinline__ const unsigned short *cell_ptr(int ix, int iy, int iz) const
     {
-        // ix in [-1, n-1]: brick of max(ix, 0), local index ix - 32 b + 1 in [0, 32]
-        const int bx = max(ix, 0) >> 5, by = max(iy, 0) >> 5, bz = max(iz, 0) >> 5;
-        const int lx = ix - (bx << 5) + 1, ly = iy - (by << 5) + 1, lz = iz - (bz << 5) + 1;
+        // ix in [-1, n-1]: brick of max(ix, 0), local index ix - E b + 1 in [0, E]
+        const int bx = max(ix, 0) >> kShift, by = max(iy, 0) >> kShift, bz = max(iz, 0) >> kShift;
+        const int lx = ix - (bx << kShift) + 1, ly = iy - (by << kShift) + 1, lz = iz - (bz << kShift) + 1;
         const Idx brick = ((Idx)bz * nby + by) * nbx + bx;
-        return v + (brick * (Idx)kBrickElems + (lz * S + ly) * S + lx);
+        return v + (brick * (Idx)kElems + (lz * S + ly) * S + lx);
     }
 
     template <bool CLAMP = true>
@@ -177,9 +181,10 @@ struct SamplerBrick {
         } else {
             check_voxel(x, y, z, nx, ny, nz);
         }
-        const int bx = x >> 5, by = y >> 5, bz = z >> 5;
+        const int bx = x >> kShift, by = y >> kShift, bz = z >> kShift;
         const Idx brick = ((Idx)bz * nby + by) * nbx + bx;
-        const unsigned short *p = v + (brick * (Idx)kBrickElems + (((z & 31) + 1) * S + ((y & 31) + 1)) * S + (x & 31) + 1);
+        const unsigned short *p =
+            v + (brick * (Idx)kElems + (((z & (E - 1)) + 1) * S + ((y & (E - 1)) + 1)) * S + (x & (E - 1)) + 1);
         return to_f32<T>(__ldg(p));
     }
 

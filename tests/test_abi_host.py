@@ -48,9 +48,9 @@ def test_struct_layout(L):
     assert L.shw_struct_size(1) == C.sizeof(_lib.Camera) == 68
     assert L.shw_struct_size(2) == C.sizeof(_lib.RenderParams) == 112
     assert L.shw_struct_size(3) == C.sizeof(_lib.BatchItem) == 112
-    assert L.shw_struct_size(4) == C.sizeof(_lib.BatchInfo)
+    assert L.shw_struct_size(4) == C.sizeof(_lib.BatchInfo) == 296
     assert L.shw_struct_size(9) == 0
-    assert L.shw_abi_version() == 4
+    assert L.shw_abi_version() == 5
 
 
 def test_status_strings(L):
@@ -240,6 +240,16 @@ def test_batch_plan_rejects_invalid_arguments_on_host(L):
     items[1].mode = 2
     items[1].out_rgba = 0x4004
     assert L.shw_batch_plan_create(b(h), items, 2, b(p), 0, None) == 1
+    items[1].out_rgba = 0x4000
+    # the plan's own bricks: one pack storage, at most one fixed edge, an edge only with packing,
+    # and edge 16 only when the plan packs every item (the caller's bricks are 32^3)
+    PB, PF, B16, B32 = 4, 8, 16, 32
+    assert L.shw_batch_plan_create(b(h), items, 2, b(p), PB | PF, None) == 1
+    assert L.shw_batch_plan_create(b(h), items, 2, b(p), PB | B16 | B32, None) == 1
+    assert L.shw_batch_plan_create(b(h), items, 2, b(p), B16, None) == 1
+    assert L.shw_batch_plan_create(b(h), items, 2, b(p), B32, None) == 1
+    items[1].vol = _vol(storage=1)
+    assert L.shw_batch_plan_create(b(h), items, 2, b(p), PF | B16, None) == 2
     assert h.value is None
     assert L.shw_render_batch(None, None) == 1
     assert L.shw_batch_plan_destroy(None) == 1

@@ -52,7 +52,7 @@ def test_batch_equals_single_renders_and_oracle(m):
     m.sync_status()
     info = plan.info
     assert info["n_items"] == len(items) and info["tuned"]
-    assert all(t > 0 for (_, _, t) in info["candidates"])
+    assert all(t > 0 for (*_, t) in info["candidates"])
     for (vol, cam, mode), img, (cube, _, _, st) in zip(dev, outs, items):
         single = m.render(vol, cam, mode, lut=lut, opacity_scale=0.05)["rgba"].cpu().numpy()
         assert np.array_equal(img, single), (mode, st)
@@ -145,4 +145,111 @@ def test_render_items_equals_plan(m):
     m.sync_status()
     for x, y in zip(a, b):
         assert torch.equal(x, y)
+    plan.close()
+
+
+ROUND = {"bf16": oracle.round_bf16, "f16": oracle.round_f16}
+
+
+def _own_brick_bytes(dims, edge):
+    """Bytes of one cube as 16-bit bricks of this edge (layout of shw_pack_bricks with 32 replaced
+    by the edge and 34 by edge + 2), rounded up to the plan's 256-byte item alignment."""
+    nb = np.prod([-(-int(n) // edge) for n in dims])
+    return -(-int(nb) * (edge + 2) ** 3 * 2 // 256) * 256
+
+
+@pytest.mark.parametrize("pack", ["bf16", "f16"])
+@pytest.mark.parametrize("brick", [16, 32])
+def test_batch_packs_its_own_bricks(m, pack, brick):
+    """A plan that rounds its float32 items into 16-bit bricks of its own, at a fixed edge: every
+    image equals shw_render of shw_pack_bricks of the item (32^3 bricks; the values and the
+    arithmetic do not depend on the edge), and matches the oracle run on the rounded cube."""
+    items = _batch(n=14, lo=1, hi=70, storage_cycle=("f32",), modes=("mip", "composite", "avg", "spectral"))
+    items[0] = (scene.batch_subcube(90, (1, 1, 1)), scene.orbit_camera((1, 1, 1), 20, 10, 24, 16), "mip", "f32")
+    items[1] = (scene.batch_subcube(91, (16, 17, 33)), scene.orbit_camera((16, 17, 33), 70, -30, 40, 36), "avg", "f32")
+    lut = to_dev(scene.linear_lut())
+    dev = _dev_items(m, items)
+    for interp in ("trilinear", "nearest"):
+        plan = m.BatchPlan(dev, lut=lut, opacity_scale=0.05, interp=interp, tune=False, pack=pack, brick=brick)
+        outs = [o.clone() for o in plan.render()]
+        m.sync_status()
+        info = plan.info
+        assert info["brick"] == brick and not info["tuned"]
+        want = sum(_own_brick_bytes(cube.shape[::-1], brick) for cube, *_ in items)
+        assert info["packed_bytes"] == want
+        assert [c[2] for c in info["candidates"]] == [brick] * 6
+        for (vol, cam, mode), img in zip(dev, outs):
+            single = m.render(m.pack_bricks(vol, pack), cam, mode, lut=lut, opacity_scale=0.05, interp=interp)["rgba"]
+            assert torch.equal(img, single), (mode, interp)
+        plan.close()
+    for (cube, cam, mode, _), img in list(zip(items, outs))[:6]:
+        o = oracle.render(ROUND[pack](cube), cam, mode, lut=scene.linear_lut(), opacity_scale=0.05, interp="nearest",
+                          eps_pos=1e-6, eps_val=1e-4)
+        ok = o["fragile"] == 0
+        err = np.abs(img.cpu().numpy() - o["rgba"])[ok].max()
+        assert err <= 1e-5, (mode, err)
+
+
+def test_batch_tunes_the_brick_edge(m):
+    """Packing plans time every tile / CTAs-per-SM choice at both brick edges, keep the fastest
+    and cache it; the images do not depend on the choice."""
+    items = _batch(n=16, lo=16, hi=96, storage_cycle=("f32",), modes=("mip", "composite"))
+    lut = to_dev(scene.linear_lut())
+    dev = _dev_items(m, items)
+    p1 = m.BatchPlan(dev, lut=lut, opacity_scale=0.05, pack="bf16", retune=True)
+    a = [o.clone() for o in p1.render()]
+    m.sync_status()
+    info = p1.info
+    assert info["tuned"] and len(info["candidates"]) == 12
+    assert sorted({c[2] for c in info["candidates"]}) == [16, 32]
+    assert all(t > 0 for (*_, t) in info["candidates"])
+    best = min(info["candidates"], key=lambda c: c[3])
+    assert (info["tile"], info["ctas_per_sm"], info["brick"]) == best[:3]
+    for (vol, cam, mode), img in zip(dev, a):
+        assert torch.equal(img, m.render(m.pack_bricks(vol, "bf16"), cam, mode, lut=lut, opacity_scale=0.05)["rgba"])
+    p2 = m.BatchPlan(dev, lut=lut, opacity_scale=0.05, pack="bf16")
+    assert not p2.info["tuned"] and p2.info["brick"] == info["brick"]
+    b = p2.render()
+    m.sync_status()
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    for p in (p1, p2):
+        p.close()
+
+
+def test_batch_pack_beside_callers_bricks(m):
+    """Items the caller packed (32^3) beside float32 items the plan packs: the edge stays 32
+    (16 is refused), and every image still equals its single render."""
+    items = _batch(n=9, storage_cycle=("f32", "bf16", "f16"), modes=("mip", "composite", "avg"))
+    lut = to_dev(scene.linear_lut())
+    dev = _dev_items(m, items)
+    plan = m.BatchPlan(dev, lut=lut, opacity_scale=0.05, pack="f16", retune=True)
+    outs = plan.render()
+    m.sync_status()
+    info = plan.info
+    assert info["brick"] == 32 and [c[2] for c in info["candidates"]] == [32] * 6
+    for (vol, cam, mode), img, (_, _, _, st) in zip(dev, outs, items):
+        v = m.pack_bricks(vol, "f16") if st == "f32" else vol
+        assert torch.equal(img, m.render(v, cam, mode, lut=lut, opacity_scale=0.05)["rgba"]), (mode, st)
+    plan.close()
+    with pytest.raises(m.ShwError) as e:
+        m.BatchPlan(dev, lut=lut, pack="f16", brick=16, tune=False)
+    assert e.value.status == 2  # SHW_EUNSUPPORTED
+    with pytest.raises(m.ShwError) as e:
+        m.BatchPlan(dev, lut=lut, brick=16, tune=False)  # an edge without a pack storage
+    assert e.value.status == 1  # SHW_EINVAL
+
+
+def test_batch_of_bricks_only(m):
+    """A plan whose items are all the caller's bricks takes the kernel without the float32 path;
+    the images are unchanged."""
+    items = _batch(n=8, storage_cycle=("bf16", "f16"), modes=("mip", "composite", "spectral", "avg"))
+    lut = to_dev(scene.linear_lut())
+    dev = _dev_items(m, items)
+    plan = m.BatchPlan(dev, lut=lut, opacity_scale=0.05, tune=False)
+    outs = [o.clone() for o in plan.render()]
+    m.sync_status()
+    assert plan.info["brick"] == 0
+    for (vol, cam, mode), img in zip(dev, outs):
+        assert torch.equal(img, m.render(vol, cam, mode, lut=lut, opacity_scale=0.05)["rgba"]), mode
     plan.close()

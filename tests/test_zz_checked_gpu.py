@@ -6,7 +6,7 @@ the staged marcher's shared-memory reads, the plane sweep's offsets and planes a
 smoothing's output planes; a violating index is clamped into its array and recorded, and
 shw_sync_status reports SHW_EBOUNDS.  Here the test builds that library and runs every
 kernel family through it -- views of every class, both marchers, each storage, the sweep,
-both smoothings, a batch plan, the adjoint -- requiring no violation and outputs
+both smoothings, batch plans (one on its own 16^3 bricks), the adjoint -- requiring no violation and outputs
 bit-identical to the normal library's (the checks change no result)."""
 import numpy as np
 import pytest
@@ -158,6 +158,18 @@ def test_checked_batch_and_adjoint(libs):
         finally:
             plan.close()
     _both(libs, batch)
+
+    own = [(to_dev(scene.batch_subcube(i, d)), scene.orbit_camera(d, 25 * i, -20, 44, 36), ("avg", "spectral")[i % 2])
+           for i, d in enumerate(((17, 40, 33), (48, 16, 21), (1, 5, 9)))]
+
+    def own_bricks():
+        # the plan's own 16^3 bricks (the kernel without the float32 path)
+        plan = m.BatchPlan(own, lut=lut, pack="bf16", brick=16, tune=False)
+        try:
+            return [o.clone() for o in plan.render()]
+        finally:
+            plan.close()
+    _both(libs, own_bricks)
 
     dims = (40, 36, 44)
     ct = to_dev(scene.diff_cube(dims=dims, n_sources=2))

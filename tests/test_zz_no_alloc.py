@@ -85,6 +85,23 @@ def test_noalloc_matches_batch_plan_on_two_calls():
             assert torch.equal(o, r), (call, i)
 
 
+def test_noalloc_bricks_only_matches_single_renders():
+    """Items that are all bricks take the kernel without the float32 path: the images are those
+    of single renders of the same bricks."""
+    m = shw()
+    from paper_1707_00442_gb300 import _lib
+    lut = to_dev(scene.linear_lut())
+    items, _ = _items(m, n=8, config_id=45)
+    items = [(v if not isinstance(v, torch.Tensor) else m.pack_bricks(v, "f16"), c, md) for v, c, md in items]
+    outs = [torch.full((int(c.height), int(c.width), 4), -1.0, device="cuda") for _, c, _ in items]
+    arr = _table(items, outs)
+    stream = torch.cuda.current_stream().cuda_stream
+    assert _call(arr, len(items), lut, opacity_scale=0.05) == _lib.SHW_OK
+    assert _lib.lib().shw_sync_status(stream) == _lib.SHW_OK
+    for i, ((vol, cam, mode), o) in enumerate(zip(items, outs)):
+        assert torch.equal(o, m.render(vol, cam, mode, lut=lut, opacity_scale=0.05)["rgba"]), i
+
+
 def test_noalloc_smaller_second_call_uses_only_its_own_table():
     """A large call, then a smaller call with other cubes: the second must not consume the
     first call's (longer) work list or item table left in the shared scratch."""
