@@ -348,10 +348,10 @@ uint32_t shw_set_debug_flags(uint32_t flags);
 /* ---- batched rendering of many sub-cubes ----------------------------------- */
 
 /* Survey pipelines cut a sub-cube around each of many detected sources (Section 1).
- * A plan renders all of them with ONE persistent kernel launch captured in a CUDA
- * graph: every (item, image tile) is a work item, CTAs pop work items from a device
- * counter, tiles of the largest items first.  Each image is the same as shw_render
- * of that item with the shared parameters.  */
+ * A plan renders all of them with ONE graph launch: a persistent kernel per kind of
+ * item (float32 cubes, bricks), captured in a CUDA graph; every (item, image tile) is a
+ * work item, CTAs pop work items from a device counter, tiles of the largest items
+ * first.  Each image is the same as shw_render of that item with the shared parameters. */
 
 typedef struct shw_batch_plan shw_batch_plan; /* opaque */
 
@@ -376,7 +376,7 @@ typedef struct {
 typedef struct {
     int32_t n_items, n_work;     /* items, work items (tiles) */
     int32_t tile, ctas_per_sm;   /* the chosen tile edge (pixels) and persistent CTAs per SM */
-    int32_t grid, tuned;         /* CTAs launched; 1 if the autotuner ran for this plan */
+    int32_t grid, tuned;         /* CTAs of each kernel; 1 if the autotuner ran for this plan */
     int32_t brick;               /* edge of the plan's own bricks (16 or 32); 0 when it packs none */
     int32_t n_candidates;        /* configurations the autotuner times: tile x CTAs per SM, and
                                     x brick edge when the plan packs bricks and the edge is free */
@@ -387,8 +387,10 @@ typedef struct {
 
 /* Build a plan for n items sharing the parameters p (p->mode is ignored: each item
  * has its own; interp, step, lo, hi, lut, opacity_scale, term_alpha are shared).
- * Allocates device memory for the item table, the work list and the counter, and
- * captures the launch into a CUDA graph.  With SHW_BATCH_PACK_BF16 or _F16 it also
+ * Allocates device memory for the item table, the work list and the counters, and
+ * captures the launch into a CUDA graph: one persistent kernel for the float32 items and
+ * one for the brick items, one after the other (a kernel for both would hold the
+ * registers of both paths).  With SHW_BATCH_PACK_BF16 or _F16 it also
  * allocates the 16-bit bricks of its float32 items (the layout of shw_pack_bricks with
  * 32 replaced by the edge E and 34 by E + 2) and fills them on `stream`; the float32
  * cubes are not read after that.  Unless SHW_BATCH_NO_TUNE, the first plan of a batch
@@ -426,7 +428,7 @@ shw_status shw_batch_plan_destroy(shw_batch_plan *plan);
  * the GPU through its own pool or budget (for example a plugin inside a
  * visualisation application), or an interactive loop that must never stall in an
  * allocator.  It renders the same images as a batch plan (16 x 16 tiles, 4 CTAs per
- * SM, no autotuning) but keeps the item table, the work list and the work counter
+ * SM, no autotuning) but keeps the item table, the work list and the work counters
  * in a fixed device array that is part of the library: every GPU that loads
  * libshw.so holds SHW_NOALLOC_SCRATCH_BYTES of it until the process exits.  The
  * call makes no cudaMalloc/cudaFree or other allocating call; the caller passes the
@@ -441,7 +443,7 @@ shw_status shw_batch_plan_destroy(shw_batch_plan *plan);
  *    the work already enqueued on `stream` has finished and the table has been handed
  *    to the copy engine: the host waits for the stream, though no allocator is touched.
  *  - Every call reuses the one array per device and overwrites the previous call's
- *    contents (the counter is cleared on `stream` first).  Calls whose work can
+ *    contents (the counters are cleared on `stream` first).  Calls whose work can
  *    overlap on the GPU -- on different streams without ordering -- race with each
  *    other; calls on one stream are ordered.
  *  - Other errors as for shw_batch_plan_create. */

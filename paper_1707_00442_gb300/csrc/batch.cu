@@ -8,7 +8,10 @@
 // ones fill the tail); a persistent grid of CTAs pops work items from one atomic
 // counter -- no CTA ever waits on another -- and renders each tile with the same
 // per-ray code as shw_render.  The counter reset and the launch are captured once
-// into a CUDA graph, so a batch render is a single graph launch.  An autotuner
+// into a CUDA graph, so a batch render is a single graph launch.  Float32 cubes and
+// bricks are rendered by two kernels (one work list each, run one after the other in
+// the same graph): a kernel for both kinds would hold the registers of both paths.  An
+// autotuner
 // times the candidate tile shapes and CTAs-per-SM -- and, for plans that round their
 // float32 items into 16-bit bricks of their own, the brick edge (16 or 32 voxels) -- at
 // plan creation and caches the winner per batch signature.
@@ -34,14 +37,42 @@ size_t bricked_bytes_edge(int nx, int ny, int nz, int edge);
 shw_status pack_bricks_edge(const float *in, int nx, int ny, int nz, int storage, int edge, void *out,
                             cudaStream_t st);
 
-BatchKernel batch_kernel_for(int tile, int interp, int brick, bool f32)
+BatchKernel batch_kernel_for(int tile, int interp, int kind)
 {
-    if (brick == 16) return batch_kernel_b16(tile, interp);
-    if (!f32) return batch_kernel_b32(tile, interp);
-    if (tile == 8)
-        return interp == SHW_NEAREST ? batch_kernel<8, SHW_NEAREST, 32, true> : batch_kernel<8, SHW_TRILINEAR, 32, true>;
-    return interp == SHW_NEAREST ? batch_kernel<16, SHW_NEAREST, 32, true>
-                                 : batch_kernel<16, SHW_TRILINEAR, 32, true>;
+    if (kind == 16) return batch_kernel_b16(tile, interp);
+    if (kind == 32) return batch_kernel_b32(tile, interp);
+    if (tile == 8) return interp == SHW_NEAREST ? batch_kernel<8, SHW_NEAREST, 0> : batch_kernel<8, SHW_TRILINEAR, 0>;
+    return interp == SHW_NEAREST ? batch_kernel<16, SHW_NEAREST, 0> : batch_kernel<16, SHW_TRILINEAR, 0>;
+}
+
+// One kernel's share of a batch: the items of one kind (0: float32, else the brick
+// edge), `n` work items from `off` in the work list, counter `counter`.
+struct WorkGroup {
+    int kind, off, n, counter;
+};
+
+// Work items (item, tile) of every image, the largest items' tiles first (LPT), split by
+// kind: float32 items first, then bricks.  Fills `work` and `groups` (empty kinds left out);
+// false when there are 2^31 work items or more.
+static bool group_work(const BatchItemDev *items, const std::vector<int> &order, int tile, int brick_kind,
+                       std::vector<int2> &work, std::vector<WorkGroup> &groups)
+{
+    std::vector<int2> by_kind[2];
+    for (int i : order) {
+        const BatchItemDev &it = items[i];
+        const int nt = ceil_div(it.cam.width, tile) * ceil_div(it.cam.height, tile);
+        std::vector<int2> &w = by_kind[it.storage == SHW_F32 ? 0 : 1];
+        for (int t = 0; t < nt; ++t) w.push_back(make_int2(i, t));
+    }
+    work.clear();
+    groups.clear();
+    if (by_kind[0].size() + by_kind[1].size() > (size_t)0x7fffffff) return false;
+    for (int k = 0; k < 2; ++k) {
+        if (by_kind[k].empty()) continue;
+        groups.push_back({k == 0 ? 0 : brick_kind, (int)work.size(), (int)by_kind[k].size(), (int)groups.size()});
+        work.insert(work.end(), by_kind[k].begin(), by_kind[k].end());
+    }
+    return true;
 }
 
 struct TileChoice {
@@ -75,9 +106,9 @@ struct shw_batch_plan {
     std::vector<BatchItemDev> items;
     std::vector<int> order;  // items sorted by estimated cost, descending
     std::vector<Candidate> cands;
+    std::vector<WorkGroup> groups;  // one kernel per kind of item, in launch order
     // bricks the plan packs itself (SHW_BATCH_PACK_*): one buffer per edge (16, 32)
     int brick = 0, pack_storage = 0;
-    bool any_f32 = true;             // an item left as float32: the kernel with the float32 path
     std::vector<const float *> src;  // each packed item's float32 cube, else nullptr
     void *d_packed[2] = {nullptr, nullptr};
     size_t packed_bytes[2] = {0, 0};
@@ -108,16 +139,11 @@ static bool fault(uint32_t flag) { return debug(flag); }
 // (re)build the work list for a tile size: tiles of the biggest items first
 static shw_status build_work(shw_batch_plan *pl, int tile)
 {
+    for (BatchItemDev &it : pl->items) it.tiles_x = ceil_div(it.cam.width, tile);
     std::vector<int2> work;
-    for (int i : pl->order) {
-        BatchItemDev &it = pl->items[i];
-        it.tiles_x = ceil_div(it.cam.width, tile);
-        const int ty = ceil_div(it.cam.height, tile);
-        for (int t = 0; t < it.tiles_x * ty; ++t) work.push_back(make_int2(i, t));
-    }
-    if (work.size() > (size_t)0x7fffffff) return SHW_EUNSUPPORTED;
+    if (!group_work(pl->items.data(), pl->order, tile, pl->brick == 16 ? 16 : 32, work, pl->groups))
+        return SHW_EUNSUPPORTED;
     pl->nwork = (int)work.size();
-    pl->sh.nwork = pl->nwork;
     if (pl->d_work) cudaFree(pl->d_work);
     pl->d_work = nullptr;
     if (fault(SHW_DEBUG_FAULT_ALLOC) || cudaMalloc(&pl->d_work, work.size() * sizeof(int2)) != cudaSuccess) {
@@ -182,17 +208,27 @@ static void use_edge(shw_batch_plan *pl, int edge)
     pl->brick = edge;
 }
 
-static BatchKernel plan_kernel(const shw_batch_plan *pl)
+// Enqueue one render of the batch on `st`: clear the counters, then one persistent kernel
+// per kind of item.  note: count the kernels as launched (not while capturing).
+static shw_status enqueue_groups(const std::vector<WorkGroup> &groups, const BatchItemDev *d_items,
+                                 const int2 *d_work, int *d_counter, BatchShared sh, int tile, int interp, int grid,
+                                 cudaStream_t st, bool note)
 {
-    return batch_kernel_for(pl->tile, pl->interp, pl->brick == 16 ? 16 : 32, pl->any_f32);
+    if (cudaMemsetAsync(d_counter, 0, 2 * sizeof(int), st) != cudaSuccess) return SHW_ECUDA;
+    for (const WorkGroup &g : groups) {
+        sh.nwork = g.n;
+        batch_kernel_for(tile, interp, g.kind)<<<grid, tile * tile, 0, st>>>(d_items, d_work + g.off,
+                                                                             d_counter + g.counter, sh);
+        if (note) note_launch();
+        if (cudaGetLastError() != cudaSuccess) return SHW_ECUDA;
+    }
+    return SHW_OK;
 }
 
 static shw_status launch_direct(shw_batch_plan *pl, int ctas_per_sm, cudaStream_t st)
 {
-    if (cudaMemsetAsync(pl->d_counter, 0, sizeof(int), st) != cudaSuccess) return SHW_ECUDA;
-    const int grid = pl->sms * ctas_per_sm;
-    plan_kernel(pl)<<<grid, pl->tile * pl->tile, 0, st>>>(pl->d_items, pl->d_work, pl->d_counter, pl->sh);
-    return after_launch();
+    return enqueue_groups(pl->groups, pl->d_items, pl->d_work, pl->d_counter, pl->sh, pl->tile, pl->interp,
+                          pl->sms * ctas_per_sm, st, true);
 }
 
 static shw_status capture(shw_batch_plan *pl)
@@ -203,9 +239,10 @@ static shw_status capture(shw_batch_plan *pl)
     pl->graph = nullptr;
     if (fault(SHW_DEBUG_FAULT_GRAPH)) return SHW_ECUDA;
     if (cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SHW_ECUDA;
-    cudaMemsetAsync(pl->d_counter, 0, sizeof(int), pl->cap);
     pl->grid = pl->sms * pl->ctas_per_sm;
-    plan_kernel(pl)<<<pl->grid, pl->tile * pl->tile, 0, pl->cap>>>(pl->d_items, pl->d_work, pl->d_counter, pl->sh);
+    // (an error here is reported by the end of the capture)
+    enqueue_groups(pl->groups, pl->d_items, pl->d_work, pl->d_counter, pl->sh, pl->tile, pl->interp, pl->grid,
+                   pl->cap, false);
     cudaError_t e = cudaStreamEndCapture(pl->cap, &pl->graph);
     if (e != cudaSuccess || !pl->graph) {
         cudaGetLastError();
@@ -375,14 +412,12 @@ shw_status shw_batch_plan_create(shw_batch_plan **out, const shw_batch_item *ite
         // expected work: pixels x mean chord (~ cube size) in samples
         cost[i] = (double)b.cam.width * b.cam.height * std::cbrt((double)b.vol.nx * b.vol.ny * b.vol.nz) / p->step;
     }
-    pl->any_f32 = false;
-    for (int i = 0; i < n; ++i) pl->any_f32 = pl->any_f32 || (items[i].vol.storage == SHW_F32 && !pl->src[i]);
     pl->order.resize(n);
     for (int i = 0; i < n; ++i) pl->order[i] = i;
     std::stable_sort(pl->order.begin(), pl->order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
 
     if (fault(SHW_DEBUG_FAULT_ALLOC) || cudaMalloc(&pl->d_items, sizeof(BatchItemDev) * n) != cudaSuccess ||
-        cudaMalloc(&pl->d_counter, sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&pl->d_counter, 2 * sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
         plan_free(pl);
         return SHW_ENOMEM;
@@ -466,7 +501,7 @@ shw_status shw_render_batch(shw_batch_plan *plan, void *stream)
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->device) return SHW_EINVAL;
     if (cudaGraphLaunch(plan->exec, as_stream(stream)) != cudaSuccess) return SHW_ECUDA;
-    note_launch();
+    for (size_t g = 0; g < plan->groups.size(); ++g) note_launch();  // one kernel per kind of item
     return SHW_OK;
 }
 
@@ -520,7 +555,7 @@ namespace shw {
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SHW_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kNoallocMaxDevices = 64;
-constexpr size_t kNoallocCounterBytes = 256;  // the work counter lives in the first aligned slot
+constexpr size_t kNoallocCounterBytes = 256;  // the two work counters live in the first aligned slot
 static std::mutex g_noalloc_mu;
 static unsigned char *g_noalloc_ptr[kNoallocMaxDevices] = {};
 static int g_noalloc_sms[kNoallocMaxDevices] = {};
@@ -617,11 +652,12 @@ extern "C" shw_status shw_render_batch_noalloc(const shw_batch_item *items, int3
         d.tiles_x = ceil_div(b.cam.width, tile);
         std::memcpy(hitems + i, &d, sizeof d);
     }
-    long long w = 0;
-    for (int i : order) {
-        const int nt = ceil_div(items[i].cam.width, tile) * ceil_div(items[i].cam.height, tile);
-        for (int t = 0; t < nt; ++t) hwork[w++] = make_int2(i, t);
-    }
+    // one work list per kind of item (float32, bricks), each largest items first
+    std::vector<int2> work;
+    std::vector<WorkGroup> groups;
+    if (!group_work(hitems, order, tile, kBrick, work, groups) || (long long)work.size() != nwork)
+        return SHW_EUNSUPPORTED;
+    std::memcpy(hwork, work.data(), work.size() * sizeof(int2));
     BatchShared sh{};
     sh.lut = reinterpret_cast<const float4 *>(p->lut);
     sh.step = p->step;
@@ -629,19 +665,14 @@ extern "C" shw_status shw_render_batch_noalloc(const shw_batch_item *items, int3
     sh.inv_range = 1.0f / (p->hi - p->lo);
     sh.opacity_scale = p->opacity_scale;
     sh.term_alpha = p->term_alpha;
-    sh.nwork = (int)nwork;
 
     cudaStream_t st = as_stream(stream);
-    int *counter = reinterpret_cast<int *>(scratch);
-    // the array keeps the previous call's contents: the counter must start at zero
-    if (cudaMemsetAsync(counter, 0, sizeof(int), st) != cudaSuccess) return SHW_ECUDA;
+    // the array keeps the previous call's contents: the two counters (the first slot) are
+    // cleared on the stream by enqueue_groups, after the table's copy is enqueued
     if (cudaMemcpyAsync(scratch + items_off, host.data(), host.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return SHW_ECUDA;
-    bool any_f32 = false;
-    for (int i = 0; i < n; ++i) any_f32 = any_f32 || items[i].vol.storage == SHW_F32;
-    batch_kernel_for(tile, p->interp, kBrick, any_f32)<<<sms * ctas_per_sm, tile * tile, 0, st>>>(
-        reinterpret_cast<const BatchItemDev *>(scratch + items_off), reinterpret_cast<const int2 *>(scratch + work_off),
-        counter, sh);
-    return after_launch();
+    return enqueue_groups(groups, reinterpret_cast<const BatchItemDev *>(scratch + items_off),
+                          reinterpret_cast<const int2 *>(scratch + work_off), reinterpret_cast<int *>(scratch), sh,
+                          tile, p->interp, sms * ctas_per_sm, st, true);
 }
 

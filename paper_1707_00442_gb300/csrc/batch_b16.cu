@@ -1,5 +1,5 @@
-// batch_b16.cu -- the batch kernel for plans whose items are all 16^3 bricks the plan
-// packed itself (a translation unit of its own so that it compiles beside batch.cu).
+// batch_b16.cu -- the batch kernel for items that are 16^3 bricks a plan packed itself;
+// a translation unit of its own so that it compiles beside batch.cu.
 #include "batch_kernel.cuh"
 
 namespace shw {
@@ -7,8 +7,8 @@ namespace shw {
 BatchKernel batch_kernel_b16(int tile, int interp)
 {
     if (tile == 8)
-        return interp == SHW_NEAREST ? batch_kernel<8, SHW_NEAREST, 16, false> : batch_kernel<8, SHW_TRILINEAR, 16, false>;
-    return interp == SHW_NEAREST ? batch_kernel<16, SHW_NEAREST, 16, false> : batch_kernel<16, SHW_TRILINEAR, 16, false>;
+        return interp == SHW_NEAREST ? batch_kernel<8, SHW_NEAREST, 16> : batch_kernel<8, SHW_TRILINEAR, 16>;
+    return interp == SHW_NEAREST ? batch_kernel<16, SHW_NEAREST, 16> : batch_kernel<16, SHW_TRILINEAR, 16>;
 }
 
 }  // namespace shw

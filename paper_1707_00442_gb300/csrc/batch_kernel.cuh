@@ -1,10 +1,11 @@
-// batch_kernel.cuh -- the persistent kernel of batch plans: CTAs pop (item, image tile)
-// work items from one atomic counter and render each tile with the per-ray code of
-// shw_render.  E is the edge of the brick items the kernel reads (32: shw_pack_bricks;
-// 16: only bricks that a plan packed itself); F32: whether it also reads float32 items.
-// The float32 path holds more registers (194 against 128 for bricks alone, trilinear),
-// so a plan whose items are all bricks takes a kernel without it.  Instances: batch.cu
-// (32, with float32), batch_b32.cu and batch_b16.cu (bricks only), compiled in parallel.
+// batch_kernel.cuh -- the persistent kernels of batch plans: CTAs pop (item, image tile)
+// work items from an atomic counter and render each tile with the per-ray code of
+// shw_render.  One kernel reads one kind of item: K = 0 float32 cubes, K = 32 or 16
+// bfloat16 / binary16 bricks of that edge (32: shw_pack_bricks; 16: only bricks that a
+// plan packed itself).  A kernel that read both float32 cubes and bricks would hold the
+// registers of both paths (191-194 against 124-128 for either alone, trilinear), so a
+// batch with both runs one kernel per kind, one after the other, each over its own work
+// list.  Instances: batch.cu (K = 0), batch_b32.cu and batch_b16.cu, compiled in parallel.
 #pragma once
 
 #include "render_impl.cuh"
@@ -36,12 +37,11 @@ __device__ __forceinline__ void batch_pixel(const S &s, const BatchItemDev &it, 
     }
 }
 
-template <int TILE, int INTERP, int E, bool F32>
+template <int TILE, int INTERP, int K>
 __global__ void __launch_bounds__(TILE *TILE) batch_kernel(const BatchItemDev *__restrict__ items,
                                                            const int2 *__restrict__ work, int *counter, BatchShared sh)
 {
-    static_assert(E == 16 || E == 32, "brick edge 16 or 32");
-    static_assert(E == 32 || !F32, "float32 items only beside 32^3 bricks");
+    static_assert(K == 0 || K == 16 || K == 32, "float32 items, or bricks of edge 16 or 32");
     __shared__ float4 lut_s[kLut];
     __shared__ int w_s;
     for (int i = threadIdx.x; i < kLut; i += blockDim.x) lut_s[i] = sh.lut[i];
@@ -73,32 +73,29 @@ __global__ void __launch_bounds__(TILE *TILE) batch_kernel(const BatchItemDev *_
         a.nx = it.nx;
         a.ny = it.ny;
         a.nz = it.nz;
-        if constexpr (F32) {
-            if (it.storage == SHW_F32) {
-                const SamplerF32<int> s{static_cast<const float *>(it.data), it.nx, it.ny, it.nz, it.nx,
-                                        it.nx * it.ny};
-                batch_pixel<INTERP>(s, it, a, lut_s, px, py);
-                continue;
-            }
-        }
-        if (it.storage == SHW_BF16_BRICK) {
-            const SamplerBrick<__nv_bfloat16, long long, E> s{static_cast<const unsigned short *>(it.data), it.nx,
-                                                              it.ny, it.nz, it.nbx, it.nby};
+        if constexpr (K == 0) {
+            const SamplerF32<int> s{static_cast<const float *>(it.data), it.nx, it.ny, it.nz, it.nx, it.nx * it.ny};
             batch_pixel<INTERP>(s, it, a, lut_s, px, py);
         } else {
-            const SamplerBrick<__half, long long, E> s{static_cast<const unsigned short *>(it.data), it.nx, it.ny,
-                                                       it.nz, it.nbx, it.nby};
-            batch_pixel<INTERP>(s, it, a, lut_s, px, py);
+            if (it.storage == SHW_BF16_BRICK) {
+                const SamplerBrick<__nv_bfloat16, long long, K> s{static_cast<const unsigned short *>(it.data), it.nx,
+                                                                  it.ny, it.nz, it.nbx, it.nby};
+                batch_pixel<INTERP>(s, it, a, lut_s, px, py);
+            } else {
+                const SamplerBrick<__half, long long, K> s{static_cast<const unsigned short *>(it.data), it.nx,
+                                                           it.ny, it.nz, it.nbx, it.nby};
+                batch_pixel<INTERP>(s, it, a, lut_s, px, py);
+            }
         }
     }
 }
 
 using BatchKernel = void (*)(const BatchItemDev *, const int2 *, int *, BatchShared);
 
-// The kernel for a tile edge (8 or 16), an interpolation, a brick edge (16 or 32) and
-// whether any item is float32 (brick edge 32 only); without float32 every item must be
-// a bfloat16 or binary16 brick item of that edge.
-BatchKernel batch_kernel_for(int tile, int interp, int brick, bool f32);
+// The kernel for a tile edge (8 or 16), an interpolation and a kind of item (0: float32
+// cubes; 16, 32: bfloat16 or binary16 bricks of that edge).  Every item of its work list
+// must be of that kind.
+BatchKernel batch_kernel_for(int tile, int interp, int kind);
 BatchKernel batch_kernel_b16(int tile, int interp);  // batch_b16.cu
 BatchKernel batch_kernel_b32(int tile, int interp);  // batch_b32.cu
 

@@ -253,3 +253,20 @@ def test_batch_of_bricks_only(m):
     for (vol, cam, mode), img in zip(dev, outs):
         assert torch.equal(img, m.render(vol, cam, mode, lut=lut, opacity_scale=0.05)["rgba"]), mode
     plan.close()
+
+
+def test_batch_runs_one_kernel_per_kind(m):
+    """Float32 cubes and bricks in one plan run as two kernels in the plan's graph (one
+    work list each); a plan of one kind runs one.  The images equal the single renders."""
+    lut = to_dev(scene.linear_lut())
+    for cycle, kernels in ((("f32", "bf16", "f16"), 2), (("f32",), 1), (("bf16", "f16"), 1)):
+        items = _batch(n=7, storage_cycle=cycle, modes=("mip", "composite", "avg", "spectral"))
+        dev = _dev_items(m, items)
+        plan = m.BatchPlan(dev, lut=lut, opacity_scale=0.05, tune=False)
+        before = m.launch_count()
+        outs = plan.render()
+        assert m.launch_count() == before + kernels, cycle
+        m.sync_status()
+        for (vol, cam, mode), img in zip(dev, outs):
+            assert torch.equal(img, m.render(vol, cam, mode, lut=lut, opacity_scale=0.05)["rgba"]), (cycle, mode)
+        plan.close()
