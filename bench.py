@@ -673,12 +673,23 @@ def variant_precision(shw, torch, step, W, per_kernel, samples_per):
                                      "gather marcher; both hold the same rounded values"}
 
 
+def best_by_brick_edge(candidates):
+    """The fastest (tile, CTAs per SM, time) of each brick edge among a plan's tuned candidates
+    (tile, ctas_per_sm, edge, ms); ties keep the earlier candidate, as the autotuner does."""
+    best = {}
+    for tile, ctas, edge, ms in candidates:
+        if edge not in best or ms < best[edge][2]:
+            best[edge] = (tile, ctas, ms)
+    return {str(e): {"tile": t, "ctas_per_sm": c, "tune_ms": round(ms, 3)} for e, (t, c, ms) in sorted(best.items())}
+
+
 def variant_batch(shw, torch, step, B):
     """2,000 sub-cubes (axes log-uniform in [32, 256]; float32 and BF16 bricks alternating; MIP and
     compositing alternating; 256x256 random views): one graph-captured persistent launch
     against one launch per sub-cube issued by the library's own loop.  Then the same
-    sub-cubes all as float32 in a plan that rounds them into bfloat16 bricks of its own, the
-    autotuner choosing the brick edge (16 or 32) with the tile and CTAs per SM."""
+    sub-cubes all as float32, in a plan that renders them as they are and in one that rounds
+    them into bfloat16 bricks of its own, the autotuner choosing the brick edge (16 or 32)
+    with the tile and CTAs per SM."""
     import concurrent.futures as cf
     dev = step.s1.device
     dims = scene.batch_dims(n=B["n"], lo=B["lo"], hi=B["hi"])
@@ -709,6 +720,11 @@ def variant_batch(shw, torch, step, B):
     info = plan.info
     plan.close()
     del items
+    # every sub-cube as float32, rendered as it is
+    f32_plan = shw.BatchPlan(f32_items, lut=step.lut, step=B["step"], opacity_scale=B["opacity_scale"], retune=True)
+    t_f32 = _timeit(torch, f32_plan.render, reps=3)
+    finf = f32_plan.info
+    f32_plan.close()
     # every sub-cube as float32, rounded by the plan into bfloat16 bricks of the edge it tunes
     t0 = time.time()
     own = shw.BatchPlan(f32_items, lut=step.lut, step=B["step"], opacity_scale=B["opacity_scale"], pack="bf16",
@@ -718,14 +734,13 @@ def variant_batch(shw, torch, step, B):
     oinf = own.info
     own.close()
     del f32_items
-    by_edge = {}
-    for tile, ctas, edge, ms in oinf["candidates"]:
-        if str(edge) not in by_edge or ms < by_edge[str(edge)]["tune_ms"]:
-            by_edge[str(edge)] = {"tile": tile, "ctas_per_sm": ctas, "tune_ms": round(ms, 3)}
+    by_edge = best_by_brick_edge(oinf["candidates"])
     own_bricks = {"persistent_graph_ms": round(t_own, 3), "subcubes_per_s": round(len(dims) / (t_own * 1e-3), 1),
                   "brick": oinf["brick"], "tile": oinf["tile"], "ctas_per_sm": oinf["ctas_per_sm"],
                   "packed_gb": round(oinf["packed_bytes"] / 1e9, 3), "plan_create_s": round(t_create, 2),
-                  "best_by_brick_edge": by_edge}
+                  "best_by_brick_edge": by_edge, "speedup_vs_all_float32_plan": round(t_f32 / t_own, 3)}
+    all_f32 = {"persistent_graph_ms": round(t_f32, 3), "subcubes_per_s": round(len(dims) / (t_f32 * 1e-3), 1),
+               "tile": finf["tile"], "ctas_per_sm": finf["ctas_per_sm"]}
     return {"n": int(len(dims)), "voxels": int(nvox), "samples": ns,
             "persistent_graph_ms": round(t_plan, 3), "one_launch_per_cube_ms": round(t_loop, 3),
             "subcubes_per_s": round(len(dims) / (t_plan * 1e-3), 1),
@@ -733,7 +748,7 @@ def variant_batch(shw, torch, step, B):
             "speedup": round(t_loop / t_plan, 3), "gsamples_per_s": round(ns / (t_plan * 1e-3) / 1e9, 2),
             "tile": info["tile"], "ctas_per_sm": info["ctas_per_sm"],
             "baseline": "one shw_render launch per sub-cube from the library's loop (shw_render_items)",
-            "own_bf16_bricks": own_bricks}
+            "all_float32": all_f32, "own_bf16_bricks": own_bricks}
 
 
 def variant_adjoint(shw, torch, step):

@@ -83,3 +83,15 @@ def test_clock_record_keeps_this_gpus_rows():
     other.lines = cs.lines
     r2 = other.summary()
     assert r2["samples"] == 3 and r2["gpu_pci"] == "all listed GPUs"
+
+
+def test_best_by_brick_edge_compares_unrounded_times():
+    """The per-edge summary of a tuned plan picks what the autotuner picks: the smallest
+    measured time (not a rounded one), the earlier candidate on a tie."""
+    import bench
+    cands = [(16, 2, 16, 50.0), (8, 8, 16, 43.07440), (8, 32, 16, 43.07420), (8, 16, 16, 43.07420),
+             (16, 4, 32, 44.0), (8, 32, 32, 43.3461)]
+    got = bench.best_by_brick_edge(cands)
+    assert got == {"16": {"tile": 8, "ctas_per_sm": 32, "tune_ms": 43.074},
+                   "32": {"tile": 8, "ctas_per_sm": 32, "tune_ms": 43.346}}
+    assert bench.best_by_brick_edge([]) == {}
