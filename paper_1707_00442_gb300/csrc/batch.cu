@@ -5,16 +5,15 @@
 // detect (Section 1); rendering each with its own launch wastes most of the GPU on
 // launch latency and tail effects.  A plan lays out every (item, image tile) as a
 // work item, ordered longest-first (an LPT schedule: big cubes' tiles first, small
-// ones fill the tail); a persistent grid of CTAs pops work items from one atomic
+// ones fill the tail); a persistent grid of CTAs pops work items from an atomic
 // counter -- no CTA ever waits on another -- and renders each tile with the same
-// per-ray code as shw_render.  The counter reset and the launch are captured once
+// per-ray code as shw_render.  The counter resets and the launches are captured once
 // into a CUDA graph, so a batch render is a single graph launch.  Float32 cubes and
 // bricks are rendered by two kernels (one work list each, run one after the other in
 // the same graph): a kernel for both kinds would hold the registers of both paths.  An
-// autotuner
-// times the candidate tile shapes and CTAs-per-SM -- and, for plans that round their
-// float32 items into 16-bit bricks of their own, the brick edge (16 or 32 voxels) -- at
-// plan creation and caches the winner per batch signature.
+// autotuner times the candidate tile shapes and CTAs-per-SM -- and, for plans that round
+// their float32 items into 16-bit bricks of their own, the brick edge (16 or 32 voxels)
+// -- at plan creation and caches the winner per batch signature.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
