@@ -367,7 +367,8 @@ typedef struct shw_batch_plan shw_batch_plan; /* opaque */
 #define SHW_BATCH_BRICK_32 32 /* with a PACK flag: 32^3 bricks, the edge not tuned */
 
 typedef struct {
-    shw_volume vol;  /* the sub-cube: any storage, < 2^31 voxels */
+    shw_volume vol;  /* the sub-cube: SHW_F32 or 16-bit bricks, < 2^31 voxels; bricks (the caller's, or
+                        the plan's own at either edge) < 2^31 stored elements, else SHW_EUNSUPPORTED */
     shw_camera cam;  /* its view; its image is cam.width x cam.height */
     float *out_rgba; /* device [H][W][4] float32, 16-byte aligned; written by every shw_render_batch */
     int32_t mode;    /* SHW_MIP, SHW_AVG, SHW_COMPOSITE or SHW_SPECTRAL (SHW_RATIO: SHW_EUNSUPPORTED) */

@@ -33,6 +33,16 @@ bool valid_volume(const shw_volume *v);
 bool valid_camera(const shw_camera *c);
 long long max_samples(const shw_volume *v, float step);
 size_t bricked_bytes_edge(int nx, int ny, int nz, int edge);
+
+// Brick items are addressed with 32-bit element offsets: a storage of 2^31 elements or more
+// (a cube of about 1280^3 voxels) is not taken in a batch.  edge: 0 for the caller's
+// storage, else the edge of the plan's own bricks.
+static bool bricks_fit_int(const shw_volume &v, int edge)
+{
+    const size_t bytes =
+        edge ? bricked_bytes_edge(v.nx, v.ny, v.nz, edge) : shw_bricked_bytes(v.nx, v.ny, v.nz, v.storage);
+    return bytes / 2 < ((size_t)1 << 31);
+}
 shw_status pack_bricks_edge(const float *in, int nx, int ny, int nz, int storage, int edge, void *out,
                             cudaStream_t st);
 
@@ -353,6 +363,9 @@ shw_status shw_batch_plan_create(shw_batch_plan **out, const shw_batch_item *ite
         if ((long long)b.vol.nx * b.vol.ny * b.vol.nz >= (1LL << 31)) return SHW_EUNSUPPORTED;
         if (b.vol.storage >= SHW_F32_PAIR) return SHW_EUNSUPPORTED;  // the line ratios' storages
         if (max_samples(&b.vol, p->step) > (1LL << 30)) return SHW_EINVAL;
+        if (b.vol.storage != SHW_F32 && !bricks_fit_int(b.vol, 0)) return SHW_EUNSUPPORTED;
+        if (pack && b.vol.storage == SHW_F32 && (!bricks_fit_int(b.vol, 16) || !bricks_fit_int(b.vol, 32)))
+            return SHW_EUNSUPPORTED;
         n_own += (pack && b.vol.storage == SHW_F32) ? 1 : 0;
     }
     // brick edges to try: 16 needs its own kernel, which reads only the plan's bricks, so
@@ -584,6 +597,7 @@ extern "C" shw_status shw_render_batch_noalloc(const shw_batch_item *items, int3
         if ((long long)b.vol.nx * b.vol.ny * b.vol.nz >= (1LL << 31)) return SHW_EUNSUPPORTED;
         if (b.vol.storage >= SHW_F32_PAIR) return SHW_EUNSUPPORTED;  // the line ratios' storages
         if (max_samples(&b.vol, p->step) > (1LL << 30)) return SHW_EINVAL;
+        if (b.vol.storage != SHW_F32 && !bricks_fit_int(b.vol, 0)) return SHW_EUNSUPPORTED;
         nwork += (long long)ceil_div(b.cam.width, tile) * ceil_div(b.cam.height, tile);
         cost[i] = (double)b.cam.width * b.cam.height * std::cbrt((double)b.vol.nx * b.vol.ny * b.vol.nz) / p->step;
     }

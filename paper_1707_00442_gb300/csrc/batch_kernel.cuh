@@ -77,13 +77,14 @@ __global__ void __launch_bounds__(TILE *TILE) batch_kernel(const BatchItemDev *_
             const SamplerF32<int> s{static_cast<const float *>(it.data), it.nx, it.ny, it.nz, it.nx, it.nx * it.ny};
             batch_pixel<INTERP>(s, it, a, lut_s, px, py);
         } else {
+            // 32-bit element offsets: the plans admit brick items of fewer than 2^31 elements
             if (it.storage == SHW_BF16_BRICK) {
-                const SamplerBrick<__nv_bfloat16, long long, K> s{static_cast<const unsigned short *>(it.data), it.nx,
-                                                                  it.ny, it.nz, it.nbx, it.nby};
+                const SamplerBrick<__nv_bfloat16, int, K> s{static_cast<const unsigned short *>(it.data), it.nx, it.ny,
+                                                            it.nz, it.nbx, it.nby};
                 batch_pixel<INTERP>(s, it, a, lut_s, px, py);
             } else {
-                const SamplerBrick<__half, long long, K> s{static_cast<const unsigned short *>(it.data), it.nx,
-                                                           it.ny, it.nz, it.nbx, it.nby};
+                const SamplerBrick<__half, int, K> s{static_cast<const unsigned short *>(it.data), it.nx, it.ny, it.nz,
+                                                     it.nbx, it.nby};
                 batch_pixel<INTERP>(s, it, a, lut_s, px, py);
             }
         }

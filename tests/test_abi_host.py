@@ -250,6 +250,13 @@ def test_batch_plan_rejects_invalid_arguments_on_host(L):
     assert L.shw_batch_plan_create(b(h), items, 2, b(p), B32, None) == 1
     items[1].vol = _vol(storage=1)
     assert L.shw_batch_plan_create(b(h), items, 2, b(p), PF | B16, None) == 2
+    # brick items are addressed with 32-bit offsets: a 1281^3 cube (< 2^31 voxels) as 32^3
+    # bricks holds 41^3 * 34^3 > 2^31 elements, and is refused as bricks, plain or packed
+    items[1].vol = _vol(n=(1281, 1281, 1281), storage=1)
+    assert L.shw_batch_plan_create(b(h), items, 2, b(p), 0, None) == 2
+    assert L.shw_render_batch_noalloc(items, 2, b(p), None) == 2
+    items[1].vol = _vol(n=(1281, 1281, 1281), storage=0)
+    assert L.shw_batch_plan_create(b(h), items, 2, b(p), PB, None) == 2
     assert h.value is None
     assert L.shw_render_batch(None, None) == 1
     assert L.shw_batch_plan_destroy(None) == 1
