@@ -42,6 +42,25 @@ def test_binding_covers_header(L):
     assert set(_lib.SIGNATURES) == set(declared_functions())
 
 
+def header_defines():
+    src = "".join(open(h).read() for h in glob.glob(os.path.join(ROOT, "include", "*.h")))
+    return {m.group(1): int(m.group(2), 0) for m in re.finditer(r"#define\s+(SHW_[A-Z0-9_]+)\s+\(?(0x[0-9a-fA-F]+|\d+)",
+                                                                  src)}
+
+
+def test_binding_flags_match_header():
+    """The binding's flag and switch values are the header's #defines."""
+    from paper_1707_00442_gb300 import _lib
+    d = header_defines()
+    assert (_lib.BATCH_NO_TUNE, _lib.BATCH_RETUNE) == (d["SHW_BATCH_NO_TUNE"], d["SHW_BATCH_RETUNE"])
+    assert _lib.BATCH_PACK == {None: 0, "bf16": d["SHW_BATCH_PACK_BF16"], "f16": d["SHW_BATCH_PACK_F16"]}
+    assert _lib.BATCH_BRICK == {None: 0, 16: d["SHW_BATCH_BRICK_16"], 32: d["SHW_BATCH_BRICK_32"]}
+    for name, value in _lib.DEBUG.items():
+        assert d["SHW_DEBUG_" + name.upper()] == value, name
+    assert _lib.ABI_VERSION == d["SHW_ABI_VERSION"]
+    assert _lib.NOALLOC_SCRATCH_BYTES == 8 << 20
+
+
 def test_struct_layout(L):
     from paper_1707_00442_gb300 import _lib
     assert L.shw_struct_size(0) == C.sizeof(_lib.Volume) == 24
